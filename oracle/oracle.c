@@ -1,0 +1,581 @@
+/* Plain, slow FP64 CPU oracle for the FFTK/Tarang hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY: loaded by the tests, the smoke check and the
+ * benchmark's CPU-baseline leg, never by the product library.  It shares no
+ * code with the CUDA path.  Every routine is written for readability: a
+ * textbook recursive radix-2 FFT, line-by-line 3D passes in the order of the
+ * paper's Sec. 3, and pointwise loops for the solver.  OpenMP only splits
+ * independent lines / points across threads; it changes no arithmetic order
+ * within a line.
+ *
+ * Parity status: every function here is pinned by the CPU tests against closed
+ * forms, brute-force sums, invariants or numpy's FFT (see the test files);
+ * the turbulent 512^3 run after many steps is checked only through those pins.
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define TWO_PI 6.283185307179586476925286766559005768
+
+typedef ocplx cplx;
+
+static int is_pow2(long n) { return n >= 1 && (n & (n - 1)) == 0; }
+
+/* tw[m] = exp(sign * 2 pi i m / n) for m < max(n/2, 1), FP64 host libm. */
+static cplx *make_twiddles(long n, int sign) {
+  long h = n / 2 > 0 ? n / 2 : 1;
+  cplx *tw = (cplx *)malloc(sizeof(cplx) * (size_t)h);
+  if (!tw) return NULL;
+  for (long m = 0; m < h; m++) {
+    double ang = TWO_PI * (double)m / (double)n;
+    tw[m] = cos(ang) + (double)sign * sin(ang) * I;
+  }
+  return tw;
+}
+
+/* Recursive radix-2 decimation in time (Cooley and Tukey, 1965):
+ *   out[k] = sum_{j<n} in[j*stride] exp(sign 2 pi i j k / n).
+ * The sub-transform of length n uses tw[k * twstep], twstep = n_top / n. */
+static void fft_rec(const cplx *in, long stride, cplx *out, long n,
+                    const cplx *tw, long twstep) {
+  if (n == 1) {
+    out[0] = in[0];
+    return;
+  }
+  long h = n / 2;
+  fft_rec(in, 2 * stride, out, h, tw, 2 * twstep);          /* even samples */
+  fft_rec(in + stride, 2 * stride, out + h, h, tw, 2 * twstep); /* odd samples */
+  for (long k = 0; k < h; k++) {
+    cplx e = out[k];
+    cplx o = tw[k * twstep] * out[k + h];
+    out[k] = e + o;
+    out[k + h] = e - o;
+  }
+}
+
+int oracle_fft1d(const cplx *in, cplx *out, long n, int sign) {
+  if (!is_pow2(n) || (sign != 1 && sign != -1)) return -1;
+  cplx *tw = make_twiddles(n, sign);
+  if (!tw) return -2;
+  fft_rec(in, 1, out, n, tw, 1);
+  free(tw);
+  return 0;
+}
+
+/* The DFT by its definition, O(n^2); the phase j*k is reduced mod n first. */
+int oracle_dft1d(const cplx *in, cplx *out, long n, int sign) {
+  if (n < 1 || (sign != 1 && sign != -1)) return -1;
+  for (long k = 0; k < n; k++) {
+    cplx s = 0;
+    for (long j = 0; j < n; j++) {
+      long m = (j * k) % n;
+      double ang = TWO_PI * (double)m / (double)n;
+      s += in[j] * (cos(ang) + (double)sign * sin(ang) * I);
+    }
+    out[k] = s;
+  }
+  return 0;
+}
+
+/* ---------------------------------------------------------------- 3D ---- */
+
+static long maxl3(long a, long b, long c) {
+  long m = a > b ? a : b;
+  return m > c ? m : c;
+}
+
+/* Forward: Sec. 3 steps 1 (r2c along z), 3 (c2c along y), 5 (c2c along x);
+ * the 1/(Nx Ny Nz) factor makes Eq. (1) its inverse. */
+int oracle_rfft3(const double *in, cplx *out, int nx, int ny, int nz) {
+  if (!is_pow2(nx) || !is_pow2(ny) || !is_pow2(nz) || nz < 2) return -1;
+  const long NX = nx, NY = ny, NZ = nz, HZ = nz / 2 + 1;
+  cplx *twz = make_twiddles(NZ, -1), *twy = make_twiddles(NY, -1),
+       *twx = make_twiddles(NX, -1);
+  const long LMAX = maxl3(NX, NY, NZ);
+  int rc = 0;
+#pragma omp parallel
+  {
+    cplx *lin = (cplx *)malloc(sizeof(cplx) * (size_t)LMAX);
+    cplx *lout = (cplx *)malloc(sizeof(cplx) * (size_t)LMAX);
+    /* step 1: real-to-complex along z for every (i, j) column */
+#pragma omp for schedule(static)
+    for (long ij = 0; ij < NX * NY; ij++) {
+      for (long l = 0; l < NZ; l++) lin[l] = in[ij * NZ + l];
+      fft_rec(lin, 1, lout, NZ, twz, 1);
+      for (long c = 0; c < HZ; c++) out[ij * HZ + c] = lout[c];
+    }
+    /* step 3: complex-to-complex along y for every (i, k_z) */
+#pragma omp for schedule(static)
+    for (long ic = 0; ic < NX * HZ; ic++) {
+      long i = ic / HZ, c = ic % HZ;
+      for (long j = 0; j < NY; j++) lin[j] = out[(i * NY + j) * HZ + c];
+      fft_rec(lin, 1, lout, NY, twy, 1);
+      for (long j = 0; j < NY; j++) out[(i * NY + j) * HZ + c] = lout[j];
+    }
+    /* step 5: complex-to-complex along x for every (k_y, k_z) */
+#pragma omp for schedule(static)
+    for (long jc = 0; jc < NY * HZ; jc++) {
+      for (long i = 0; i < NX; i++) lin[i] = out[i * NY * HZ + jc];
+      fft_rec(lin, 1, lout, NX, twx, 1);
+      for (long i = 0; i < NX; i++) out[i * NY * HZ + jc] = lout[i];
+    }
+    free(lin);
+    free(lout);
+  }
+  const double scale = 1.0 / ((double)NX * (double)NY * (double)NZ);
+  const long M = NX * NY * HZ;
+#pragma omp parallel for schedule(static)
+  for (long m = 0; m < M; m++) out[m] *= scale;
+  free(twz);
+  free(twy);
+  free(twx);
+  return rc;
+}
+
+/* Inverse: the reverse of the forward passes (Sec. 3): x, y, then z c2r.  The
+ * z line is extended by f(N-c) = conj(f(c)) and the real part is kept. */
+int oracle_irfft3(const cplx *in, double *out, int nx, int ny, int nz) {
+  if (!is_pow2(nx) || !is_pow2(ny) || !is_pow2(nz) || nz < 2) return -1;
+  const long NX = nx, NY = ny, NZ = nz, HZ = nz / 2 + 1;
+  const long M = NX * NY * HZ;
+  cplx *work = (cplx *)malloc(sizeof(cplx) * (size_t)M);
+  if (!work) return -2;
+  memcpy(work, in, sizeof(cplx) * (size_t)M);
+  cplx *twz = make_twiddles(NZ, +1), *twy = make_twiddles(NY, +1),
+       *twx = make_twiddles(NX, +1);
+  const long LMAX = maxl3(NX, NY, NZ);
+#pragma omp parallel
+  {
+    cplx *lin = (cplx *)malloc(sizeof(cplx) * (size_t)LMAX);
+    cplx *lout = (cplx *)malloc(sizeof(cplx) * (size_t)LMAX);
+#pragma omp for schedule(static)
+    for (long jc = 0; jc < NY * HZ; jc++) {
+      for (long i = 0; i < NX; i++) lin[i] = work[i * NY * HZ + jc];
+      fft_rec(lin, 1, lout, NX, twx, 1);
+      for (long i = 0; i < NX; i++) work[i * NY * HZ + jc] = lout[i];
+    }
+#pragma omp for schedule(static)
+    for (long ic = 0; ic < NX * HZ; ic++) {
+      long i = ic / HZ, c = ic % HZ;
+      for (long j = 0; j < NY; j++) lin[j] = work[(i * NY + j) * HZ + c];
+      fft_rec(lin, 1, lout, NY, twy, 1);
+      for (long j = 0; j < NY; j++) work[(i * NY + j) * HZ + c] = lout[j];
+    }
+#pragma omp for schedule(static)
+    for (long ij = 0; ij < NX * NY; ij++) {
+      for (long c = 0; c < NZ; c++)
+        lin[c] = (c < HZ) ? work[ij * HZ + c] : conj(work[ij * HZ + (NZ - c)]);
+      fft_rec(lin, 1, lout, NZ, twz, 1);
+      for (long l = 0; l < NZ; l++) out[ij * NZ + l] = creal(lout[l]);
+    }
+    free(lin);
+    free(lout);
+  }
+  free(twz);
+  free(twy);
+  free(twx);
+  free(work);
+  return 0;
+}
+
+/* exp(sign 2 pi i m / n) for m reduced mod n. */
+static cplx phase(long m, long n, int sign) {
+  m %= n;
+  if (m < 0) m += n;
+  double ang = TWO_PI * (double)m / (double)n;
+  return cos(ang) + (double)sign * sin(ang) * I;
+}
+
+void oracle_rfft3_coeff_f32(const float *in, int nx, int ny, int nz, int a, int b, int c,
+                            double *re_im) {
+  const long NX = nx, NY = ny, NZ = nz;
+  cplx *ex = (cplx *)malloc(sizeof(cplx) * (size_t)NX);
+  cplx *ey = (cplx *)malloc(sizeof(cplx) * (size_t)NY);
+  cplx *ez = (cplx *)malloc(sizeof(cplx) * (size_t)NZ);
+  for (long i = 0; i < NX; i++) ex[i] = phase((long)a * i, NX, -1);
+  for (long j = 0; j < NY; j++) ey[j] = phase((long)b * j, NY, -1);
+  for (long l = 0; l < NZ; l++) ez[l] = phase((long)c * l, NZ, -1);
+  double sre = 0.0, sim = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : sre, sim)
+  for (long i = 0; i < NX; i++) {
+    cplx si = 0;
+    for (long j = 0; j < NY; j++) {
+      cplx sj = 0;
+      const float *line = in + (i * NY + j) * NZ;
+      for (long l = 0; l < NZ; l++) sj += (double)line[l] * ez[l];
+      si += ey[j] * sj;
+    }
+    cplx t = ex[i] * si;
+    sre += creal(t);
+    sim += cimag(t);
+  }
+  free(ex);
+  free(ey);
+  free(ez);
+  const double scale = 1.0 / ((double)NX * (double)NY * (double)NZ);
+  re_im[0] = sre * scale;
+  re_im[1] = sim * scale;
+}
+
+double oracle_irfft3_point_c64(const float *in, int nx, int ny, int nz, int i, int j, int l) {
+  const long NX = nx, NY = ny, NZ = nz, HZ = nz / 2 + 1;
+  double s = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : s)
+  for (long a = 0; a < NX; a++) {
+    cplx pa = phase(a * i, NX, +1);
+    double sa = 0.0;
+    for (long b = 0; b < NY; b++) {
+      cplx pab = pa * phase(b * j, NY, +1);
+      for (long c = 0; c < HZ; c++) {
+        const float *v = in + 2 * ((a * NY + b) * HZ + c);
+        cplx f = (double)v[0] + (double)v[1] * I;
+        double w = (c == 0 || 2 * c == NZ) ? 1.0 : 2.0;
+        sa += w * creal(f * pab * phase(c * l, NZ, +1));
+      }
+    }
+    s += sa;
+  }
+  return s;
+}
+
+/* --------------------------------------------------------- wavenumbers ---- */
+
+/* Wavenumber of index a on an x or y axis: a if a < n/2, else a - n
+ * (the Nyquist index n/2 stands for -n/2); on z the index is the wavenumber. */
+static long kxy(long a, long n) { return (2 * a < n) ? a : a - n; }
+/* Wavenumber used inside derivatives: the Nyquist mode gets i k := 0. */
+static long kder(long k, long n) { return (2 * labs(k) == n) ? 0 : k; }
+/* 2/3 rule (Sec. 2.2): keep the mode only if 3|k| < N along every axis. */
+static int kept(long kx, long ky, long kz, long n) {
+  return 3 * labs(kx) < n && 3 * labs(ky) < n && 3 * labs(kz) < n;
+}
+
+int oracle_dealias(cplx *f, int nfields, int n) {
+  const long N = n, HZ = n / 2 + 1, M = N * N * HZ;
+  for (int fld = 0; fld < nfields; fld++)
+    for (long a = 0; a < N; a++)
+      for (long b = 0; b < N; b++)
+        for (long c = 0; c < HZ; c++)
+          if (!kept(kxy(a, N), kxy(b, N), c, N)) f[fld * M + (a * N + b) * HZ + c] = 0;
+  return 0;
+}
+
+/* Projection onto divergence-free fields, Eq. (8): u <- u - k (k.u)/|k|^2,
+ * with u(0) = 0. */
+int oracle_project(cplx *u, int n) {
+  const long N = n, HZ = n / 2 + 1, M = N * N * HZ;
+  for (long a = 0; a < N; a++)
+    for (long b = 0; b < N; b++)
+      for (long c = 0; c < HZ; c++) {
+        long idx = (a * N + b) * HZ + c;
+        double kx = (double)kxy(a, N), ky = (double)kxy(b, N), kz = (double)c;
+        double k2 = kx * kx + ky * ky + kz * kz;
+        if (k2 == 0.0) {
+          u[idx] = u[M + idx] = u[2 * M + idx] = 0;
+          continue;
+        }
+        cplx kdotu = kx * u[idx] + ky * u[M + idx] + kz * u[2 * M + idx];
+        u[idx] -= kx * kdotu / k2;
+        u[M + idx] -= ky * kdotu / k2;
+        u[2 * M + idx] -= kz * kdotu / k2;
+      }
+  return 0;
+}
+
+static double mode_weight(long c, long nz) { return (c == 0 || 2 * c == nz) ? 1.0 : 2.0; }
+
+static double sq(cplx z) { return creal(z) * creal(z) + cimag(z) * cimag(z); }
+
+/* ------------------------------------------------------ Navier-Stokes ---- */
+
+/* Sum over forced modes of 1/2 w |u|^2. */
+static double forced_energy(const cplx *u, int n, const oracle_ns_params *p) {
+  const long N = n, HZ = n / 2 + 1, M = N * N * HZ;
+  double e = 0.0;
+  for (long a = 0; a < N; a++)
+    for (long b = 0; b < N; b++)
+      for (long c = 0; c < HZ; c++) {
+        long kx = kxy(a, N), ky = kxy(b, N), k2 = kx * kx + ky * ky + c * c;
+        if (k2 < p->force_k2min || k2 > p->force_k2max) continue;
+        long idx = (a * N + b) * HZ + c;
+        e += 0.5 * mode_weight(c, N) * (sq(u[idx]) + sq(u[M + idx]) + sq(u[2 * M + idx]));
+      }
+  return e;
+}
+
+int oracle_ns_rhs(const cplx *uhat, cplx *nhat, int n, const oracle_ns_params *p) {
+  if (!is_pow2(n) || n < 2) return -1;
+  const long N = n, HZ = n / 2 + 1, M = N * N * HZ, R = N * N * N;
+  cplx *what = (cplx *)malloc(sizeof(cplx) * 3 * (size_t)M);
+  double *ur = (double *)malloc(sizeof(double) * 3 * (size_t)R);
+  double *wr = (double *)malloc(sizeof(double) * 3 * (size_t)R);
+  double *nr = (double *)malloc(sizeof(double) * 3 * (size_t)R);
+  if (!what || !ur || !wr || !nr) return -2;
+  /* 1. vorticity omega = curl u, in Fourier space i k x u */
+  for (long a = 0; a < N; a++)
+    for (long b = 0; b < N; b++)
+      for (long c = 0; c < HZ; c++) {
+        long idx = (a * N + b) * HZ + c;
+        double kx = (double)kder(kxy(a, N), N), ky = (double)kder(kxy(b, N), N),
+               kz = (double)kder(c, N);
+        cplx ux = uhat[idx], uy = uhat[M + idx], uz = uhat[2 * M + idx];
+        what[idx] = I * (ky * uz - kz * uy);
+        what[M + idx] = I * (kz * ux - kx * uz);
+        what[2 * M + idx] = I * (kx * uy - ky * ux);
+      }
+  /* 2. velocity and vorticity in real space */
+  for (int f = 0; f < 3; f++) {
+    oracle_irfft3(uhat + f * M, ur + f * R, n, n, n);
+    oracle_irfft3(what + f * M, wr + f * R, n, n, n);
+  }
+  /* 3. pointwise product u x omega (the pseudo-spectral step of Sec. 2.2) */
+#pragma omp parallel for schedule(static)
+  for (long x = 0; x < R; x++) {
+    double ux = ur[x], uy = ur[R + x], uz = ur[2 * R + x];
+    double wx = wr[x], wy = wr[R + x], wz = wr[2 * R + x];
+    nr[x] = uy * wz - uz * wy;
+    nr[R + x] = uz * wx - ux * wz;
+    nr[2 * R + x] = ux * wy - uy * wx;
+  }
+  /* 4. back to Fourier space, 5. dealias, 6. project */
+  for (int f = 0; f < 3; f++) oracle_rfft3(nr + f * R, nhat + f * M, n, n, n);
+  oracle_dealias(nhat, 3, n);
+  oracle_project(nhat, n);
+  /* 7. constant-power forcing: f = eps u / (2 E_f) on the forced modes */
+  if (p && p->force_eps > 0.0) {
+    double ef = forced_energy(uhat, n, p);
+    if (ef > 0.0) {
+      double g = p->force_eps / (2.0 * ef);
+      for (long a = 0; a < N; a++)
+        for (long b = 0; b < N; b++)
+          for (long c = 0; c < HZ; c++) {
+            long kx = kxy(a, N), ky = kxy(b, N), k2 = kx * kx + ky * ky + c * c;
+            if (k2 < p->force_k2min || k2 > p->force_k2max) continue;
+            long idx = (a * N + b) * HZ + c;
+            for (int f = 0; f < 3; f++) nhat[f * M + idx] += g * uhat[f * M + idx];
+          }
+    }
+  }
+  free(what);
+  free(ur);
+  free(wr);
+  free(nr);
+  return 0;
+}
+
+int oracle_ns_rhs_divergence(const cplx *uhat, cplx *nhat, int n) {
+  if (!is_pow2(n) || n < 2) return -1;
+  const long N = n, HZ = n / 2 + 1, M = N * N * HZ, R = N * N * N;
+  double *ur = (double *)malloc(sizeof(double) * 3 * (size_t)R);
+  double *pr = (double *)malloc(sizeof(double) * (size_t)R);
+  cplx *th = (cplx *)malloc(sizeof(cplx) * 9 * (size_t)M); /* T_lj, full 3x3 */
+  if (!ur || !pr || !th) return -2;
+  for (int f = 0; f < 3; f++) oracle_irfft3(uhat + f * M, ur + f * R, n, n, n);
+  for (int l = 0; l < 3; l++)
+    for (int j = 0; j < 3; j++) {
+      for (long x = 0; x < R; x++) pr[x] = ur[l * R + x] * ur[j * R + x];
+      oracle_rfft3(pr, th + (l * 3 + j) * M, n, n, n);
+    }
+  for (long a = 0; a < N; a++)
+    for (long b = 0; b < N; b++)
+      for (long c = 0; c < HZ; c++) {
+        long idx = (a * N + b) * HZ + c;
+        double k[3] = {(double)kder(kxy(a, N), N), (double)kder(kxy(b, N), N),
+                       (double)kder(c, N)};
+        for (int j = 0; j < 3; j++) {
+          cplx s = 0;
+          for (int l = 0; l < 3; l++) s += k[l] * th[(l * 3 + j) * M + idx];
+          nhat[j * M + idx] = -I * s;
+        }
+      }
+  oracle_dealias(nhat, 3, n);
+  oracle_project(nhat, n);
+  free(ur);
+  free(pr);
+  free(th);
+  return 0;
+}
+
+/* RK2 (Heun) with integrating factor E = exp(-nu |k|^2 dt):
+ *   u1 = E (u + dt N(u)),   u_new = 1/2 E u + 1/2 (u1 + dt N(u1)). */
+int oracle_ns_step(cplx *uhat, int n, const oracle_ns_params *p, int nsteps) {
+  if (!is_pow2(n) || n < 2 || !p) return -1;
+  const long N = n, HZ = n / 2 + 1, M = N * N * HZ;
+  cplx *u1 = (cplx *)malloc(sizeof(cplx) * 3 * (size_t)M);
+  cplx *nh = (cplx *)malloc(sizeof(cplx) * 3 * (size_t)M);
+  double *E = (double *)malloc(sizeof(double) * (size_t)M);
+  if (!u1 || !nh || !E) return -2;
+  for (long a = 0; a < N; a++)
+    for (long b = 0; b < N; b++)
+      for (long c = 0; c < HZ; c++) {
+        double kx = (double)kxy(a, N), ky = (double)kxy(b, N), kz = (double)c;
+        E[(a * N + b) * HZ + c] = exp(-p->nu * (kx * kx + ky * ky + kz * kz) * p->dt);
+      }
+  for (int s = 0; s < nsteps; s++) {
+    int rc = oracle_ns_rhs(uhat, nh, n, p);
+    if (rc) return rc;
+    for (int f = 0; f < 3; f++)
+      for (long m = 0; m < M; m++)
+        u1[f * M + m] = E[m] * (uhat[f * M + m] + p->dt * nh[f * M + m]);
+    oracle_dealias(u1, 3, n);
+    rc = oracle_ns_rhs(u1, nh, n, p);
+    if (rc) return rc;
+    for (int f = 0; f < 3; f++)
+      for (long m = 0; m < M; m++)
+        uhat[f * M + m] = 0.5 * E[m] * uhat[f * M + m] +
+                          0.5 * (u1[f * M + m] + p->dt * nh[f * M + m]);
+    oracle_dealias(uhat, 3, n);
+  }
+  free(u1);
+  free(nh);
+  free(E);
+  return 0;
+}
+
+/* Shell index K = nint(|k|); |k| is never a half-integer for integer k. */
+static long shell_of(long k2) { return (long)floor(sqrt((double)k2) + 0.5); }
+
+int oracle_diag(const cplx *u, int n, double nu, double *E, double *eps, double *EK,
+                int kmax) {
+  const long N = n, HZ = n / 2 + 1, M = N * N * HZ;
+  double e = 0.0, d = 0.0;
+  if (EK)
+    for (int K = 0; K <= kmax; K++) EK[K] = 0.0;
+  for (long a = 0; a < N; a++)
+    for (long b = 0; b < N; b++)
+      for (long c = 0; c < HZ; c++) {
+        long idx = (a * N + b) * HZ + c;
+        long kx = kxy(a, N), ky = kxy(b, N), k2 = kx * kx + ky * ky + c * c;
+        double em = 0.5 * mode_weight(c, N) *
+                    (sq(u[idx]) + sq(u[M + idx]) + sq(u[2 * M + idx]));
+        e += em;
+        d += 2.0 * nu * (double)k2 * em;
+        long K = shell_of(k2);
+        if (EK && K <= kmax) EK[K] += em;
+      }
+  if (E) *E = e;
+  if (eps) *eps = d;
+  return 0;
+}
+
+double oracle_transfer(const cplx *u, const cplx *nh, int n) {
+  const long N = n, HZ = n / 2 + 1, M = N * N * HZ;
+  double t = 0.0;
+  for (long a = 0; a < N; a++)
+    for (long b = 0; b < N; b++)
+      for (long c = 0; c < HZ; c++) {
+        long idx = (a * N + b) * HZ + c;
+        for (int f = 0; f < 3; f++)
+          t += mode_weight(c, N) * creal(conj(u[f * M + idx]) * nh[f * M + idx]);
+      }
+  return t;
+}
+
+/* ----------------------------------------------------- initial fields ---- */
+
+static int ic_from_real(const double *ur, cplx *uhat, int n) {
+  const long N = n, HZ = n / 2 + 1, M = N * N * HZ, R = N * N * N;
+  for (int f = 0; f < 3; f++) {
+    int rc = oracle_rfft3(ur + f * R, uhat + f * M, n, n, n);
+    if (rc) return rc;
+  }
+  return 0;
+}
+
+int oracle_ic_taylor_green(cplx *uhat, int n) {
+  if (!is_pow2(n) || n < 2) return -1;
+  const long N = n, R = N * N * N;
+  double *ur = (double *)calloc(3 * (size_t)R, sizeof(double));
+  if (!ur) return -2;
+  for (long i = 0; i < N; i++)
+    for (long j = 0; j < N; j++)
+      for (long l = 0; l < N; l++) {
+        double x = TWO_PI * (double)i / (double)N, y = TWO_PI * (double)j / (double)N;
+        long r = (i * N + j) * N + l;
+        ur[r] = sin(x) * cos(y);
+        ur[R + r] = -cos(x) * sin(y);
+      }
+  int rc = ic_from_real(ur, uhat, n);
+  free(ur);
+  return rc;
+}
+
+int oracle_ic_abc(cplx *uhat, int n) {
+  if (!is_pow2(n) || n < 2) return -1;
+  const long N = n, R = N * N * N;
+  double *ur = (double *)malloc(3 * sizeof(double) * (size_t)R);
+  if (!ur) return -2;
+  for (long i = 0; i < N; i++)
+    for (long j = 0; j < N; j++)
+      for (long l = 0; l < N; l++) {
+        double x = TWO_PI * (double)i / (double)N, y = TWO_PI * (double)j / (double)N,
+               z = TWO_PI * (double)l / (double)N;
+        long r = (i * N + j) * N + l;
+        ur[r] = sin(z) + cos(y);
+        ur[R + r] = sin(x) + cos(z);
+        ur[2 * R + r] = sin(y) + cos(x);
+      }
+  int rc = ic_from_real(ur, uhat, n);
+  free(ur);
+  return rc;
+}
+
+/* Make the planes k_z = 0 and k_z = N/2 exactly Hermitian:
+ * f(-kx,-ky) = conj f(kx,ky), by averaging each pair. */
+static void hermitianize(cplx *f, int n) {
+  const long N = n, HZ = n / 2 + 1;
+  long planes[2] = {0, N / 2};
+  for (int pl = 0; pl < 2; pl++) {
+    long c = planes[pl];
+    for (long a = 0; a < N; a++)
+      for (long b = 0; b < N; b++) {
+        long a2 = (N - a) % N, b2 = (N - b) % N;
+        long i1 = (a * N + b) * HZ + c, i2 = (a2 * N + b2) * HZ + c;
+        if (i2 < i1) continue;
+        if (i1 == i2) {
+          f[i1] = creal(f[i1]);
+        } else {
+          cplx avg = 0.5 * (f[i1] + conj(f[i2]));
+          f[i1] = avg;
+          f[i2] = conj(avg);
+        }
+      }
+  }
+}
+
+int oracle_ic_random(const double *normals, cplx *uhat, int n, double k0, double E0) {
+  if (!is_pow2(n) || n < 2 || k0 <= 0.0 || E0 <= 0.0) return -1;
+  const long N = n, HZ = n / 2 + 1, M = N * N * HZ;
+  int rc = ic_from_real(normals, uhat, n);
+  if (rc) return rc;
+  oracle_dealias(uhat, 3, n);
+  oracle_project(uhat, n);
+  for (int f = 0; f < 3; f++) hermitianize(uhat + f * M, n);
+  const long KMAX = shell_of(3 * (N / 2) * (N / 2)) + 1;
+  double *eK = (double *)calloc((size_t)KMAX + 1, sizeof(double));
+  if (!eK) return -2;
+  oracle_diag(uhat, n, 0.0, NULL, NULL, eK, (int)KMAX);
+  for (long a = 0; a < N; a++)
+    for (long b = 0; b < N; b++)
+      for (long c = 0; c < HZ; c++) {
+        long kx = kxy(a, N), ky = kxy(b, N), k2 = kx * kx + ky * ky + c * c;
+        long K = shell_of(k2);
+        long idx = (a * N + b) * HZ + c;
+        double s = 0.0;
+        if (K >= 1 && eK[K] > 0.0) {
+          double Kd = (double)K;
+          double target = Kd * Kd * Kd * Kd * exp(-2.0 * (Kd / k0) * (Kd / k0));
+          s = sqrt(target / eK[K]);
+        }
+        for (int f = 0; f < 3; f++) uhat[f * M + idx] *= s;
+      }
+  double E = 0.0;
+  oracle_diag(uhat, n, 0.0, &E, NULL, NULL, 0);
+  double g = sqrt(E0 / E);
+  for (long m = 0; m < 3 * M; m++) uhat[m] *= g;
+  free(eK);
+  return 0;
+}

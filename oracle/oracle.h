@@ -1,0 +1,83 @@
+/* Plain, slow FP64 CPU oracle for the FFTK/Tarang hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the benchmark's
+ * CPU-baseline leg load this library; the product (libfftk) never does, and the
+ * two share no code.
+ *
+ * Conventions (Sec. 2.1, Eq. (1) and the Fourier basis of Eq. (2a)):
+ *   inverse  f(x) = sum_k fhat(k) exp(+i k.x)            (no factor)
+ *   forward  fhat(k) = (1/(Nx Ny Nz)) sum_x f(x) exp(-i k.x)
+ * with x = 2 pi (i/Nx, j/Ny, l/Nz) on a 2 pi-periodic box.
+ * Real arrays are double[Nx][Ny][Nz] (z fastest); half spectra are
+ * double complex[Nx][Ny][Nz/2+1] (axes not exchanged, as in Appendix A).
+ * Index a on an x or y axis stands for k = a if a <= N/2 else a - N; on z, k = c.
+ */
+#ifndef FFTK_ORACLE_H
+#define FFTK_ORACLE_H
+
+#include <complex.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef double _Complex ocplx;
+
+/* 1D transforms, out[k] = sum_j in[j] exp(sign 2 pi i j k / n). */
+int oracle_fft1d(const ocplx *in, ocplx *out, long n, int sign);   /* recursive radix-2, n = 2^m */
+int oracle_dft1d(const ocplx *in, ocplx *out, long n, int sign);   /* O(n^2) definition, any n */
+
+/* 3D transforms in the paper's pass order (Sec. 3): forward z r2c, y c2c, x c2c
+ * then the 1/N^3 factor; inverse x c2c, y c2c, z c2r. */
+int oracle_rfft3(const double *in, ocplx *out, int nx, int ny, int nz);
+int oracle_irfft3(const ocplx *in, double *out, int nx, int ny, int nz);
+
+/* One forward coefficient by the direct sum over all grid points (float input). */
+void oracle_rfft3_coeff_f32(const float *in, int nx, int ny, int nz, int a, int b, int c,
+                            double *re_im);
+/* One inverse output point by the direct sum over the stored half spectrum
+ * (complex64 input), weights 1 on the planes c = 0 and c = Nz/2, 2 elsewhere,
+ * real part taken: the line-wise "extend, then take the real part" result. */
+double oracle_irfft3_point_c64(const float *in_c64, int nx, int ny, int nz, int i, int j, int l);
+
+/* Pseudo-spectral Navier-Stokes (Sec. 2.2, Eqs. (7)-(8)), 2 pi-periodic cubic box,
+ * velocity state uhat[3][n][n][n/2+1]. */
+typedef struct {
+  double nu;        /* kinematic viscosity */
+  double dt;        /* time step */
+  double force_eps; /* constant injected power; 0 = unforced */
+  int force_k2min;  /* forced modes: force_k2min <= |k|^2 <= force_k2max */
+  int force_k2max;
+} oracle_ns_params;
+
+/* Nonlinear term in rotational form: P[ F(u x omega) ] dealiased (2/3 rule),
+ * plus forcing.  This is the right-hand side without the viscous term. */
+int oracle_ns_rhs(const ocplx *uhat, ocplx *nhat, int n, const oracle_ns_params *p);
+/* Divergence form -i k_l F(u_l u_j), dealiased and projected (Eq. (7) as printed). */
+int oracle_ns_rhs_divergence(const ocplx *uhat, ocplx *nhat, int n);
+/* nsteps of RK2 (Heun) with the viscous integrating factor exp(-nu k^2 dt). */
+int oracle_ns_step(ocplx *uhat, int n, const oracle_ns_params *p, int nsteps);
+
+/* Diagnostics: E = 1/2 sum w |u|^2, eps = nu sum w k^2 |u|^2,
+ * EK[K] = 1/2 sum_{nint|k| = K} w |u|^2 for K = 0..kmax (modes beyond kmax dropped). */
+int oracle_diag(const ocplx *uhat, int n, double nu, double *E, double *eps,
+                double *EK, int kmax);
+/* Energy transfer sum w Re(conj(u).N); zero for the rotational form. */
+double oracle_transfer(const ocplx *uhat, const ocplx *nhat, int n);
+
+/* Initial conditions. */
+int oracle_ic_taylor_green(ocplx *uhat, int n);  /* u = (sin x cos y, -cos x sin y, 0) */
+int oracle_ic_abc(ocplx *uhat, int n);           /* u = (sin z + cos y, sin x + cos z, sin y + cos x) */
+/* Random-phase solenoidal field from three normal fields normals[3][n][n][n]:
+ * forward transform, 2/3 truncation, projection, shell K = nint|k| rescaled so that
+ * its energy is proportional to K^4 exp(-2 (K/k0)^2), uhat(0) = 0, total energy E0. */
+int oracle_ic_random(const double *normals, ocplx *uhat, int n, double k0, double E0);
+
+/* Apply the 2/3 mask, projection, and wavenumber helpers (exposed for tests). */
+int oracle_dealias(ocplx *fhat, int nfields, int n);
+int oracle_project(ocplx *uhat, int n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
