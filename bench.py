@@ -1,0 +1,457 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 FFTK/Tarang hot path.
+
+Headline (one JSON line on rank 0): 512^3 decaying-turbulence Navier-Stokes
+steps/s (RK2 with viscous integrating factor, 2/3 dealiasing, FP32 data and
+arithmetic), with the 1024^3 FP32 R2C+C2R pair rate reported beside it.
+Inputs are synthetic and resident in HBM when the timed region starts; every
+field is larger than the 126 MB L2, so no explicit L2 flush is needed.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle on the host cores instead (the
+only other place, besides the CPU-baseline leg, where this script runs it).
+Multi-GPU runs (torchrun) are independent replicas: the method is not sharded.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "1024³ R2C+C2R pairs/s & 512³ NS steps/s, % HBM roofline; mixed vs FP32 at err"
+N_NS = 512
+NU, DT, K0, E0, SEED = 1e-3, 5e-4, 4.0, 0.5, 0
+N_FFT = 1024
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------- geometry ---
+def ns_counts(n):
+    kd = (n - 1) // 3
+    kc = kd + 1
+    nk = 2 * kd + 1
+    A = nk * nk * kc  # kept modes of one field
+    Bx = n * nk * kc  # one field after the inverse x pass
+    By = n * n * kc  # one field after the inverse y pass
+    M = n * n * (n // 2 + 1)
+    return A, Bx, By, M
+
+
+def ns_kernel_bytes(n):
+    """Algorithmic bytes per launch of each fused kernel (8 bytes per complex value
+    read or written; only the rows and columns the dealiased method touches)."""
+    A, Bx, By, _ = ns_counts(n)
+    c = 8
+    return {
+        "ns_invx_curl": c * (3 * A + 6 * Bx),
+        "ns_invy": c * (6 * Bx + 6 * By),
+        "ns_z_product": c * (6 * By + 3 * By),
+        "ns_fwdy": c * (3 * By + 3 * Bx),
+        "ns_fwdx_update": c * (3 * Bx + 7.5 * A),  # mean of stage 1 (6A) and stage 2 (9A)
+    }
+
+
+def ns_step_bytes(n):
+    kb = ns_kernel_bytes(n)
+    pruned = 2 * sum(kb.values())
+    _, _, _, M = ns_counts(n)
+    unpruned = 93 * 8 * M  # 3-pass method on full arrays, no pruning
+    return pruned, unpruned
+
+
+def fft_pass_bytes(n):
+    R = n**3
+    M = n * n * (n // 2 + 1)
+    return {
+        "z_r2c": 4 * R + 8 * M, "y_fwd": 16 * M, "x_fwd": 16 * M,
+        "x_inv": 16 * M, "y_inv": 16 * M, "z_c2r": 8 * M + 4 * R,
+    }
+
+
+# ----------------------------------------------------------------- clocks ---
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100",
+                 "-i", self.gpu_id], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons, n = [], None, set(), 0
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            n += 1
+            for name, v in zip(self.REASONS, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": n}
+
+
+# ------------------------------------------------------------ distributed ---
+def dist_setup(args):
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        backend = "nccl" if (args.impl == "ours" and torch.cuda.is_available()) else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world, dev=None):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(world, value, dev):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------- GPU arm --
+def run_ours(args, world, rank, local):
+    import torch
+
+    import paper_1805_07801_gb300 as fk
+    from paper_1805_07801_gb300 import build as fkbuild
+
+    fkbuild.build()
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    st_obj = torch.cuda.Stream(dev)
+    st = st_obj.cuda_stream
+    hbm, peak_kind = peaks()
+    props = torch.cuda.get_device_properties(dev)
+    gpu_id = str(local)
+    uuid = getattr(props, "uuid", None)
+    if uuid is not None:
+        gpu_id = "GPU-" + str(uuid) if not str(uuid).startswith("GPU-") else str(uuid)
+
+    n = N_NS
+    plan = fk.fftk_plan_create(n, n, n)
+    with torch.cuda.stream(st_obj):
+        normals = torch.empty((3, n, n, n), dtype=torch.float32, device=dev)
+        for f in range(3):
+            fk.fftk_fill_normal(normals[f].data_ptr(), n**3, SEED, f, st)
+        u = torch.empty((3, n, n, n // 2 + 1, 2), dtype=torch.float32, device=dev)
+        fk.tarang_ic_random(plan, normals.data_ptr(), u.data_ptr(), K0, E0, st)
+    del normals
+    prm = fk.make_params(NU, DT)
+    for _ in range(args.warmup):
+        fk.tarang_ns_step(plan, u.data_ptr(), prm, 1, False, st)
+    torch.cuda.synchronize(dev)
+
+    fk.fftk_profile_enable(plan, True)
+    clocks = Clocks(gpu_id)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    c0 = fk.fftk_launch_count(plan)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st_obj)
+    for _ in range(args.steps):
+        fk.tarang_ns_step(plan, u.data_ptr(), prm, 1, False, st)
+    e1.record(st_obj)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    clk = clocks.stop()
+    launches = fk.fftk_launch_count(plan) - c0
+    t_ms = e0.elapsed_time(e1)
+    t_ms = max_over_ranks(world, t_ms, dev)
+    kern = {}
+    for k in range(fk.fftk_kernel_kinds()):
+        ms, cnt = fk.fftk_profile_read(plan, k)
+        if cnt:
+            kern[fk.fftk_kernel_name(k)] = (ms, cnt)
+    fk.fftk_profile_enable(plan, False)
+    E, eps, _ = fk.tarang_diag(plan, u.data_ptr(), NU, st)
+
+    kb = ns_kernel_bytes(n)
+    kernels = {}
+    for name, (ms, cnt) in kern.items():
+        avg = ms / cnt
+        row = {"launches": cnt, "ms_avg": round(avg, 5), "share": round(ms / sum(v[0] for v in kern.values()), 4)}
+        if name in kb:
+            row["GBps"] = round(kb[name] / (avg * 1e-3) / 1e9, 1)
+        kernels[name] = row
+    dom = max(kern.items(), key=lambda kv: kv[1][0])[0]
+    dom_avg = kern[dom][0] / kern[dom][1]
+    achieved = kb[dom] / (dom_avg * 1e-3) / 1e9
+    pruned, unpruned = ns_step_bytes(n)
+    ms_step = t_ms / args.steps
+    value = world * args.steps / (t_ms * 1e-3)
+
+    # end to end through the C ABI with host buffers: H2D of the step's input
+    # state from pinned memory, the step, D2H of its diagnostics (E, eps, E(K))
+    k_e2e = min(args.steps, 10)
+    host_u = torch.empty(u.shape, dtype=torch.float32, pin_memory=True)
+    host_u.copy_(u)
+    u2 = torch.empty_like(u)
+    kmax = fk.tarang_diag_kmax(plan)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        with torch.cuda.stream(st_obj):
+            u2.copy_(host_u, non_blocking=True)
+        fk.tarang_ns_step(plan, u2.data_ptr(), prm, 1, True, st)
+    torch.cuda.synchronize(dev)
+    t_e2e = time.perf_counter() - t0
+    t_e2e = max_over_ranks(world, t_e2e, dev)
+    e2e = {"value": round(world * k_e2e / t_e2e, 3), "unit": "steps/s",
+           "h2d_bytes_per_step": int(u.numel() * 4), "d2h_bytes_per_step": int((2 + kmax + 1) * 8)}
+    del u2, host_u
+
+    fft = None
+    if not args.no_fft:
+        fft = bench_fft(fk, torch, dev, st_obj, args, hbm, peak_kind)
+    fk.fftk_plan_destroy(plan)
+
+    line = {
+        "metric": METRIC,
+        "value": round(value, 3),
+        "unit": "steps/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_step, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic: random-phase solenoidal field from the library's SplitMix64 normals, seed 0",
+        "config": {
+            "workload": "512^3 decaying turbulence, pseudo-spectral NS, RK2 + viscous integrating factor, "
+                        "2/3 dealiasing, nu=1e-3, dt=5e-4, E(k)~k^4 exp(-2(k/4)^2), E=0.5",
+            "n": n, "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+            "l2": "no flush: every field (539 MB) exceeds the 126 MB L2",
+        },
+        "roofline": {
+            "bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+            "frac": round(achieved / hbm, 4), "traffic": None, "peak_kind": peak_kind,
+            "bytes_per_launch": int(kb[dom]),
+        },
+        "step_roofline": {
+            "pruned_bytes": int(pruned), "unpruned_bytes": int(unpruned),
+            "frac_pruned": round(pruned / (ms_step * 1e-3) / 1e9 / hbm, 4),
+            "frac_unpruned": round(unpruned / (ms_step * 1e-3) / 1e9 / hbm, 4),
+            "peak_kind": peak_kind,
+        },
+        "kernels": kernels,
+        "gpu_launches": int(launches),
+        "e2e": e2e,
+        "clocks": clk,
+        "state_after": {"E": E, "eps": eps},
+    }
+    if fft is not None:
+        line["fft_pair_1024"] = fft
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    return line
+
+
+def bench_fft(fk, torch, dev, st_obj, args, hbm, peak_kind):
+    n = N_FFT
+    st = st_obj.cuda_stream
+    plan = fk.fftk_plan_create(n, n, n)
+    try:
+        with torch.cuda.stream(st_obj):
+            x = torch.empty((n, n, n), dtype=torch.float32, device=dev)
+            fk.fftk_fill_normal(x.data_ptr(), n**3, SEED, 0, st)
+            F = torch.empty((n, n, n // 2 + 1, 2), dtype=torch.float32, device=dev)
+            y = torch.empty_like(x)
+        for _ in range(max(3, args.warmup)):
+            fk.fftk_r2c(plan, x.data_ptr(), F.data_ptr(), 1, st)
+            fk.fftk_c2r(plan, F.data_ptr(), y.data_ptr(), 1, st)
+        torch.cuda.synchronize(dev)
+        kp = 20
+        fk.fftk_profile_enable(plan, True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st_obj)
+        for _ in range(kp):
+            fk.fftk_r2c(plan, x.data_ptr(), F.data_ptr(), 1, st)
+            fk.fftk_c2r(plan, F.data_ptr(), y.data_ptr(), 1, st)
+        e1.record(st_obj)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / kp
+        pb = fft_pass_bytes(n)
+        kern = {}
+        for k in range(fk.fftk_kernel_kinds()):
+            t, cnt = fk.fftk_profile_read(plan, k)
+            if cnt:
+                name = fk.fftk_kernel_name(k)
+                avg = t / cnt
+                kern[name] = {"launches": cnt, "ms_avg": round(avg, 5),
+                              "GBps": round(pb[name] / (avg * 1e-3) / 1e9, 1) if name in pb else None}
+        fk.fftk_profile_enable(plan, False)
+        rt = (torch.linalg.vector_norm((y - x).double()) / torch.linalg.vector_norm(x.double())).item()
+        pair = sum(pb.values())
+        dom = max(kern.items(), key=lambda kv: kv[1]["ms_avg"] * kv[1]["launches"])[0]
+        return {
+            "value": round(1e3 / ms, 3), "unit": "pairs/s", "ms_per_pair": round(ms, 4),
+            "config": "1024^3 FP32 real field, normal(0,1) seed 0, batch 1",
+            "pair_bytes": int(pair),
+            "frac_pair": round(pair / (ms * 1e-3) / 1e9 / hbm, 4),
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["GBps"], "peak": hbm,
+                         "unit": "GB/s", "frac": round(kern[dom]["GBps"] / hbm, 4), "traffic": None,
+                         "peak_kind": peak_kind},
+            "kernels": kern,
+            "round_trip_rel_l2": rt,
+            "nominal_gflops": round(2 * 5 * n**3 * 3 * 10 / (ms * 1e-3) / 1e9, 1),
+        }
+    finally:
+        fk.fftk_plan_destroy(plan)
+
+
+# ------------------------------------------------------ CPU oracle timing ---
+def _oracle_state(n):
+    import numpy as np
+
+    import oracle
+    import synth
+
+    u = oracle.ic_random(synth.normal_fields(SEED, 3, (n, n, n)), k0=K0, E0=E0)
+    return u.astype(np.complex64).astype(np.complex128)
+
+
+def cpu_baseline():
+    """One RK2-IF step of the 512^3 workload by the FP64 oracle on the host cores."""
+    import oracle
+
+    u = _oracle_state(N_NS)
+    t0 = time.perf_counter()
+    oracle.ns_step(u, NU, DT, 1)
+    t = time.perf_counter() - t0
+    return {"value": round(1.0 / t, 5), "unit": "steps/s", "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"one full RK2-IF step of the 512^3 workload (FP64 oracle, OpenMP over lines), {t:.1f} s"}
+
+
+def run_reference(args, world, rank):
+    """The oracle as the reference arm: each step is a bounded sample of the
+    512^3 step, one inverse + one forward 3D transform of a velocity component
+    (2 of the 18 transforms of an RK2 step); steps/s = 1 / (9 t_sample).
+    The pointwise work (products, projection, update) is not counted."""
+    import numpy as np
+
+    import oracle
+
+    u = _oracle_state(N_NS)
+    ux = np.ascontiguousarray(u[0])
+    n = N_NS
+    for _ in range(args.warmup):
+        oracle.rfft3(oracle.irfft3(ux, n))
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.rfft3(oracle.irfft3(ux, n))
+        ts.append(time.perf_counter() - t0)
+    t = sum(ts) / len(ts)
+    value = 1.0 / (9.0 * t)
+    sample = ("per step: one inverse + one forward 3D FP64 transform of a 512^3 velocity component "
+              "(2 of the 18 transforms of an RK2-IF step), scaled x9; pointwise work not counted")
+    return {
+        "metric": METRIC, "value": round(value, 6), "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(9.0 * t * 1e3, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (oracle's own initial field)",
+        "config": {"workload": "512^3 decaying turbulence, pseudo-spectral NS, RK2 + viscous integrating factor, "
+                               "2/3 dealiasing, nu=1e-3, dt=5e-4, E(k)~k^4 exp(-2(k/4)^2), E=0.5", "n": n},
+        "impl": "reference",
+        "cpu_baseline": {"value": round(value, 6), "unit": "steps/s", "cores": oracle.threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 6), "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fft", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args, world, rank)), flush=True)
+        return
+    line = run_ours(args, world, rank, local)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,180 @@
+/* fftk.h -- C ABI of the GB300 (sm_103a) FFTK/Tarang hot-path library.
+ *
+ * Chatterjee, Verma, Kumar, Samtaney, Hadri, Khurram, "Scaling of a Fast
+ * Fourier Transform and a Pseudo-spectral Fluid Solver up to 196608 cores"
+ * (arXiv:1805.07801).  This library implements, on one GPU, the paper's 3D
+ * real-to-complex / complex-to-real FFT (FFTK, Sec. 3) and the pseudo-spectral
+ * incompressible Navier-Stokes step built on it (Tarang, Sec. 2.2).
+ *
+ * Conventions
+ *   Transform (Sec. 2.1, Eq. (1) with the Fourier basis of Eq. (2a)):
+ *     inverse  f(x) = sum_k fhat(k) exp(+i k.x)                 (no factor)
+ *     forward  fhat(k) = (1/(nx ny nz)) sum_x f(x) exp(-i k.x)
+ *   on the 2 pi-periodic grid x = 2 pi (i/nx, j/ny, l/nz).
+ *   Real array:    float [batch][nx][ny][nz], z fastest (Sec. 3: z is local).
+ *   Complex array: float2 (re, im) [batch][nx][ny][nz/2+1]; the axes are not
+ *                  exchanged (the transpose-free layout of Appendix A).  Index
+ *                  a on x or y means k = a for a < n/2, a - n otherwise; on z,
+ *                  k = c.
+ *   Sizes: nx, ny are powers of two in [1, 4096]; nz a power of two in
+ *          [2, 4096] (ny = 1 gives the paper's 2D mode, Sec. 3).
+ *   Pointers: device pointers, 16-byte aligned.  Streams: a cudaStream_t
+ *          passed as void* (NULL = legacy default stream).  Calls are
+ *          asynchronous on that stream unless stated otherwise.
+ *   Ownership: the caller owns every data buffer and stream.  A plan owns its
+ *          twiddle tables and, unless fftk_set_workspace was called, its
+ *          workspace.  A plan must be used by one stream at a time.
+ *   Errors: no call aborts or exits.  Argument checks run before any CUDA
+ *          call.  Launch failures return FFTK_ERR_CUDA; faults inside a kernel
+ *          surface as FFTK_ERR_CUDA from a later synchronising call.
+ */
+#ifndef FFTK_H
+#define FFTK_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fftk_plan_s *fftk_plan; /* opaque; created and freed by the library */
+
+typedef enum {
+  FFTK_OK = 0,
+  FFTK_ERR_INVALID_ARG = 1,      /* NULL / misaligned / overlapping pointer, bad count */
+  FFTK_ERR_UNSUPPORTED_SIZE = 2, /* a dimension outside the supported set */
+  FFTK_ERR_NO_DEVICE = 3,        /* no CUDA device visible */
+  FFTK_ERR_OOM = 4,              /* device allocation failed */
+  FFTK_ERR_CUDA = 5,             /* a CUDA runtime call or launch failed */
+  FFTK_ERR_NONFINITE = 6,        /* a solver diagnostic was NaN or Inf */
+  FFTK_ERR_TIMEOUT = 7           /* a bounded device-side wait expired */
+} fftk_status;
+
+typedef enum {
+  FFTK_R32 = 0,         /* FP32 data, FP32 arithmetic, FP64-built FP32 twiddles */
+  FFTK_R32_SPLIT16 = 1  /* FP32 data; radix-16 stages on tensor cores, split FP16 hi/lo operands */
+} fftk_dtype;
+
+/* Human-readable name of a status code (static storage). */
+const char *fftk_status_string(fftk_status s);
+
+/* Create a plan for nx x ny x nz transforms (paper Sec. 3).  Builds the
+ * twiddle table exp(-2 pi i m / LT), LT = max(nx, ny, nz), in FP64 on the host
+ * and rounds it once to FP32.  Binds the plan to the current CUDA device.
+ * Errors: INVALID_ARG (out NULL, bad dtype), UNSUPPORTED_SIZE, NO_DEVICE, OOM,
+ * CUDA.  On error *out is set to NULL. */
+fftk_status fftk_plan_create(int nx, int ny, int nz, fftk_dtype dtype, fftk_plan *out);
+
+/* Free a plan and everything it owns.  Synchronises the device.  NULL is
+ * INVALID_ARG. */
+fftk_status fftk_plan_destroy(fftk_plan p);
+
+/* Bytes of device workspace fftk_c2r needs for `batch` transforms
+ * (one complex array: batch * nx * ny * (nz/2+1) * 8).  0 on bad arguments. */
+size_t fftk_workspace_bytes(fftk_plan p, int batch);
+
+/* Hand the plan a caller-owned device workspace (NULL, 0 = go back to a
+ * plan-owned one).  The caller keeps it alive while the plan uses it. */
+fftk_status fftk_set_workspace(fftk_plan p, void *dev_ptr, size_t bytes);
+
+/* Forward 3D real-to-complex transform (paper Sec. 3, steps 1-5): z r2c, then
+ * y c2c, then x c2c, with the 1/(nx ny nz) factor of Eq. (1)'s inverse.
+ * in:  float [batch][nx][ny][nz]; out: float2 [batch][nx][ny][nz/2+1].
+ * Out-of-place: overlapping in/out is INVALID_ARG.  `in` is not modified. */
+fftk_status fftk_r2c(fftk_plan p, const float *in, void *out, int batch, void *cuda_stream);
+
+/* Inverse 3D complex-to-real transform ("the reverse of the above", Sec. 3):
+ * x c2c, y c2c, then z c2r, no factor.  in: float2 [batch][nx][ny][nz/2+1];
+ * out: float [batch][nx][ny][nz].  `in` is not modified (the y/x passes run in
+ * the plan's workspace).  For each z line the imaginary parts of its k_z = 0
+ * and k_z = nz/2 coefficients are ignored, which is the exact inverse for
+ * Hermitian-consistent spectra (those produced by fftk_r2c).  Out-of-place. */
+fftk_status fftk_c2r(fftk_plan p, const void *in, float *out, int batch, void *cuda_stream);
+
+/* ---------------------------------------------------------------- Tarang --
+ * Pseudo-spectral incompressible Navier-Stokes on a 2 pi-periodic cubic grid
+ * (plan with nx = ny = nz = n, n >= 8), paper Sec. 2.2, Eqs. (7)-(8).
+ * Velocity: float2 uhat[3][n][n][n/2+1] (component outermost), the forward
+ * transform of the real velocity.  Modes outside the 2/3-rule set
+ * (3|k_x| < n and 3|k_y| < n and 3|k_z| < n) must be zero on entry and stay
+ * zero; the solver never reads them. */
+typedef struct {
+  double nu;        /* kinematic viscosity */
+  double dt;        /* time step (tarang_ns_step only) */
+  double force_eps; /* constant injected power; 0 disables forcing */
+  int force_k2min;  /* forced modes: force_k2min <= |k|^2 <= force_k2max */
+  int force_k2max;
+} tarang_params;
+
+/* Nonlinear right-hand side without the viscous term:
+ *   nhat = P[ F(u x omega) ] on the 2/3 set, 0 elsewhere, + forcing,
+ * with omega = curl u, P the projection k_j uhat_j = 0 of Eq. (8), and the
+ * product formed in real space (Orszag's pseudo-spectral method, Sec. 2.2).
+ * Forcing (when force_eps > 0): nhat += force_eps uhat / (2 E_f) on the forced
+ * modes, E_f = 1/2 sum w |uhat|^2 over them (FP64 reduction), so exactly
+ * force_eps is injected.  uhat, nhat: float2 [3][n][n][n/2+1], distinct. */
+fftk_status tarang_ns_rhs(fftk_plan p, const void *uhat, void *nhat, const tarang_params *prm,
+                          void *cuda_stream);
+
+/* nsteps steps of RK2 (Heun) with the viscous integrating factor
+ * E = exp(-nu |k|^2 dt):
+ *   u1 = E (u + dt N(u)),   u <- 1/2 E u + 1/2 (u1 + dt N(u1)).
+ * uhat is updated in place.  diag_host: NULL, or room for 2 + kmax + 1
+ * doubles, kmax = nint(sqrt(3) n / 2) + 1 (see tarang_diag_kmax); when given,
+ * the call synchronises and writes E, eps and E(K) of the final state, and
+ * returns FFTK_ERR_NONFINITE if E is not finite. */
+fftk_status tarang_ns_step(fftk_plan p, void *uhat, const tarang_params *prm, int nsteps,
+                           double *diag_host, void *cuda_stream);
+
+/* Largest shell index reported by the diagnostics for this plan. */
+int tarang_diag_kmax(fftk_plan p);
+
+/* Diagnostics of a velocity state, reduced in FP64 in a fixed order
+ * (bitwise reproducible):  E = 1/2 sum w |u|^2,  eps = nu sum w |k|^2 |u|^2,
+ * E(K) = 1/2 sum_{nint|k| = K} w |u|^2, w = 1 on k_z = 0 and k_z = n/2,
+ * 2 elsewhere.  Writes 2 + kmax + 1 doubles to diag_host; synchronises. */
+fftk_status tarang_diag(fftk_plan p, const void *uhat, double nu, double *diag_host,
+                        void *cuda_stream);
+
+/* Random-phase solenoidal initial velocity (used by the decaying- and
+ * forced-turbulence workloads): the forward transform of three real fields
+ * `normals` (device float [3][n][n][n], e.g. from fftk_fill_normal), 2/3
+ * truncation, projection (Eq. (8)), the k_z = 0 plane made exactly Hermitian,
+ * each shell K = nint|k| >= 1 rescaled so that its energy is proportional to
+ * K^4 exp(-2 (K/k0)^2), uhat(0) = 0, and a final factor making the total
+ * energy E0.  Shell energies are reduced in FP64 and the scale factors are
+ * computed in FP64 on the host.  Synchronises the stream.
+ * uhat: float2 [3][n][n][n/2+1]. */
+fftk_status tarang_ic_random(fftk_plan p, const float *normals, void *uhat, double k0, double E0,
+                             void *cuda_stream);
+
+/* Counter-based SplitMix64 generator (Steele, Lea, Flood 2014): element i of
+ * field f for seed s uses the outputs at counters c = s 2^40 + f 2^36 + 2i and
+ * c + 1 of the stream started at state 0, x_c = mix64((c + 1) * 0x9E3779B97F4A7C15).
+ * fftk_fill_normal: Box-Muller, u1 = ((x1 >> 11) + 1) 2^-53,
+ *   u2 = (x2 >> 11) 2^-53, value = sqrt(-2 ln u1) cos(2 pi u2) in FP64, stored
+ *   as float.
+ * fftk_fill_uniform: value = 2 (x_i >> 40) 2^-24 - 1 with x_i at counter
+ *   s 2^40 + f 2^36 + i (exact in FP32, uniform on [-1, 1)).
+ * dev: device float[count]; seed < 2^24, field < 16, 2 count <= 2^36. */
+fftk_status fftk_fill_normal(float *dev, long long count, int seed, int field, void *cuda_stream);
+fftk_status fftk_fill_uniform(float *dev, long long count, int seed, int field, void *cuda_stream);
+
+/* ------------------------------------------------------- instrumentation --
+ * Kernel launches made by this plan since its creation. */
+long long fftk_launch_count(fftk_plan p);
+
+/* Turn per-launch CUDA-event timing on (and clear old records) or off. */
+fftk_status fftk_profile_enable(fftk_plan p, int on);
+
+/* Sum of device time (ms) and number of launches recorded for kernel kind
+ * `kind` (0 .. fftk_kernel_kinds()-1) since profiling was enabled.
+ * Synchronises on the recorded events. */
+fftk_status fftk_profile_read(fftk_plan p, int kind, double *total_ms, long long *launches);
+int fftk_kernel_kinds(void);
+const char *fftk_kernel_name(int kind);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FFTK_H */

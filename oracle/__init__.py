@@ -42,6 +42,8 @@ def lib():
             c = ctypes
             dp = c.POINTER(c.c_double)
             vp = c.c_void_p
+            L.oracle_threads.argtypes = []
+            L.oracle_threads.restype = c.c_int
             L.oracle_fft1d.argtypes = [vp, vp, c.c_long, c.c_int]
             L.oracle_dft1d.argtypes = [vp, vp, c.c_long, c.c_int]
             L.oracle_rfft3.argtypes = [vp, vp, c.c_int, c.c_int, c.c_int]
@@ -82,6 +84,10 @@ def _ptr(a: np.ndarray):
 def _check(rc: int, what: str):
     if rc != 0:
         raise RuntimeError(f"oracle {what} failed with code {rc}")
+
+
+def threads() -> int:
+    return int(lib().oracle_threads())
 
 
 def fft1d(x, sign: int = -1) -> np.ndarray:

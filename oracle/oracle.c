@@ -17,12 +17,23 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define TWO_PI 6.283185307179586476925286766559005768
 
 typedef ocplx cplx;
 
 static int is_pow2(long n) { return n >= 1 && (n & (n - 1)) == 0; }
+
+int oracle_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
 
 /* tw[m] = exp(sign * 2 pi i m / n) for m < max(n/2, 1), FP64 host libm. */
 static cplx *make_twiddles(long n, int sign) {

@@ -23,6 +23,9 @@ extern "C" {
 
 typedef double _Complex ocplx;
 
+/* OpenMP threads the oracle uses for independent lines (1 without OpenMP). */
+int oracle_threads(void);
+
 /* 1D transforms, out[k] = sum_j in[j] exp(sign 2 pi i j k / n). */
 int oracle_fft1d(const ocplx *in, ocplx *out, long n, int sign);   /* recursive radix-2, n = 2^m */
 int oracle_dft1d(const ocplx *in, ocplx *out, long n, int sign);   /* O(n^2) definition, any n */

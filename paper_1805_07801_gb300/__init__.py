@@ -1,0 +1,205 @@
+"""Python binding of libfftk (GB300 FFTK/Tarang hot path).
+
+Argument marshalling only: every function here forwards to the C ABI declared
+in include/fftk.h (same names); all arithmetic runs in the library's CUDA
+kernels.  Device buffers are passed as integer addresses (e.g. a torch CUDA
+tensor's data_ptr()) and streams as integer cudaStream_t handles
+(torch.cuda.current_stream().cuda_stream).  The library must be built
+(build.build()); there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfftk.so")
+
+FFTK_OK = 0
+FFTK_ERR_INVALID_ARG = 1
+FFTK_ERR_UNSUPPORTED_SIZE = 2
+FFTK_ERR_NO_DEVICE = 3
+FFTK_ERR_OOM = 4
+FFTK_ERR_CUDA = 5
+FFTK_ERR_NONFINITE = 6
+FFTK_ERR_TIMEOUT = 7
+
+FFTK_R32 = 0
+FFTK_R32_SPLIT16 = 1
+
+
+class FFTKError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {fftk_status_string(status)} ({status})")
+
+
+class tarang_params(ctypes.Structure):
+    _fields_ = [
+        ("nu", ctypes.c_double),
+        ("dt", ctypes.c_double),
+        ("force_eps", ctypes.c_double),
+        ("force_k2min", ctypes.c_int),
+        ("force_k2max", ctypes.c_int),
+    ]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libfftk.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run paper_1805_07801_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        c = ctypes
+        vp, i, d, ll = c.c_void_p, c.c_int, c.c_double, c.c_longlong
+        sig = {
+            "fftk_status_string": ([i], c.c_char_p),
+            "fftk_plan_create": ([i, i, i, i, c.POINTER(vp)], i),
+            "fftk_plan_destroy": ([vp], i),
+            "fftk_workspace_bytes": ([vp, i], c.c_size_t),
+            "fftk_set_workspace": ([vp, vp, c.c_size_t], i),
+            "fftk_r2c": ([vp, vp, vp, i, vp], i),
+            "fftk_c2r": ([vp, vp, vp, i, vp], i),
+            "tarang_ns_rhs": ([vp, vp, vp, c.POINTER(tarang_params), vp], i),
+            "tarang_ns_step": ([vp, vp, c.POINTER(tarang_params), i, vp, vp], i),
+            "tarang_diag_kmax": ([vp], i),
+            "tarang_diag": ([vp, vp, d, vp, vp], i),
+            "tarang_ic_random": ([vp, vp, vp, d, d, vp], i),
+            "fftk_fill_normal": ([vp, ll, i, i, vp], i),
+            "fftk_fill_uniform": ([vp, ll, i, i, vp], i),
+            "fftk_launch_count": ([vp], ll),
+            "fftk_profile_enable": ([vp, i], i),
+            "fftk_profile_read": ([vp, i, c.POINTER(d), c.POINTER(ll)], i),
+            "fftk_kernel_kinds": ([], i),
+            "fftk_kernel_name": ([i], c.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def _vp(x):
+    return ctypes.c_void_p(int(x) if x is not None else 0)
+
+
+def _check(st: int, where: str):
+    if st != FFTK_OK:
+        raise FFTKError(st, where)
+
+
+def fftk_status_string(s: int) -> str:
+    return lib().fftk_status_string(int(s)).decode()
+
+
+def fftk_plan_create(nx: int, ny: int, nz: int, dtype: int = FFTK_R32) -> int:
+    out = ctypes.c_void_p()
+    _check(lib().fftk_plan_create(nx, ny, nz, dtype, ctypes.byref(out)), "fftk_plan_create")
+    return out.value
+
+
+def fftk_plan_destroy(plan: int) -> None:
+    _check(lib().fftk_plan_destroy(_vp(plan)), "fftk_plan_destroy")
+
+
+def fftk_workspace_bytes(plan: int, batch: int) -> int:
+    return int(lib().fftk_workspace_bytes(_vp(plan), batch))
+
+
+def fftk_set_workspace(plan: int, dev_ptr, nbytes: int) -> None:
+    _check(lib().fftk_set_workspace(_vp(plan), _vp(dev_ptr), nbytes), "fftk_set_workspace")
+
+
+def fftk_r2c(plan: int, in_ptr, out_ptr, batch: int = 1, stream=0) -> None:
+    _check(lib().fftk_r2c(_vp(plan), _vp(in_ptr), _vp(out_ptr), batch, _vp(stream)), "fftk_r2c")
+
+
+def fftk_c2r(plan: int, in_ptr, out_ptr, batch: int = 1, stream=0) -> None:
+    _check(lib().fftk_c2r(_vp(plan), _vp(in_ptr), _vp(out_ptr), batch, _vp(stream)), "fftk_c2r")
+
+
+def make_params(nu: float, dt: float = 0.0, force_eps: float = 0.0, force_k2=(1, 4)) -> tarang_params:
+    return tarang_params(float(nu), float(dt), float(force_eps), int(force_k2[0]), int(force_k2[1]))
+
+
+def tarang_ns_rhs(plan: int, uhat_ptr, nhat_ptr, params: tarang_params, stream=0) -> None:
+    _check(lib().tarang_ns_rhs(_vp(plan), _vp(uhat_ptr), _vp(nhat_ptr), ctypes.byref(params), _vp(stream)),
+           "tarang_ns_rhs")
+
+
+def tarang_diag_kmax(plan: int) -> int:
+    return int(lib().tarang_diag_kmax(_vp(plan)))
+
+
+def tarang_ns_step(plan: int, uhat_ptr, params: tarang_params, nsteps: int = 1, diag: bool = False, stream=0):
+    """Advance nsteps; with diag=True returns (E, eps, E(K) list)."""
+    buf = None
+    if diag:
+        buf = (ctypes.c_double * (2 + tarang_diag_kmax(plan) + 1))()
+    _check(lib().tarang_ns_step(_vp(plan), _vp(uhat_ptr), ctypes.byref(params), nsteps,
+                                ctypes.cast(buf, ctypes.c_void_p) if buf is not None else None, _vp(stream)),
+           "tarang_ns_step")
+    if buf is None:
+        return None
+    vals = list(buf)
+    return vals[0], vals[1], vals[2:]
+
+
+def tarang_diag(plan: int, uhat_ptr, nu: float, stream=0):
+    """(E, eps, E(K) list) of a velocity state; synchronises."""
+    buf = (ctypes.c_double * (2 + tarang_diag_kmax(plan) + 1))()
+    _check(lib().tarang_diag(_vp(plan), _vp(uhat_ptr), float(nu), ctypes.cast(buf, ctypes.c_void_p), _vp(stream)),
+           "tarang_diag")
+    vals = list(buf)
+    return vals[0], vals[1], vals[2:]
+
+
+def tarang_ic_random(plan: int, normals_ptr, uhat_ptr, k0: float = 4.0, E0: float = 0.5, stream=0) -> None:
+    _check(lib().tarang_ic_random(_vp(plan), _vp(normals_ptr), _vp(uhat_ptr), float(k0), float(E0), _vp(stream)),
+           "tarang_ic_random")
+
+
+def fftk_fill_normal(dev_ptr, count: int, seed: int, field: int, stream=0) -> None:
+    _check(lib().fftk_fill_normal(_vp(dev_ptr), int(count), int(seed), int(field), _vp(stream)), "fftk_fill_normal")
+
+
+def fftk_fill_uniform(dev_ptr, count: int, seed: int, field: int, stream=0) -> None:
+    _check(lib().fftk_fill_uniform(_vp(dev_ptr), int(count), int(seed), int(field), _vp(stream)),
+           "fftk_fill_uniform")
+
+
+def fftk_launch_count(plan: int) -> int:
+    return int(lib().fftk_launch_count(_vp(plan)))
+
+
+def fftk_profile_enable(plan: int, on: bool = True) -> None:
+    _check(lib().fftk_profile_enable(_vp(plan), int(bool(on))), "fftk_profile_enable")
+
+
+def fftk_profile_read(plan: int, kind: int):
+    ms = ctypes.c_double()
+    n = ctypes.c_longlong()
+    _check(lib().fftk_profile_read(_vp(plan), kind, ctypes.byref(ms), ctypes.byref(n)), "fftk_profile_read")
+    return ms.value, n.value
+
+
+def fftk_kernel_kinds() -> int:
+    return int(lib().fftk_kernel_kinds())
+
+
+def fftk_kernel_name(kind: int) -> str:
+    r = lib().fftk_kernel_name(kind)
+    return r.decode() if r else ""
+
+
+def kernel_index(name: str) -> int:
+    for k in range(fftk_kernel_kinds()):
+        if fftk_kernel_name(k) == name:
+            return k
+    raise KeyError(name)

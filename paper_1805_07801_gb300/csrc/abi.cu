@@ -1,0 +1,280 @@
+// C ABI entry points for the transforms, the planner and instrumentation.
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+
+namespace fftk {
+
+const char* const kKernelNames[KK_COUNT] = {
+    "z_r2c", "y_fwd", "x_fwd", "x_inv", "y_inv", "z_c2r",
+    "ns_invx_curl", "ns_invy", "ns_z_product", "ns_fwdy", "ns_fwdx_update",
+    "ns_reduce", "aux"};
+
+bool is_pow2(long long v) { return v >= 1 && (v & (v - 1)) == 0; }
+int ilog2(long long v) {
+  int l = 0;
+  while ((1LL << l) < v) ++l;
+  return l;
+}
+
+cudaEvent_t Profiler::take() {
+  if (next < pool.size()) return pool[next++];
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  pool.push_back(e);
+  ++next;
+  return e;
+}
+
+void Profiler::clear() {
+  recs.clear();
+  next = 0;
+}
+
+Profiler::~Profiler() {
+  for (cudaEvent_t e : pool) cudaEventDestroy(e);
+}
+
+LaunchScope::LaunchScope(fftk_plan p_, int kind_, cudaStream_t st_) : p(p_), kind(kind_), st(st_) {
+  p->launches.fetch_add(1, std::memory_order_relaxed);
+  if (p->prof.on) {
+    cudaEvent_t a = p->prof.take();
+    b = p->prof.take();
+    if (a && b) {
+      cudaEventRecord(a, st);
+      p->prof.recs.push_back({kind, a, b});
+    } else {
+      b = nullptr;
+    }
+  }
+}
+
+LaunchScope::~LaunchScope() {
+  if (b) cudaEventRecord(b, st);
+}
+
+static bool misaligned(const void* ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 15u) != 0; }
+
+static bool overlap(const void* a, size_t na, const void* b, size_t nb) {
+  const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+  return x < y + nb && y < x + na;
+}
+
+fftk_status from_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return FFTK_OK;
+  if (e == cudaErrorMemoryAllocation) return FFTK_ERR_OOM;
+  if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver) return FFTK_ERR_NO_DEVICE;
+  return FFTK_ERR_CUDA;
+}
+
+// Plan-owned workspace of at least `bytes`.
+static fftk_status ensure_ws(fftk_plan p, size_t bytes, void** out) {
+  std::lock_guard<std::mutex> g(p->mu);
+  if (p->ws && p->ws_bytes >= bytes) {
+    *out = p->ws;
+    return FFTK_OK;
+  }
+  if (p->ws && !p->ws_owned) return FFTK_ERR_INVALID_ARG;  // caller's buffer is too small
+  if (p->ws) cudaFree(p->ws);
+  p->ws = nullptr;
+  p->ws_bytes = 0;
+  void* w = nullptr;
+  cudaError_t e = cudaMalloc(&w, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return FFTK_ERR_OOM;
+  }
+  p->ws = w;
+  p->ws_bytes = bytes;
+  p->ws_owned = true;
+  *out = w;
+  return FFTK_OK;
+}
+
+}  // namespace fftk
+
+using namespace fftk;
+
+extern "C" const char* fftk_status_string(fftk_status s) {
+  switch (s) {
+    case FFTK_OK: return "FFTK_OK";
+    case FFTK_ERR_INVALID_ARG: return "FFTK_ERR_INVALID_ARG";
+    case FFTK_ERR_UNSUPPORTED_SIZE: return "FFTK_ERR_UNSUPPORTED_SIZE";
+    case FFTK_ERR_NO_DEVICE: return "FFTK_ERR_NO_DEVICE";
+    case FFTK_ERR_OOM: return "FFTK_ERR_OOM";
+    case FFTK_ERR_CUDA: return "FFTK_ERR_CUDA";
+    case FFTK_ERR_NONFINITE: return "FFTK_ERR_NONFINITE";
+    case FFTK_ERR_TIMEOUT: return "FFTK_ERR_TIMEOUT";
+  }
+  return "FFTK_ERR_UNKNOWN";
+}
+
+extern "C" fftk_status fftk_plan_create(int nx, int ny, int nz, fftk_dtype dtype, fftk_plan* out) {
+  if (!out) return FFTK_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (dtype != FFTK_R32) return FFTK_ERR_INVALID_ARG;
+  if (!is_pow2(nx) || !is_pow2(ny) || !is_pow2(nz) || nx > 4096 || ny > 4096 || nz > 4096 ||
+      nz < 2)
+    return FFTK_ERR_UNSUPPORTED_SIZE;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || ndev <= 0) {
+    cudaGetLastError();
+    return FFTK_ERR_NO_DEVICE;
+  }
+  fftk_plan p = new (std::nothrow) fftk_plan_s;
+  if (!p) return FFTK_ERR_OOM;
+  p->nx = nx;
+  p->ny = ny;
+  p->nz = nz;
+  p->hz = nz / 2 + 1;
+  p->dtype = dtype;
+  cudaGetDevice(&p->device);
+  int lt = nx;
+  if (ny > lt) lt = ny;
+  if (nz > lt) lt = nz;
+  p->twlog = ilog2(lt);
+  // Twiddles in FP64 (host libm), rounded once to FP32.
+  std::vector<float2> h((size_t)lt);
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int m = 0; m < lt; ++m) {
+    const double ang = two_pi * (double)m / (double)lt;
+    h[(size_t)m] = make_float2((float)std::cos(ang), (float)(-std::sin(ang)));
+  }
+  e = cudaMalloc(&p->d_tw, sizeof(float2) * (size_t)lt);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(p->d_tw, h.data(), sizeof(float2) * (size_t)lt, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    fftk_status s = from_cuda(e);
+    cudaGetLastError();
+    if (p->d_tw) cudaFree(p->d_tw);
+    delete p;
+    return s;
+  }
+  *out = p;
+  return FFTK_OK;
+}
+
+void ns_free(fftk_plan p);  // ns.cu
+
+extern "C" fftk_status fftk_plan_destroy(fftk_plan p) {
+  if (!p) return FFTK_ERR_INVALID_ARG;
+  cudaDeviceSynchronize();
+  ns_free(p);
+  if (p->d_tw) cudaFree(p->d_tw);
+  if (p->ws && p->ws_owned) cudaFree(p->ws);
+  delete p;
+  return FFTK_OK;
+}
+
+extern "C" size_t fftk_workspace_bytes(fftk_plan p, int batch) {
+  if (!p || batch < 1) return 0;
+  return (size_t)batch * (size_t)p->nx * (size_t)p->ny * (size_t)p->hz * sizeof(float2);
+}
+
+extern "C" fftk_status fftk_set_workspace(fftk_plan p, void* dev_ptr, size_t bytes) {
+  if (!p) return FFTK_ERR_INVALID_ARG;
+  if ((dev_ptr == nullptr) != (bytes == 0)) return FFTK_ERR_INVALID_ARG;
+  if (dev_ptr && misaligned(dev_ptr)) return FFTK_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> g(p->mu);
+  if (p->ws && p->ws_owned) cudaFree(p->ws);
+  p->ws = dev_ptr;
+  p->ws_bytes = bytes;
+  p->ws_owned = false;
+  return FFTK_OK;
+}
+
+extern "C" fftk_status fftk_r2c(fftk_plan p, const float* in, void* out, int batch,
+                                void* cuda_stream) {
+  if (!p || !in || !out || batch < 1) return FFTK_ERR_INVALID_ARG;
+  if (misaligned(in) || misaligned(out)) return FFTK_ERR_INVALID_ARG;
+  const long long B = batch;
+  const size_t in_bytes = (size_t)B * p->nx * p->ny * p->nz * sizeof(float);
+  const size_t out_bytes = fftk_workspace_bytes(p, batch);
+  if (overlap(in, in_bytes, out, out_bytes)) return FFTK_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  float2* o = static_cast<float2*>(out);
+  const float scale = (float)(1.0 / ((double)p->nx * (double)p->ny * (double)p->nz));
+  const bool do_y = p->ny > 1, do_x = p->nx > 1;
+  cudaError_t e = launch_z_r2c(p, in, o, B * p->nx * p->ny, (do_x || do_y) ? 1.f : scale, st);
+  if (e == cudaSuccess && do_y)
+    e = launch_cpass(p, p->ny, -1, o, o, B * p->nx, p->hz, do_x ? 1.f : scale, KK_Y_FWD, st);
+  if (e == cudaSuccess && do_x)
+    e = launch_cpass(p, p->nx, -1, o, o, B, (long long)p->ny * p->hz, scale, KK_X_FWD, st);
+  return from_cuda(e);
+}
+
+extern "C" fftk_status fftk_c2r(fftk_plan p, const void* in, float* out, int batch,
+                                void* cuda_stream) {
+  if (!p || !in || !out || batch < 1) return FFTK_ERR_INVALID_ARG;
+  if (misaligned(in) || misaligned(out)) return FFTK_ERR_INVALID_ARG;
+  const long long B = batch;
+  const size_t in_bytes = fftk_workspace_bytes(p, batch);
+  const size_t out_bytes = (size_t)B * p->nx * p->ny * p->nz * sizeof(float);
+  if (overlap(in, in_bytes, out, out_bytes)) return FFTK_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  const float2* src = static_cast<const float2*>(in);
+  const bool do_x = p->nx > 1, do_y = p->ny > 1;
+  cudaError_t e = cudaSuccess;
+  if (do_x || do_y) {
+    void* wv = nullptr;
+    fftk_status s = ensure_ws(p, in_bytes, &wv);
+    if (s != FFTK_OK) return s;
+    if (overlap(wv, in_bytes, in, in_bytes) || overlap(wv, in_bytes, out, out_bytes))
+      return FFTK_ERR_INVALID_ARG;
+    float2* w = static_cast<float2*>(wv);
+    if (do_x) {
+      e = launch_cpass(p, p->nx, +1, src, w, B, (long long)p->ny * p->hz, 1.f, KK_X_INV, st);
+      src = w;
+    }
+    if (e == cudaSuccess && do_y) {
+      e = launch_cpass(p, p->ny, +1, src, w, B * p->nx, p->hz, 1.f, KK_Y_INV, st);
+      src = w;
+    }
+  }
+  if (e == cudaSuccess) e = launch_z_c2r(p, src, out, B * p->nx * p->ny, st);
+  return from_cuda(e);
+}
+
+extern "C" long long fftk_launch_count(fftk_plan p) {
+  return p ? p->launches.load(std::memory_order_relaxed) : -1;
+}
+
+extern "C" fftk_status fftk_profile_enable(fftk_plan p, int on) {
+  if (!p) return FFTK_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> g(p->mu);
+  p->prof.clear();
+  p->prof.on = on != 0;
+  return FFTK_OK;
+}
+
+extern "C" fftk_status fftk_profile_read(fftk_plan p, int kind, double* total_ms,
+                                         long long* launches) {
+  if (!p || kind < 0 || kind >= KK_COUNT || !total_ms || !launches) return FFTK_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> g(p->mu);
+  double t = 0.0;
+  long long n = 0;
+  for (const auto& r : p->prof.recs) {
+    if (r.kind != kind) continue;
+    cudaError_t e = cudaEventSynchronize(r.b);
+    if (e != cudaSuccess) return from_cuda(e);
+    float ms = 0.f;
+    e = cudaEventElapsedTime(&ms, r.a, r.b);
+    if (e != cudaSuccess) return from_cuda(e);
+    t += ms;
+    ++n;
+  }
+  *total_ms = t;
+  *launches = n;
+  return FFTK_OK;
+}
+
+extern "C" int fftk_kernel_kinds(void) { return KK_COUNT; }
+
+extern "C" const char* fftk_kernel_name(int kind) {
+  return (kind >= 0 && kind < KK_COUNT) ? kKernelNames[kind] : nullptr;
+}

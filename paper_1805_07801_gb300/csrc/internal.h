@@ -1,0 +1,98 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <mutex>
+#include <vector>
+
+#include "../../include/fftk.h"
+
+namespace fftk {
+
+// Kernel kinds, for launch counting and event-based profiling.
+enum KernelKind : int {
+  KK_Z_R2C = 0,
+  KK_Y_FWD,
+  KK_X_FWD,
+  KK_X_INV,
+  KK_Y_INV,
+  KK_Z_C2R,
+  KK_NS_INVX,
+  KK_NS_INVY,
+  KK_NS_Z,
+  KK_NS_FWDY,
+  KK_NS_FWDX,
+  KK_NS_REDUCE,
+  KK_AUX,
+  KK_COUNT
+};
+extern const char* const kKernelNames[KK_COUNT];
+
+struct Profiler {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  struct Rec {
+    int kind;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> recs;
+  size_t next = 0;
+  cudaEvent_t take();
+  void clear();
+  ~Profiler();
+};
+
+struct NSWork;  // solver workspace, ns.cu
+
+}  // namespace fftk
+
+struct fftk_plan_s {
+  int nx, ny, nz, hz;  // hz = nz/2 + 1
+  fftk_dtype dtype;
+  int device;
+  int twlog;                 // LT = 2^twlog = max(nx, ny, nz)
+  float2* d_tw = nullptr;    // exp(-2 pi i m / LT), m < LT
+  // c2r workspace (one complex field per batch element)
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  bool ws_owned = false;
+  // solver state
+  fftk::NSWork* ns = nullptr;
+  // bookkeeping
+  std::atomic<long long> launches{0};
+  fftk::Profiler prof;
+  std::mutex mu;
+};
+
+namespace fftk {
+
+// Launch bracketing: counts the launch and records profiling events.
+struct LaunchScope {
+  fftk_plan p;
+  int kind;
+  cudaStream_t st;
+  cudaEvent_t b = nullptr;
+  LaunchScope(fftk_plan p_, int kind_, cudaStream_t st_);
+  ~LaunchScope();
+};
+
+// ---------------------------------------------------------- FFT passes -----
+// z pass, real -> half complex, lines of nz reals -> nz/2+1 complex (scale applied).
+cudaError_t launch_z_r2c(fftk_plan p, const float* in, float2* out, long long nlines, float scale,
+                         cudaStream_t st);
+// z pass, half complex -> real (unnormalised); Im of the k=0 and k=nz/2 terms ignored.
+cudaError_t launch_z_c2r(fftk_plan p, const float2* in, float* out, long long nlines,
+                         cudaStream_t st);
+// strided c2c pass: array [P][L][Q], transform along L (element stride Q),
+// in may equal out.  sign = -1 forward, +1 inverse; output multiplied by scale.
+cudaError_t launch_cpass(fftk_plan p, int L, int sign, const float2* in, float2* out, long long P,
+                         long long Q, float scale, int kind, cudaStream_t st);
+
+bool is_pow2(long long v);
+int ilog2(long long v);
+
+}  // namespace fftk

@@ -1,0 +1,881 @@
+// Pseudo-spectral incompressible Navier-Stokes (paper Sec. 2.2, Eqs. (7)-(8))
+// in rotational form, fused into the FFT passes of Sec. 3.
+//
+// One evaluation of the nonlinear term is five kernels:
+//   1. ns_invx_curl : uhat (3) -> inverse x pass of u and omega = i k x u (6)
+//   2. ns_invy      : inverse y pass of the 6 fields
+//   3. ns_z_product : per z line: c2r of the 6 fields, n = u x omega in
+//                     registers, r2c of the 3 products (real fields never
+//                     touch global memory)
+//   4. ns_fwdy      : forward y pass of the 3 fields
+//   5. ns_fwdx      : forward x pass + 1/N^3 + 2/3 dealias + projection
+//                     + forcing + the RK2 integrating-factor update
+//
+// Dealiasing (2/3 rule, "filling up only 2/3 of the array in each direction")
+// is exploited throughout: modes with 3|k| >= n on any axis are zero in the
+// state, so every pass reads only the rows and columns that can be nonzero
+// and writes only those a later pass reads.  The arrays keep the full
+// [n][n][n/2+1] layout; the untouched parts are never read.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "fft_engine.cuh"
+#include "internal.h"
+
+namespace fftk {
+
+fftk_status from_cuda(cudaError_t e);
+
+struct NSGeom {
+  int n;         // grid size
+  int h1;        // n/2 + 1
+  int kd;        // largest kept |k| = (n-1)/3
+  int kc;        // kept k_z count = kd + 1
+  int nk;        // kept count on x and y = 2 kd + 1
+  long long M;   // n * n * h1 (complex elements per field)
+};
+
+__device__ __forceinline__ bool kept_xy(int a, int n, int kd) { return a <= kd || a >= n - kd; }
+// wavenumber of index a on the x or y axis
+__device__ __forceinline__ int kwav(int a, int n) { return 2 * a < n ? a : a - n; }
+// index of the d-th kept x/y mode (d in [0, 2kd]): 0..kd, then n-kd..n-1
+__device__ __forceinline__ int dense_to_a(int d, int n, int kd) {
+  return d <= kd ? d : n - (2 * kd + 1 - d);
+}
+__device__ __forceinline__ float2 mul_i(float2 a, float k) {  // a * (i k)
+  return make_float2(-k * a.y, k * a.x);
+}
+
+// ------------------------------------------------------------ x/y config ---
+template <int N>
+struct NXCfg {
+  static constexpr int G = N < 8 ? N : 8;
+  static constexpr int S = N / G;
+  static constexpr int T = S >= 32 ? (S == 32 ? 16 : (S == 64 ? 8 : 4)) : 16;
+  static constexpr int THREADS = T * S;
+  static constexpr size_t SMEM = sizeof(float2) * (size_t)N * T;
+};
+
+// 1. inverse x pass with the curl.  Columns: kept (k_y, k_z); rows: k_x.
+//    U_c = F^-1_x(u_c), D_c = F^-1_x(i k_x u_c), then
+//    omega_x = i (k_y U_z - k_z U_y), omega_y = i k_z U_x - D_z,
+//    omega_z = D_y - i k_y U_x   (five transforms instead of six).
+//    Output field order: u_x, u_y, u_z, omega_x, omega_y, omega_z.
+template <int N>
+__global__ void __launch_bounds__(NXCfg<N>::THREADS)
+    k_ns_invx(const float2* __restrict__ u, float2* __restrict__ w, NSGeom g, int ktiles,
+              const float2* __restrict__ tw, int twlog) {
+  using C = NXCfg<N>;
+  constexpr int G = C::G, S = C::S, T = C::T;
+  extern __shared__ float2 smn[];
+  const int c = threadIdx.x % T, j = threadIdx.x / T;
+  const int dky = blockIdx.x / ktiles;
+  const int kz = (blockIdx.x - dky * ktiles) * T + c;
+  const bool valid = kz < g.kc;
+  const int ay = dense_to_a(dky, N, g.kd);
+  const long long q = (long long)ay * g.h1 + kz;
+  const long long rs = (long long)N * g.h1;
+  const float ky = (float)kwav(ay, N), kzf = (float)kz;
+  const ColX<T> xc{smn, c};
+  auto load = [&](int f, float2(&v)[G], bool ikx) {
+#pragma unroll
+    for (int m = 0; m < G; ++m) {
+      const int pos = j + m * S;
+      float2 a = make_float2(0.f, 0.f);
+      if (valid && kept_xy(pos, N, g.kd)) a = u[f * g.M + pos * rs + q];
+      v[m] = ikx ? mul_i(a, (float)kwav(pos, N)) : a;
+    }
+  };
+  auto store = [&](int f, const float2(&v)[G]) {
+    if (valid) {
+#pragma unroll
+      for (int m = 0; m < G; ++m) w[f * g.M + (j + m * S) * rs + q] = v[m];
+    }
+  };
+  float2 a[G], b[G];
+  load(1, a, true);
+  fft_line<N, G, +1>(a, j, xc, tw, twlog);  // D_y
+  load(0, b, false);
+  fft_line<N, G, +1>(b, j, xc, tw, twlog);  // U_x
+  store(0, b);
+#pragma unroll
+  for (int m = 0; m < G; ++m) a[m] = csub(a[m], mul_i(b[m], ky));  // omega_z
+  store(5, a);
+  load(2, a, true);
+  fft_line<N, G, +1>(a, j, xc, tw, twlog);  // D_z
+#pragma unroll
+  for (int m = 0; m < G; ++m) a[m] = csub(mul_i(b[m], kzf), a[m]);  // omega_y
+  store(4, a);
+  load(1, a, false);
+  fft_line<N, G, +1>(a, j, xc, tw, twlog);  // U_y
+  store(1, a);
+  load(2, b, false);
+  fft_line<N, G, +1>(b, j, xc, tw, twlog);  // U_z
+  store(2, b);
+#pragma unroll
+  for (int m = 0; m < G; ++m)
+    b[m] = make_float2(-(ky * b[m].y - kzf * a[m].y), ky * b[m].x - kzf * a[m].x);  // omega_x
+  store(3, b);
+}
+
+// 2./4. y pass on `nf` fields, columns (x, k_z < kc).  SIGN=+1: only kept k_y
+// rows are read, every y row is written; SIGN=-1: every y row is read, only
+// kept k_y rows are written.
+template <int N, int SIGN>
+__global__ void __launch_bounds__(NXCfg<N>::THREADS)
+    k_ns_ypass(float2* w, NSGeom g, int ktiles, const float2* __restrict__ tw, int twlog) {
+  using C = NXCfg<N>;
+  constexpr int G = C::G, S = C::S, T = C::T;
+  extern __shared__ float2 smn[];
+  const int c = threadIdx.x % T, j = threadIdx.x / T;
+  const int kt = blockIdx.x % ktiles;
+  const int rest = blockIdx.x / ktiles;
+  const int x = rest % N;
+  const int f = rest / N;
+  const int kz = kt * T + c;
+  const bool valid = kz < g.kc;
+  float2* base = w + f * g.M + (long long)x * N * g.h1 + kz;
+  float2 v[G];
+#pragma unroll
+  for (int m = 0; m < G; ++m) {
+    const int pos = j + m * S;
+    const bool rd = valid && (SIGN < 0 || kept_xy(pos, N, g.kd));
+    v[m] = rd ? base[(long long)pos * g.h1] : make_float2(0.f, 0.f);
+  }
+  fft_line<N, G, SIGN>(v, j, ColX<T>{smn, c}, tw, twlog);
+  if (valid) {
+#pragma unroll
+    for (int m = 0; m < G; ++m) {
+      const int pos = j + m * S;
+      if (SIGN > 0 || kept_xy(pos, N, g.kd)) base[(long long)pos * g.h1] = v[m];
+    }
+  }
+}
+
+// ------------------------------------------------------------- z product ---
+template <int N>
+struct NZCfg {
+  static constexpr int H = N / 2;
+  static constexpr int G = H < 8 ? H : 8;
+  static constexpr int S = H / G;
+  static constexpr int LPC = S >= 256 ? 1 : 256 / S;
+  static constexpr int THREADS = LPC * S;
+  static constexpr bool WARP = S <= 32;
+};
+
+// 3. per (x, y) line: the six c2r transforms, the product n = u x omega and
+//    the three r2c transforms.  Reads k_z < kc of fields 0..5, writes k_z < kc
+//    of fields 0..2 (in place: a line is fully read before it is written).
+template <int N>
+__global__ void __launch_bounds__(NZCfg<N>::THREADS)
+    k_ns_z(float2* w, NSGeom g, const float2* __restrict__ tw, int twlog) {
+  using C = NZCfg<N>;
+  constexpr int H = C::H, G = C::G, S = C::S;
+  constexpr int LOGN = Log2<N>::value;
+  __shared__ float2 sm[C::LPC * H];
+  const int li = threadIdx.x / S, j = threadIdx.x % S;
+  const long long line = (long long)blockIdx.x * C::LPC + li;
+  const bool valid = line < (long long)N * N;
+  const LineX<C::WARP> xc{sm + li * H};
+  float2 U[6][G];
+#pragma unroll
+  for (int f = 0; f < 6; ++f) {
+    const float2* src = w + f * g.M + line * g.h1;
+#pragma unroll
+    for (int m = 0; m < G; ++m) {
+      const int k = j + m * S;
+      float2 A = make_float2(0.f, 0.f), B = make_float2(0.f, 0.f);
+      if (valid && k < g.kc) A = src[k];
+      if (valid && H - k < g.kc) B = src[H - k];
+      if (k == 0) {
+        A.y = 0.f;
+        B.y = 0.f;
+      }
+      const float2 Bc = cconj(B);
+      const float2 E = cadd(A, Bc);
+      const float2 W = __ldg(&tw[k << (twlog - LOGN)]);
+      const float2 O = cmulc(csub(A, Bc), W);
+      U[f][m] = make_float2(E.x - O.y, E.y + O.x);
+    }
+    fft_line<H, G, +1>(U[f], j, xc, tw, twlog);
+  }
+  // n = u x omega at the two real points held by each complex slot
+#pragma unroll
+  for (int m = 0; m < G; ++m) {
+    const float2 ux = U[0][m], uy = U[1][m], uz = U[2][m];
+    const float2 wx = U[3][m], wy = U[4][m], wz = U[5][m];
+    U[0][m] = make_float2(uy.x * wz.x - uz.x * wy.x, uy.y * wz.y - uz.y * wy.y);
+    U[1][m] = make_float2(uz.x * wx.x - ux.x * wz.x, uz.y * wx.y - ux.y * wz.y);
+    U[2][m] = make_float2(ux.x * wy.x - uy.x * wx.x, ux.y * wy.y - uy.y * wx.y);
+  }
+#pragma unroll
+  for (int f = 0; f < 3; ++f) {
+    fft_line<H, G, -1>(U[f], j, xc, tw, twlog);
+#pragma unroll
+    for (int m = 0; m < G; ++m) xc.st(j + m * S, U[f][m]);
+    xc.sync();
+    float2* dst = w + f * g.M + line * g.h1;
+#pragma unroll
+    for (int m = 0; m < G; ++m) {
+      const int k = j + m * S;
+      const float2 A = U[f][m];
+      const float2 Bc = cconj(xc.ld((H - k) & (H - 1)));
+      const float2 E = cscale(cadd(A, Bc), 0.5f);
+      const float2 D = csub(A, Bc);
+      const float2 O = make_float2(0.5f * D.y, -0.5f * D.x);
+      const float2 W = __ldg(&tw[k << (twlog - LOGN)]);
+      if (valid && k < g.kc) dst[k] = cadd(E, cmul(W, O));
+    }
+    xc.sync();
+  }
+}
+
+// ----------------------------------------------------- x pass + update -----
+enum NSMode : int { NS_RHS = 0, NS_STAGE1 = 1, NS_STAGE2 = 2 };
+
+struct NSUpdate {
+  const float2* etab;  // exp(-nu k^2 dt) = hi + lo (two FP32 parts), indexed by integer k^2
+  const double* ef;    // forced-mode energy (device scalar)
+  double feps;         // injected power (0 = off)
+  int k2min, k2max;
+  float dt;
+  float scale;         // 1 / n^3
+};
+
+// 5. forward x pass of the 3 nonlinear fields, then on every kept mode:
+//    N = P[n] (Eq. (8)), + forcing, and
+//    RHS:    out = N
+//    STAGE1: out = E (u0 + dt N)                      (out = u1)
+//    STAGE2: out = 1/2 E u0 + 1/2 (u1 + dt N)         (out = u0, in place)
+template <int N>
+__global__ void __launch_bounds__(NXCfg<N>::THREADS)
+    k_ns_fwdx(const float2* __restrict__ nh, const float2* u0, const float2* u1, float2* out,
+              NSGeom g, int ktiles, NSUpdate upd, int mode, const float2* __restrict__ tw,
+              int twlog) {
+  using C = NXCfg<N>;
+  constexpr int G = C::G, S = C::S, T = C::T;
+  extern __shared__ float2 smn[];
+  const int c = threadIdx.x % T, j = threadIdx.x / T;
+  const int dky = blockIdx.x / ktiles;
+  const int kz = (blockIdx.x - dky * ktiles) * T + c;
+  const bool valid = kz < g.kc;
+  const int ay = dense_to_a(dky, N, g.kd);
+  const long long q = (long long)ay * g.h1 + kz;
+  const long long rs = (long long)N * g.h1;
+  const ColX<T> xc{smn, c};
+  float2 V[3][G];
+#pragma unroll
+  for (int f = 0; f < 3; ++f) {
+#pragma unroll
+    for (int m = 0; m < G; ++m)
+      V[f][m] = valid ? nh[f * g.M + (j + m * S) * rs + q] : make_float2(0.f, 0.f);
+    fft_line<N, G, -1>(V[f], j, xc, tw, twlog);
+  }
+  if (!valid) return;
+  const int ky = kwav(ay, N);
+  float gforce = 0.f;
+  if (upd.feps > 0.0) {
+    const double ef = *upd.ef;
+    gforce = ef > 0.0 ? (float)(upd.feps / (2.0 * ef)) : 0.f;
+  }
+#pragma unroll
+  for (int m = 0; m < G; ++m) {
+    const int pos = j + m * S;
+    if (!kept_xy(pos, N, g.kd)) continue;
+    const int kx = kwav(pos, N);
+    const int k2 = kx * kx + ky * ky + kz * kz;
+    const long long idx = pos * rs + q;
+    float2 nx = cscale(V[0][m], upd.scale), ny = cscale(V[1][m], upd.scale),
+           nz = cscale(V[2][m], upd.scale);
+    if (k2 == 0) {
+      nx = ny = nz = make_float2(0.f, 0.f);
+    } else {
+      const float fkx = (float)kx, fky = (float)ky, fkz = (float)kz;
+      const float inv = 1.f / (float)k2;
+      const float2 kn = make_float2((fkx * nx.x + fky * ny.x + fkz * nz.x) * inv,
+                                    (fkx * nx.y + fky * ny.y + fkz * nz.y) * inv);
+      nx = csub(nx, cscale(kn, fkx));
+      ny = csub(ny, cscale(kn, fky));
+      nz = csub(nz, cscale(kn, fkz));
+    }
+    const bool forced = gforce != 0.f && k2 >= upd.k2min && k2 <= upd.k2max;
+    const float2* ucur = (mode == NS_STAGE2) ? u1 : u0;
+    if (forced) {
+      nx = cadd(nx, cscale(ucur[idx], gforce));
+      ny = cadd(ny, cscale(ucur[idx + g.M], gforce));
+      nz = cadd(nz, cscale(ucur[idx + 2 * g.M], gforce));
+    }
+    if (mode == NS_RHS) {
+      out[idx] = nx;
+      out[idx + g.M] = ny;
+      out[idx + 2 * g.M] = nz;
+    } else {
+      // E = hi + lo carries the factor to ~2^-48; v * E is formed as
+      // fma(v, hi, v * lo), one rounding, so repeated steps do not bias the decay.
+      const float2 E = __ldg(&upd.etab[k2]);
+      const float dt = upd.dt;
+      const float2 n3[3] = {nx, ny, nz};
+#pragma unroll
+      for (int f = 0; f < 3; ++f) {
+        const float2 a = u0[idx + f * g.M];
+        float2 r;
+        if (mode == NS_STAGE1) {
+          const float sx = a.x + dt * n3[f].x, sy = a.y + dt * n3[f].y;
+          r = make_float2(fmaf(sx, E.x, sx * E.y), fmaf(sy, E.x, sy * E.y));
+        } else {
+          const float2 b = u1[idx + f * g.M];
+          const float ex = fmaf(a.x, E.x, a.x * E.y), ey = fmaf(a.y, E.x, a.y * E.y);
+          r = make_float2(0.5f * (ex + (b.x + dt * n3[f].x)), 0.5f * (ey + (b.y + dt * n3[f].y)));
+        }
+        out[idx + f * g.M] = r;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------ reductions ---
+// Energy of the forced modes, 1/2 sum w |u|^2 over k2min <= |k|^2 <= k2max,
+// in FP64; one block, fixed order.
+__global__ void k_forced_energy(const float2* __restrict__ u, NSGeom g, int kr, int k2min,
+                                int k2max, double* ef) {
+  __shared__ double red[256];
+  const int side = 2 * kr + 1;
+  const int count = side * side * (kr + 1);
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < count; i += blockDim.x) {
+    const int kz = i % (kr + 1);
+    const int t = i / (kr + 1);
+    const int ky = t % side - kr, kx = t / side - kr;
+    const int k2 = kx * kx + ky * ky + kz * kz;
+    if (k2 < k2min || k2 > k2max) continue;
+    const int ax = kx < 0 ? kx + g.n : kx, ay = ky < 0 ? ky + g.n : ky;
+    const long long idx = ((long long)ax * g.n + ay) * g.h1 + kz;
+    const double w = kz == 0 ? 1.0 : 2.0;
+    double s = 0.0;
+    for (int f = 0; f < 3; ++f) {
+      const float2 v = u[idx + f * g.M];
+      s += (double)v.x * v.x + (double)v.y * v.y;
+    }
+    acc += 0.5 * w * s;
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *ef = red[0];
+}
+
+constexpr int DIAG_BLOCKS = 256;
+constexpr int DIAG_WARPS = 8;
+
+// Deterministic FP64 diagnostics over the kept modes.  A work item is 32
+// consecutive k_z of one (k_x, k_y) line; along a line the shell index is
+// non-decreasing, so a warp sums each shell's run with a segmented shuffle
+// reduction (fixed order) and one lane adds it to the warp's histogram.
+// Items are assigned to warps by a fixed grid stride; partials per block are
+// summed in block order by k_diag_final.
+__global__ void __launch_bounds__(DIAG_WARPS * 32)
+    k_diag(const float2* __restrict__ u, NSGeom g, double nu, int kmax, double* part) {
+  extern __shared__ double hist[];  // [DIAG_WARPS][kmax+1]
+  __shared__ double we[DIAG_WARPS], wd[DIAG_WARPS];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nb = kmax + 1;
+  for (int i = threadIdx.x; i < DIAG_WARPS * nb; i += blockDim.x) hist[i] = 0.0;
+  __syncthreads();
+  double* h = hist + warp * nb;
+  const int nchunk = (g.kc + 31) / 32;
+  const long long items = (long long)g.nk * g.nk * nchunk;
+  double accE = 0.0, accD = 0.0;
+  for (long long it = (long long)blockIdx.x * DIAG_WARPS + warp; it < items;
+       it += (long long)gridDim.x * DIAG_WARPS) {
+    const long long line = it / nchunk;
+    const int chunk = (int)(it - line * nchunk);
+    const int ax = dense_to_a((int)(line / g.nk), g.n, g.kd);
+    const int ay = dense_to_a((int)(line % g.nk), g.n, g.kd);
+    const int kz = chunk * 32 + lane;
+    const bool valid = kz < g.kc;
+    double e = 0.0;
+    int shell = kmax + 1;
+    if (valid) {
+      const long long idx = ((long long)ax * g.n + ay) * g.h1 + kz;
+      double s = 0.0;
+      for (int f = 0; f < 3; ++f) {
+        const float2 v = u[idx + f * g.M];
+        s += (double)v.x * v.x + (double)v.y * v.y;
+      }
+      const double w = (kz == 0 || 2 * kz == g.n) ? 1.0 : 2.0;
+      e = 0.5 * w * s;
+      const long long kx = kwav(ax, g.n), ky = kwav(ay, g.n);
+      const long long k2 = kx * kx + ky * ky + (long long)kz * kz;
+      long long K = (long long)floor(sqrt((double)k2));
+      while (K * K > k2) --K;
+      while ((K + 1) * (K + 1) <= k2) ++K;
+      if (k2 >= K * K + K + 1) ++K;  // nint(|k|): |k| >= K + 1/2
+      shell = K <= kmax ? (int)K : kmax + 1;
+      accE += e;
+      accD += 2.0 * nu * (double)k2 * e;
+    }
+    // segmented suffix sums over lanes with the same shell
+    double v = e;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const double other = __shfl_down_sync(0xffffffffu, v, o);
+      const int os = __shfl_down_sync(0xffffffffu, shell, o);
+      if (lane + o < 32 && os == shell) v += other;
+    }
+    const int prev = __shfl_up_sync(0xffffffffu, shell, 1);
+    if (valid && shell <= kmax && (lane == 0 || prev != shell)) h[shell] += v;
+    __syncwarp();
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    accE += __shfl_down_sync(0xffffffffu, accE, o);
+    accD += __shfl_down_sync(0xffffffffu, accD, o);
+  }
+  if (lane == 0) {
+    we[warp] = accE;
+    wd[warp] = accD;
+  }
+  __syncthreads();
+  double* out = part + (long long)blockIdx.x * (2 + nb);
+  for (int s = threadIdx.x; s < nb; s += blockDim.x) {
+    double t = 0.0;
+    for (int w2 = 0; w2 < DIAG_WARPS; ++w2) t += hist[w2 * nb + s];
+    out[2 + s] = t;
+  }
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w2 = 0; w2 < DIAG_WARPS; ++w2) {
+      a += we[w2];
+      b += wd[w2];
+    }
+    out[0] = a;
+    out[1] = b;
+  }
+}
+
+__global__ void k_diag_final(const double* __restrict__ part, int width, int nblocks, double* out) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= width) return;
+  double t = 0.0;
+  for (int b = 0; b < nblocks; ++b) t += part[(long long)b * width + s];
+  out[s] = t;
+}
+
+// ------------------------------------------------------------ workspace ----
+struct NSWork {
+  NSGeom g;
+  float2* w = nullptr;     // 6 fields
+  float2* u1 = nullptr;    // 3 fields
+  float2* etab = nullptr;  // exp(-nu k^2 dt) as hi + lo, k^2 in [0, 3 kd^2]
+  int etab_len = 0;
+  double etab_nu = -1.0, etab_dt = -1.0;
+  double* ef = nullptr;    // forced energy
+  double* part = nullptr;  // diag partials
+  double* dout = nullptr;  // diag result (device)
+  double* hout = nullptr;  // diag result (pinned host)
+  int kmax = 0;
+  int diag_smem = 0;
+};
+
+static int ns_kmax(int n) { return (int)std::floor(std::sqrt(3.0) * (n / 2) + 0.5) + 1; }
+
+static NSGeom make_geom(int n) {
+  NSGeom g;
+  g.n = n;
+  g.h1 = n / 2 + 1;
+  g.kd = (n - 1) / 3;
+  g.kc = g.kd + 1;
+  g.nk = 2 * g.kd + 1;
+  g.M = (long long)n * n * g.h1;
+  return g;
+}
+
+static fftk_status ns_ensure(fftk_plan p) {
+  std::lock_guard<std::mutex> lk(p->mu);
+  if (p->ns) return FFTK_OK;
+  NSWork* s = new (std::nothrow) NSWork;
+  if (!s) return FFTK_ERR_OOM;
+  s->g = make_geom(p->nx);
+  s->kmax = ns_kmax(p->nx);
+  s->etab_len = 3 * s->g.kd * s->g.kd + 1;
+  const size_t fb = sizeof(float2) * (size_t)s->g.M;
+  const int width = 2 + s->kmax + 1;
+  cudaError_t e = cudaMalloc(&s->w, 6 * fb);
+  if (e == cudaSuccess) e = cudaMalloc(&s->u1, 3 * fb);
+  if (e == cudaSuccess) e = cudaMemset(s->u1, 0, 3 * fb);
+  if (e == cudaSuccess) e = cudaMalloc(&s->etab, sizeof(float2) * (size_t)s->etab_len);
+  if (e == cudaSuccess) e = cudaMalloc(&s->ef, sizeof(double));
+  if (e == cudaSuccess) e = cudaMemset(s->ef, 0, sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&s->part, sizeof(double) * (size_t)DIAG_BLOCKS * width);
+  if (e == cudaSuccess) e = cudaMalloc(&s->dout, sizeof(double) * (size_t)width);
+  if (e == cudaSuccess) e = cudaMallocHost(&s->hout, sizeof(double) * (size_t)width);
+  s->diag_smem = (int)(sizeof(double) * DIAG_WARPS * (s->kmax + 1));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, s->diag_smem);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(s->w);
+    cudaFree(s->u1);
+    cudaFree(s->etab);
+    cudaFree(s->ef);
+    cudaFree(s->part);
+    cudaFree(s->dout);
+    if (s->hout) cudaFreeHost(s->hout);
+    delete s;
+    return e == cudaErrorMemoryAllocation ? FFTK_ERR_OOM : FFTK_ERR_CUDA;
+  }
+  p->ns = s;
+  return FFTK_OK;
+}
+
+// exp(-nu k^2 dt) for integer k^2, FP64 on the host, split into an FP32 pair
+// hi = fl(E), lo = fl(E - hi).
+static fftk_status ns_etab(fftk_plan p, double nu, double dt) {
+  NSWork* s = p->ns;
+  if (s->etab_nu == nu && s->etab_dt == dt) return FFTK_OK;
+  std::vector<float2> h((size_t)s->etab_len);
+  for (int k2 = 0; k2 < s->etab_len; ++k2) {
+    const double E = std::exp(-nu * (double)k2 * dt);
+    const float hi = (float)E;
+    h[(size_t)k2] = make_float2(hi, (float)(E - (double)hi));
+  }
+  cudaError_t e = cudaMemcpy(s->etab, h.data(), sizeof(float2) * h.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return from_cuda(e);
+  s->etab_nu = nu;
+  s->etab_dt = dt;
+  return FFTK_OK;
+}
+
+// --------------------------------------------------------------- launchers --
+template <int N>
+struct NSLaunch {
+  static cudaError_t attrs() {
+    static std::once_flag once;
+    static cudaError_t err = cudaSuccess;
+    std::call_once(once, [] {
+      const int sm = (int)NXCfg<N>::SMEM;
+      err = cudaFuncSetAttribute(k_ns_invx<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+      if (err == cudaSuccess)
+        err = cudaFuncSetAttribute(k_ns_ypass<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+      if (err == cudaSuccess)
+        err = cudaFuncSetAttribute(k_ns_ypass<N, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+      if (err == cudaSuccess)
+        err = cudaFuncSetAttribute(k_ns_fwdx<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    });
+    return err;
+  }
+
+  // One evaluation of N(u) followed by the update selected by `mode`.
+  static cudaError_t rhs(fftk_plan p, const float2* u, const float2* u0, const float2* u1,
+                         float2* out, const NSUpdate& upd, int mode, cudaStream_t st) {
+    using X = NXCfg<N>;
+    using Z = NZCfg<N>;
+    cudaError_t e = attrs();
+    if (e != cudaSuccess) return e;
+    NSWork* s = p->ns;
+    const NSGeom g = s->g;
+    const int ktiles = (g.kc + X::T - 1) / X::T;
+    {
+      LaunchScope ls(p, KK_NS_INVX, st);
+      k_ns_invx<N><<<g.nk * ktiles, X::THREADS, X::SMEM, st>>>(u, s->w, g, ktiles, p->d_tw, p->twlog);
+    }
+    {
+      LaunchScope ls(p, KK_NS_INVY, st);
+      k_ns_ypass<N, 1><<<6 * N * ktiles, X::THREADS, X::SMEM, st>>>(s->w, g, ktiles, p->d_tw, p->twlog);
+    }
+    {
+      LaunchScope ls(p, KK_NS_Z, st);
+      const long long lines = (long long)N * N;
+      k_ns_z<N><<<(unsigned)((lines + Z::LPC - 1) / Z::LPC), Z::THREADS, 0, st>>>(s->w, g, p->d_tw,
+                                                                                 p->twlog);
+    }
+    {
+      LaunchScope ls(p, KK_NS_FWDY, st);
+      k_ns_ypass<N, -1><<<3 * N * ktiles, X::THREADS, X::SMEM, st>>>(s->w, g, ktiles, p->d_tw, p->twlog);
+    }
+    {
+      LaunchScope ls(p, KK_NS_FWDX, st);
+      k_ns_fwdx<N><<<g.nk * ktiles, X::THREADS, X::SMEM, st>>>(s->w, u0, u1, out, g, ktiles, upd, mode,
+                                                              p->d_tw, p->twlog);
+    }
+    return cudaGetLastError();
+  }
+};
+
+#define NS_SIZES(X) X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024)
+
+static cudaError_t ns_rhs_dispatch(fftk_plan p, const float2* u, const float2* u0, const float2* u1,
+                                   float2* out, const NSUpdate& upd, int mode, cudaStream_t st) {
+  switch (p->nx) {
+#define CASE(n) \
+  case n:       \
+    return NSLaunch<n>::rhs(p, u, u0, u1, out, upd, mode, st);
+    NS_SIZES(CASE)
+#undef CASE
+  }
+  return cudaErrorInvalidValue;
+}
+
+static cudaError_t forced_energy(fftk_plan p, const float2* u, const tarang_params* prm,
+                                 cudaStream_t st) {
+  int kr = 0;
+  while ((kr + 1) * (kr + 1) <= prm->force_k2max) ++kr;
+  LaunchScope ls(p, KK_NS_REDUCE, st);
+  k_forced_energy<<<1, 256, 0, st>>>(u, p->ns->g, kr, prm->force_k2min, prm->force_k2max,
+                                     p->ns->ef);
+  return cudaGetLastError();
+}
+
+static cudaError_t diag_launch(fftk_plan p, const float2* u, double nu, cudaStream_t st) {
+  NSWork* s = p->ns;
+  const int width = 2 + s->kmax + 1;
+  {
+    LaunchScope ls(p, KK_NS_REDUCE, st);
+    k_diag<<<DIAG_BLOCKS, DIAG_WARPS * 32, s->diag_smem, st>>>(u, s->g, nu, s->kmax, s->part);
+  }
+  {
+    LaunchScope ls(p, KK_NS_REDUCE, st);
+    k_diag_final<<<(width + 127) / 128, 128, 0, st>>>(s->part, width, DIAG_BLOCKS, s->dout);
+  }
+  return cudaGetLastError();
+}
+
+static bool misaligned16(const void* ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 15u) != 0; }
+
+static fftk_status ns_check(fftk_plan p, const tarang_params* prm, bool need_dt) {
+  if (!p || !prm) return FFTK_ERR_INVALID_ARG;
+  if (p->nx != p->ny || p->nx != p->nz) return FFTK_ERR_UNSUPPORTED_SIZE;
+  if (p->nx < 8 || p->nx > 1024) return FFTK_ERR_UNSUPPORTED_SIZE;
+  if (!(prm->nu >= 0.0) || !std::isfinite(prm->nu)) return FFTK_ERR_INVALID_ARG;
+  if (need_dt && (!(prm->dt > 0.0) || !std::isfinite(prm->dt))) return FFTK_ERR_INVALID_ARG;
+  if (prm->force_eps != 0.0) {
+    const int kd = (p->nx - 1) / 3;
+    if (!(prm->force_eps > 0.0) || prm->force_k2min < 1 || prm->force_k2max < prm->force_k2min ||
+        prm->force_k2max > kd * kd)
+      return FFTK_ERR_INVALID_ARG;
+  }
+  return FFTK_OK;
+}
+
+}  // namespace fftk
+
+using namespace fftk;
+
+void ns_free(fftk_plan p) {
+  NSWork* s = p->ns;
+  if (!s) return;
+  cudaFree(s->w);
+  cudaFree(s->u1);
+  cudaFree(s->etab);
+  cudaFree(s->ef);
+  cudaFree(s->part);
+  cudaFree(s->dout);
+  if (s->hout) cudaFreeHost(s->hout);
+  delete s;
+  p->ns = nullptr;
+}
+
+extern "C" int tarang_diag_kmax(fftk_plan p) { return p ? ns_kmax(p->nx) : -1; }
+
+extern "C" fftk_status tarang_ns_rhs(fftk_plan p, const void* uhat, void* nhat,
+                                     const tarang_params* prm, void* cuda_stream) {
+  fftk_status s = ns_check(p, prm, false);
+  if (s != FFTK_OK) return s;
+  if (!uhat || !nhat || uhat == nhat || misaligned16(uhat) || misaligned16(nhat))
+    return FFTK_ERR_INVALID_ARG;
+  s = ns_ensure(p);
+  if (s != FFTK_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  const NSGeom g = p->ns->g;
+  const float2* u = static_cast<const float2*>(uhat);
+  float2* out = static_cast<float2*>(nhat);
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(float2) * 3 * (size_t)g.M, st);
+  NSUpdate upd{p->ns->etab, p->ns->ef, prm->force_eps, prm->force_k2min, prm->force_k2max, 0.f,
+               (float)(1.0 / ((double)g.n * g.n * g.n))};
+  if (e == cudaSuccess && prm->force_eps > 0.0) e = forced_energy(p, u, prm, st);
+  if (e == cudaSuccess) e = ns_rhs_dispatch(p, u, u, nullptr, out, upd, NS_RHS, st);
+  return from_cuda(e);
+}
+
+extern "C" fftk_status tarang_diag(fftk_plan p, const void* uhat, double nu, double* diag_host,
+                                   void* cuda_stream) {
+  if (!p || !uhat || !diag_host || misaligned16(uhat)) return FFTK_ERR_INVALID_ARG;
+  if (p->nx != p->ny || p->nx != p->nz || p->nx < 8 || p->nx > 1024)
+    return FFTK_ERR_UNSUPPORTED_SIZE;
+  fftk_status s = ns_ensure(p);
+  if (s != FFTK_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  NSWork* w = p->ns;
+  const int width = 2 + w->kmax + 1;
+  cudaError_t e = diag_launch(p, static_cast<const float2*>(uhat), nu, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(w->hout, w->dout, sizeof(double) * width, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return from_cuda(e);
+  std::memcpy(diag_host, w->hout, sizeof(double) * width);
+  return std::isfinite(diag_host[0]) ? FFTK_OK : FFTK_ERR_NONFINITE;
+}
+
+extern "C" fftk_status tarang_ns_step(fftk_plan p, void* uhat, const tarang_params* prm, int nsteps,
+                                      double* diag_host, void* cuda_stream) {
+  fftk_status s = ns_check(p, prm, true);
+  if (s != FFTK_OK) return s;
+  if (!uhat || nsteps < 0 || misaligned16(uhat)) return FFTK_ERR_INVALID_ARG;
+  s = ns_ensure(p);
+  if (s != FFTK_OK) return s;
+  s = ns_etab(p, prm->nu, prm->dt);
+  if (s != FFTK_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  NSWork* w = p->ns;
+  const NSGeom g = w->g;
+  float2* u = static_cast<float2*>(uhat);
+  NSUpdate upd{w->etab, w->ef, prm->force_eps, prm->force_k2min, prm->force_k2max, (float)prm->dt,
+               (float)(1.0 / ((double)g.n * g.n * g.n))};
+  cudaError_t e = cudaSuccess;
+  for (int it = 0; it < nsteps && e == cudaSuccess; ++it) {
+    if (prm->force_eps > 0.0) e = forced_energy(p, u, prm, st);
+    if (e == cudaSuccess) e = ns_rhs_dispatch(p, u, u, nullptr, w->u1, upd, NS_STAGE1, st);
+    if (e == cudaSuccess && prm->force_eps > 0.0) e = forced_energy(p, w->u1, prm, st);
+    if (e == cudaSuccess) e = ns_rhs_dispatch(p, w->u1, u, w->u1, u, upd, NS_STAGE2, st);
+  }
+  if (e != cudaSuccess) return from_cuda(e);
+  if (diag_host) return tarang_diag(p, u, prm->nu, diag_host, cuda_stream);
+  return FFTK_OK;
+}
+
+// --------------------------------------------------------- initial field ---
+namespace fftk {
+
+// Zero every mode outside the 2/3 set and project the kept ones (Eq. (8)).
+__global__ void k_ic_shape(float2* u, NSGeom g) {
+  const long long total = g.M;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(i % g.h1);
+    const long long ab = i / g.h1;
+    const int b = (int)(ab % g.n), a = (int)(ab / g.n);
+    if (!(kept_xy(a, g.n, g.kd) && kept_xy(b, g.n, g.kd) && c < g.kc)) {
+      u[i] = u[i + g.M] = u[i + 2 * g.M] = make_float2(0.f, 0.f);
+      continue;
+    }
+    const float kx = (float)kwav(a, g.n), ky = (float)kwav(b, g.n), kz = (float)c;
+    const float k2 = kx * kx + ky * ky + kz * kz;
+    if (k2 == 0.f) {
+      u[i] = u[i + g.M] = u[i + 2 * g.M] = make_float2(0.f, 0.f);
+      continue;
+    }
+    const float2 ux = u[i], uy = u[i + g.M], uz = u[i + 2 * g.M];
+    const float2 kd = make_float2((kx * ux.x + ky * uy.x + kz * uz.x) / k2,
+                                  (kx * ux.y + ky * uy.y + kz * uz.y) / k2);
+    u[i] = csub(ux, cscale(kd, kx));
+    u[i + g.M] = csub(uy, cscale(kd, ky));
+    u[i + 2 * g.M] = csub(uz, cscale(kd, kz));
+  }
+}
+
+// Make the k_z = 0 plane exactly Hermitian: f(-kx,-ky) = conj f(kx,ky).
+__global__ void k_ic_herm(float2* u, NSGeom g) {
+  const long long total = 3LL * g.n * g.n;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int f = (int)(i / ((long long)g.n * g.n));
+    const int ab = (int)(i % ((long long)g.n * g.n));
+    const int a = ab / g.n, b = ab % g.n;
+    const int a2 = (g.n - a) % g.n, b2 = (g.n - b) % g.n;
+    const long long i1 = ((long long)a * g.n + b) * g.h1, i2 = ((long long)a2 * g.n + b2) * g.h1;
+    if (i2 < i1) continue;
+    float2* base = u + f * g.M;
+    if (i1 == i2) {
+      base[i1].y = 0.f;
+    } else {
+      const float2 p = base[i1], q = base[i2];
+      const float2 avg = make_float2(0.5f * (p.x + q.x), 0.5f * (p.y - q.y));
+      base[i1] = avg;
+      base[i2] = cconj(avg);
+    }
+  }
+}
+
+// u *= s[nint|k|] on the kept modes.
+__global__ void k_ic_rescale(float2* u, NSGeom g, const double* __restrict__ s, int kmax) {
+  const long long total = (long long)g.nk * g.nk * g.kc;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int kz = (int)(i % g.kc);
+    const long long t = i / g.kc;
+    const int a = dense_to_a((int)(t / g.nk), g.n, g.kd), b = dense_to_a((int)(t % g.nk), g.n, g.kd);
+    const long long kx = kwav(a, g.n), ky = kwav(b, g.n);
+    const long long k2 = kx * kx + ky * ky + (long long)kz * kz;
+    long long K = (long long)floor(sqrt((double)k2));
+    while (K * K > k2) --K;
+    while ((K + 1) * (K + 1) <= k2) ++K;
+    if (k2 >= K * K + K + 1) ++K;
+    const float sc = K <= kmax ? (float)s[K] : 0.f;
+    const long long idx = ((long long)a * g.n + b) * g.h1 + kz;
+    for (int f = 0; f < 3; ++f) u[idx + f * g.M] = cscale(u[idx + f * g.M], sc);
+  }
+}
+
+}  // namespace fftk
+
+extern "C" fftk_status tarang_ic_random(fftk_plan p, const float* normals, void* uhat, double k0,
+                                        double E0, void* cuda_stream) {
+  if (!p || !normals || !uhat || !(k0 > 0.0) || !(E0 > 0.0) || !std::isfinite(k0) ||
+      !std::isfinite(E0))
+    return FFTK_ERR_INVALID_ARG;
+  if (p->nx != p->ny || p->nx != p->nz || p->nx < 8 || p->nx > 1024)
+    return FFTK_ERR_UNSUPPORTED_SIZE;
+  fftk_status s = ns_ensure(p);
+  if (s != FFTK_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  NSWork* w = p->ns;
+  const NSGeom g = w->g;
+  float2* u = static_cast<float2*>(uhat);
+  s = fftk_r2c(p, normals, uhat, 3, cuda_stream);
+  if (s != FFTK_OK) return s;
+  {
+    LaunchScope ls(p, KK_AUX, st);
+    k_ic_shape<<<152 * 8, 256, 0, st>>>(u, g);
+  }
+  {
+    LaunchScope ls(p, KK_AUX, st);
+    k_ic_herm<<<152 * 4, 256, 0, st>>>(u, g);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return from_cuda(e);
+  const int kmax = w->kmax;
+  std::vector<double> d((size_t)(2 + kmax + 1));
+  s = tarang_diag(p, uhat, 0.0, d.data(), cuda_stream);
+  if (s != FFTK_OK) return s;
+  // per-shell factors so that E(K) ~ K^4 exp(-2 (K/k0)^2), then total E0
+  std::vector<double> sc((size_t)kmax + 1, 0.0);
+  double tsum = 0.0;
+  for (int K = 1; K <= kmax; ++K) {
+    const double eK = d[(size_t)(2 + K)];
+    if (eK > 0.0) {
+      const double t = std::pow((double)K, 4.0) * std::exp(-2.0 * ((double)K / k0) * ((double)K / k0));
+      sc[(size_t)K] = std::sqrt(t / eK);
+      tsum += t;
+    }
+  }
+  if (!(tsum > 0.0)) return FFTK_ERR_NONFINITE;
+  const double gscale = std::sqrt(E0 / tsum);
+  for (auto& v : sc) v *= gscale;
+  double* dsc = nullptr;
+  e = cudaMalloc(&dsc, sizeof(double) * sc.size());
+  if (e == cudaSuccess) e = cudaMemcpy(dsc, sc.data(), sizeof(double) * sc.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    LaunchScope ls(p, KK_AUX, st);
+    k_ic_rescale<<<152 * 8, 256, 0, st>>>(u, g, dsc, kmax);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (dsc) cudaFree(dsc);
+  return from_cuda(e);
+}
