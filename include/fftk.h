@@ -136,6 +136,27 @@ int tarang_diag_kmax(fftk_plan p);
 fftk_status tarang_diag(fftk_plan p, const void *uhat, double nu, double *diag_host,
                         void *cuda_stream);
 
+/* The diagnostics of tarang_diag for callers that cannot allocate device
+ * memory.  The paper has no counterpart: this exists for host code that must
+ * not call cudaMalloc (for instance a loop that cannot afford cudaMalloc's
+ * implicit device-wide synchronisation, or an application whose own memory
+ * manager owns all device allocations).  No plan is needed and nothing is
+ * allocated: the FP64 partial sums live in a 2 MiB array that the library
+ * reserves statically on every device that loads it, held until the process
+ * exits.  n: grid size of a cubic velocity state uhat (float2
+ * [3][n][n][n/2+1], 2/3-truncated as for tarang_ns_step), a power of two in
+ * [8, 1024]; larger n returns FFTK_ERR_UNSUPPORTED_SIZE.  diag_dev: device
+ * buffer of 2 + kmax + 1 doubles, kmax = floor(sqrt(3) n / 2 + 1/2) + 1,
+ * receiving E, eps, E(K) exactly as tarang_diag computes them (same kernels,
+ * same summation order).  Asynchronous on cuda_stream; the result is valid
+ * once the stream reaches it.  The first call on each device looks up the
+ * array's device address and sets the reduction kernel's shared-memory limit;
+ * make that first call before any stream capture.  All calls on a device
+ * share the one array, so calls that overlap on the GPU (concurrent streams,
+ * or host threads) race and must be serialised by the caller. */
+fftk_status tarang_diag_noalloc(int n, const void *uhat, double nu, double *diag_dev,
+                                void *cuda_stream);
+
 /* Random-phase solenoidal initial velocity (used by the decaying- and
  * forced-turbulence workloads): the forward transform of three real fields
  * `normals` (device float [3][n][n][n], e.g. from fftk_fill_normal), 2/3

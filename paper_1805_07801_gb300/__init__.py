@@ -68,6 +68,7 @@ def lib() -> ctypes.CDLL:
             "tarang_ns_step": ([vp, vp, c.POINTER(tarang_params), i, vp, vp], i),
             "tarang_diag_kmax": ([vp], i),
             "tarang_diag": ([vp, vp, d, vp, vp], i),
+            "tarang_diag_noalloc": ([i, vp, d, vp, vp], i),
             "tarang_ic_random": ([vp, vp, vp, d, d, vp], i),
             "fftk_fill_normal": ([vp, ll, i, i, vp], i),
             "fftk_fill_uniform": ([vp, ll, i, i, vp], i),
@@ -158,6 +159,12 @@ def tarang_diag(plan: int, uhat_ptr, nu: float, stream=0):
            "tarang_diag")
     vals = list(buf)
     return vals[0], vals[1], vals[2:]
+
+
+def tarang_diag_noalloc(n: int, uhat_ptr, nu: float, diag_dev_ptr, stream=0) -> None:
+    """Diagnostics into a caller-owned device buffer of 2 + kmax + 1 doubles; allocates nothing."""
+    _check(lib().tarang_diag_noalloc(int(n), _vp(uhat_ptr), float(nu), _vp(diag_dev_ptr), _vp(stream)),
+           "tarang_diag_noalloc")
 
 
 def tarang_ic_random(plan: int, normals_ptr, uhat_ptr, k0: float = 4.0, E0: float = 0.5, stream=0) -> None:

@@ -879,3 +879,71 @@ extern "C" fftk_status tarang_ic_random(fftk_plan p, const float* normals, void*
   if (dsc) cudaFree(dsc);
   return from_cuda(e);
 }
+
+// ------------------------------------------- diagnostics without allocation --
+// Callers that cannot allocate device memory (a real-time loop that must not
+// pay cudaMalloc's implicit device synchronisation, or a host application
+// whose memory manager forbids allocations it does not own) get the same
+// FP64 diagnostics through tarang_diag_noalloc.  Its scratch space, the
+// per-block partial sums, lives in this file-scope array for the life of the
+// process on every device that loads the library.
+namespace fftk {
+
+constexpr size_t kNoAllocScratchDoubles = 262144;  // 2 MiB: DIAG_BLOCKS x (2 + kmax + 1) for n <= 1024
+static __device__ __align__(256) double g_diag_scratch[kNoAllocScratchDoubles];
+
+constexpr int kNoAllocMaxDevices = 64;
+static std::mutex g_noalloc_mu;
+static double* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Once per device, with that device current: the device address of the
+// scratch array (the host-side symbol is only a stand-in) and the dynamic
+// shared-memory limit of the reduction kernel for the largest n.
+static fftk_status noalloc_setup(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return from_cuda(e);
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return FFTK_ERR_UNSUPPORTED_SIZE;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    double* ptr = nullptr;
+    e = cudaGetSymbolAddress((void**)&ptr, g_diag_scratch);
+    if (e != cudaSuccess) return from_cuda(e);
+    const int smem = (int)(sizeof(double) * DIAG_WARPS * (ns_kmax(1024) + 1));
+    e = cudaFuncSetAttribute(k_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return from_cuda(e);
+    g_noalloc_ptr[dev] = ptr;
+  }
+  *out = g_noalloc_ptr[dev];
+  return FFTK_OK;
+}
+
+}  // namespace fftk
+
+extern "C" fftk_status tarang_diag_noalloc(int n, const void* uhat, double nu, double* diag_dev,
+                                           void* cuda_stream) {
+  if (!uhat || !diag_dev || misaligned16(uhat) ||
+      (reinterpret_cast<uintptr_t>(diag_dev) & 7u) != 0 || !(nu >= 0.0) || !std::isfinite(nu))
+    return FFTK_ERR_INVALID_ARG;
+  if (!is_pow2(n) || n < 8 || n > 1024) return FFTK_ERR_UNSUPPORTED_SIZE;
+  const int kmax = ns_kmax(n);
+  const int width = 2 + kmax + 1;
+  if ((size_t)DIAG_BLOCKS * (size_t)width > kNoAllocScratchDoubles) return FFTK_ERR_UNSUPPORTED_SIZE;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) {
+    cudaGetLastError();
+    return FFTK_ERR_NO_DEVICE;
+  }
+  double* scratch = nullptr;
+  fftk_status s = noalloc_setup(&scratch);
+  if (s != FFTK_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  const NSGeom g = make_geom(n);
+  // Every entry of the partials that k_diag_final reads is written by k_diag
+  // in the same call, so nothing in the shared scratch needs clearing.
+  const int smem = (int)(sizeof(double) * DIAG_WARPS * (kmax + 1));
+  k_diag<<<DIAG_BLOCKS, DIAG_WARPS * 32, smem, st>>>(static_cast<const float2*>(uhat), g, nu, kmax,
+                                                   scratch);
+  k_diag_final<<<(width + 127) / 128, 128, 0, st>>>(scratch, width, DIAG_BLOCKS, diag_dev);
+  return from_cuda(cudaGetLastError());
+}
