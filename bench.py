@@ -85,6 +85,40 @@ def fft_pass_bytes(n):
     }
 
 
+# --------------------------------------------------- measured DRAM traffic ---
+KERNEL_SOURCES = {
+    "ns": ["ns.cu", "fft_engine.cuh", "internal.h"],
+    "fft": ["fft_passes.cu", "fft_engine.cuh", "internal.h"],
+}
+
+
+def source_hash(group: str) -> str:
+    """SHA-1 over the CUDA sources a kernel group is built from."""
+    import hashlib
+
+    h = hashlib.sha1()
+    for f in KERNEL_SOURCES[group]:
+        with open(os.path.join(ROOT, "paper_1805_07801_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def measured_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) recorded
+    in profiles/dram_traffic.txt for this kernel and workload, or None when no
+    record exists or the kernel sources changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 4 and not line.startswith("#") and parts[0] == kernel and parts[1] == workload:
+            group = "ns" if kernel.startswith("ns_") else "fft"
+            if parts[3] == source_hash(group):
+                return int(float(parts[2]))
+    return None
+
+
 # ----------------------------------------------------------------- clocks ---
 class Clocks:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -293,8 +327,8 @@ def run_ours(args, world, rank, local):
         },
         "roofline": {
             "bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-            "frac": round(achieved / hbm, 4), "traffic": None, "peak_kind": peak_kind,
-            "bytes_per_launch": int(kb[dom]),
+            "frac": round(achieved / hbm, 4), "traffic": measured_traffic(dom, f"ns{n}"),
+            "peak_kind": peak_kind, "bytes_per_launch": int(kb[dom]),
         },
         "step_roofline": {
             "pruned_bytes": int(pruned), "unpruned_bytes": int(unpruned),
@@ -359,8 +393,8 @@ def bench_fft(fk, torch, dev, st_obj, args, hbm, peak_kind):
             "pair_bytes": int(pair),
             "frac_pair": round(pair / (ms * 1e-3) / 1e9 / hbm, 4),
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["GBps"], "peak": hbm,
-                         "unit": "GB/s", "frac": round(kern[dom]["GBps"] / hbm, 4), "traffic": None,
-                         "peak_kind": peak_kind},
+                         "unit": "GB/s", "frac": round(kern[dom]["GBps"] / hbm, 4),
+                         "traffic": measured_traffic(dom, f"fft{n}"), "peak_kind": peak_kind},
             "kernels": kern,
             "round_trip_rel_l2": rt,
             "nominal_gflops": round(2 * 5 * n**3 * 3 * 10 / (ms * 1e-3) / 1e9, 1),
@@ -428,6 +462,44 @@ def run_reference(args, world, rank):
     }
 
 
+def run_case(case: str):
+    """One small invocation for profiler captures (no timing, no output line):
+    'ns:<n>' = random-phase field + one NS step; 'fft:<nx>,<ny>,<nz>' = two pairs."""
+    import torch
+
+    import paper_1805_07801_gb300 as fk
+    from paper_1805_07801_gb300 import build as fkbuild
+
+    fkbuild.build()
+    dev = torch.device("cuda:0")
+    st = torch.cuda.current_stream(dev).cuda_stream
+    kind, arg = case.split(":")
+    if kind == "ns":
+        n = int(arg)
+        plan = fk.fftk_plan_create(n, n, n)
+        nr = torch.empty((3, n, n, n), dtype=torch.float32, device=dev)
+        for f in range(3):
+            fk.fftk_fill_normal(nr[f].data_ptr(), n**3, SEED, f, st)
+        u = torch.empty((3, n, n, n // 2 + 1, 2), dtype=torch.float32, device=dev)
+        fk.tarang_ic_random(plan, nr.data_ptr(), u.data_ptr(), K0, E0, st)
+        del nr
+        fk.tarang_ns_step(plan, u.data_ptr(), fk.make_params(NU, DT), 1, False, st)
+    elif kind == "fft":
+        nx, ny, nz = (int(v) for v in arg.split(","))
+        plan = fk.fftk_plan_create(nx, ny, nz)
+        x = torch.empty((nx, ny, nz), dtype=torch.float32, device=dev)
+        fk.fftk_fill_normal(x.data_ptr(), x.numel(), SEED, 0, st)
+        F = torch.empty((nx, ny, nz // 2 + 1, 2), dtype=torch.float32, device=dev)
+        y = torch.empty_like(x)
+        for _ in range(2):
+            fk.fftk_r2c(plan, x.data_ptr(), F.data_ptr(), 1, st)
+            fk.fftk_c2r(plan, F.data_ptr(), y.data_ptr(), 1, st)
+    else:
+        raise SystemExit(f"unknown case {case}")
+    torch.cuda.synchronize(dev)
+    fk.fftk_plan_destroy(plan)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -436,7 +508,11 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fft", action="store_true")
+    ap.add_argument("--case", default=None, help="profiler case: ns:<n> or fft:<nx>,<ny>,<nz>")
     args = ap.parse_args()
+    if args.case:
+        run_case(args.case)
+        return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     world, rank, local = dist_setup(args)

@@ -10,7 +10,7 @@
 // directly from registers with the same coalesced pattern.
 //
 // This replaces the FFTW 1D line transforms used by FFTK (paper Sec. 3);
-// the radix-16/8/4/2 factorisation is the planner's choice (see planner.cpp).
+// the radix-16/8/4/2 factorisation is fixed at compile time by Stage below.
 //
 // Sign convention: SIGN = -1 computes X[k] = sum_n x[n] exp(-2 pi i n k / L)
 // (forward), SIGN = +1 the unnormalised inverse.
@@ -168,13 +168,25 @@ struct ColX {
   __device__ __forceinline__ void sync() const { __syncthreads(); }
 };
 
+// Position of element `pos` of one contiguous line: an XOR permutation within
+// each 16-element block, keyed by the block index B = pos >> 4 through the
+// map bits(B) -> {1, 2, 12, 8, then 1, 2, 4, 8, ...}.  Block bit 2 flips slot
+// bits 2 and 3, which makes the radix-8 exchanges (8 values per thread) as
+// well as the radix-16 ones conflict free for 64-bit accesses.
+__device__ __forceinline__ int swz_line(int pos) {
+  const int b = pos >> 4;
+  const int lo = b & 15;
+  const int h = lo ^ ((lo & 4) << 1) ^ (b >> 4) ^ (b >> 8);
+  return (pos & ~15) | ((pos ^ h) & 15);
+}
+
 // Exchange buffer for one contiguous line; WARP_SYNC when a line's threads
 // live in one warp.
 template <bool WARP_SYNC>
 struct LineX {
   float2* s;
-  __device__ __forceinline__ void st(int pos, float2 v) const { s[swz<1>(pos)] = v; }
-  __device__ __forceinline__ float2 ld(int pos) const { return s[swz<1>(pos)]; }
+  __device__ __forceinline__ void st(int pos, float2 v) const { s[swz_line(pos)] = v; }
+  __device__ __forceinline__ float2 ld(int pos) const { return s[swz_line(pos)]; }
   __device__ __forceinline__ void sync() const {
     if constexpr (WARP_SYNC)
       __syncwarp();

@@ -19,6 +19,7 @@ struct ZCfg {
   static constexpr int LPC = S >= 256 ? 1 : 256 / S;  // lines per CTA
   static constexpr int THREADS = LPC * S;
   static constexpr bool WARP = S <= 32;
+  static constexpr int MINB = 4;  // 32 warps per SM at <= 64 registers
 };
 
 // Real-to-complex along z.  The N reals of a line are packed as H = N/2
@@ -26,7 +27,7 @@ struct ZCfg {
 //   X[k] = (Z[k] + conj Z[H-k])/2 + exp(-2 pi i k/N) (Z[k] - conj Z[H-k])/(2i),
 // k = 0..H (Z[H] = Z[0]).
 template <int N>
-__global__ void __launch_bounds__(ZCfg<N>::THREADS)
+__global__ void __launch_bounds__(ZCfg<N>::THREADS, ZCfg<N>::MINB)
     k_z_r2c(const float* __restrict__ in, float2* __restrict__ out, long long nlines,
             const float2* __restrict__ tw, int twlog, float scale) {
   using C = ZCfg<N>;
@@ -67,7 +68,7 @@ __global__ void __launch_bounds__(ZCfg<N>::THREADS)
 // Z[k] = E + i O, and the unnormalised H-point inverse of Z gives
 // x[2n] + i x[2n+1].  Im X[0] and Im X[H] are ignored (line-wise c2r).
 template <int N>
-__global__ void __launch_bounds__(ZCfg<N>::THREADS)
+__global__ void __launch_bounds__(ZCfg<N>::THREADS, ZCfg<N>::MINB)
     k_z_c2r(const float2* __restrict__ in, float* __restrict__ out, long long nlines,
             const float2* __restrict__ tw, int twlog) {
   using C = ZCfg<N>;
@@ -109,17 +110,21 @@ __global__ void __launch_bounds__(ZCfg<N>::THREADS)
 // ------------------------------------------------------- strided c2c pass --
 // Tile = T adjacent columns (contiguous index q) x the full line (L rows of
 // stride Q).  Loads and stores are T-wide row segments, coalesced along q.
+// Tile width T per line length: 32 warps per SM at <= 64 registers per
+// thread (2 CTAs of 512 threads up to L = 512, one of 1024 beyond), and row
+// segments of 128 bytes (T = 16) where the 227 KB of shared memory allows.
 template <int L>
 struct CCfg {
   static constexpr int G = elems_per_thread(L);
   static constexpr int S = L / G;
-  static constexpr int T = S <= 16 ? 256 / S : (S == 32 ? 16 : (S == 64 ? 8 : 4));
+  static constexpr int T = S <= 16 ? 256 / S : (S <= 64 ? 16 : 1024 / S);
   static constexpr int THREADS = T * S;
+  static constexpr int MINB = THREADS <= 512 ? 2 : 1;
   static constexpr size_t SMEM = sizeof(float2) * (size_t)L * T;
 };
 
 template <int L, int SIGN>
-__global__ void __launch_bounds__(CCfg<L>::THREADS)
+__global__ void __launch_bounds__(CCfg<L>::THREADS, CCfg<L>::MINB)
     k_cpass(const float2* in, float2* out, long long Q, long long qtiles,
             const float2* __restrict__ tw, int twlog, float scale) {
   using C = CCfg<L>;

@@ -50,8 +50,56 @@ __device__ __forceinline__ float2 mul_i(float2 a, float k) {  // a * (i k)
 }
 
 // ------------------------------------------------------------ x/y config ---
+// Single-field passes (inverse x with the curl, both y passes): the strided
+// FFT pass configuration, 16 values per thread, 16 k_z columns per tile
+// (128-byte row segments), 32 warps per SM at <= 64 registers.
 template <int N>
 struct NXCfg {
+  static constexpr int G = N < 16 ? N : 16;
+  static constexpr int S = N / G;
+  static constexpr int T = S <= 16 ? 16 : (S <= 64 ? 16 : 1024 / S);
+  static constexpr int THREADS = T * S;
+  static constexpr int MINB = THREADS <= 512 ? (THREADS <= 256 ? 4 : 2) : 1;
+  static constexpr size_t SMEM = sizeof(float2) * (size_t)N * T;
+};
+
+// 2./4. y pass, columns (x, k_z < kc), blockIdx -> (field, x, k_z tile).
+//    SIGN=+1: only kept k_y rows are read, every y row is written;
+//    SIGN=-1: every y row is read, only kept k_y rows are written.
+template <int N, int SIGN>
+__global__ void __launch_bounds__(NXCfg<N>::THREADS, NXCfg<N>::MINB)
+    k_ns_ypass(float2* w, NSGeom g, int ktiles, const float2* __restrict__ tw, int twlog) {
+  using C = NXCfg<N>;
+  constexpr int G = C::G, S = C::S, T = C::T;
+  extern __shared__ float2 smn[];
+  const int c = threadIdx.x % T, j = threadIdx.x / T;
+  const int kt = blockIdx.x % ktiles;
+  const int rest = blockIdx.x / ktiles;
+  const int x = rest % N;
+  const int f = rest / N;
+  const int kz = kt * T + c;
+  const bool valid = kz < g.kc;
+  float2* base = w + f * g.M + (long long)x * N * g.h1 + kz;
+  float2 v[G];
+#pragma unroll
+  for (int m = 0; m < G; ++m) {
+    const int pos = j + m * S;
+    const bool rd = valid && (SIGN < 0 || kept_xy(pos, N, g.kd));
+    v[m] = rd ? base[(long long)pos * g.h1] : make_float2(0.f, 0.f);
+  }
+  fft_line<N, G, SIGN>(v, j, ColX<T>{smn, c}, tw, twlog);
+  if (valid) {
+#pragma unroll
+    for (int m = 0; m < G; ++m) {
+      const int pos = j + m * S;
+      if (SIGN > 0 || kept_xy(pos, N, g.kd)) base[(long long)pos * g.h1] = v[m];
+    }
+  }
+}
+
+// Forward x pass (three fields held at once): 8 values per thread.
+template <int N>
+struct NFCfg {
   static constexpr int G = N < 8 ? N : 8;
   static constexpr int S = N / G;
   static constexpr int T = S >= 32 ? (S == 32 ? 16 : (S == 64 ? 8 : 4)) : 16;
@@ -65,10 +113,10 @@ struct NXCfg {
 //    omega_z = D_y - i k_y U_x   (five transforms instead of six).
 //    Output field order: u_x, u_y, u_z, omega_x, omega_y, omega_z.
 template <int N>
-__global__ void __launch_bounds__(NXCfg<N>::THREADS)
+__global__ void __launch_bounds__(NFCfg<N>::THREADS)
     k_ns_invx(const float2* __restrict__ u, float2* __restrict__ w, NSGeom g, int ktiles,
               const float2* __restrict__ tw, int twlog) {
-  using C = NXCfg<N>;
+  using C = NFCfg<N>;
   constexpr int G = C::G, S = C::S, T = C::T;
   extern __shared__ float2 smn[];
   const int c = threadIdx.x % T, j = threadIdx.x / T;
@@ -119,40 +167,6 @@ __global__ void __launch_bounds__(NXCfg<N>::THREADS)
   for (int m = 0; m < G; ++m)
     b[m] = make_float2(-(ky * b[m].y - kzf * a[m].y), ky * b[m].x - kzf * a[m].x);  // omega_x
   store(3, b);
-}
-
-// 2./4. y pass on `nf` fields, columns (x, k_z < kc).  SIGN=+1: only kept k_y
-// rows are read, every y row is written; SIGN=-1: every y row is read, only
-// kept k_y rows are written.
-template <int N, int SIGN>
-__global__ void __launch_bounds__(NXCfg<N>::THREADS)
-    k_ns_ypass(float2* w, NSGeom g, int ktiles, const float2* __restrict__ tw, int twlog) {
-  using C = NXCfg<N>;
-  constexpr int G = C::G, S = C::S, T = C::T;
-  extern __shared__ float2 smn[];
-  const int c = threadIdx.x % T, j = threadIdx.x / T;
-  const int kt = blockIdx.x % ktiles;
-  const int rest = blockIdx.x / ktiles;
-  const int x = rest % N;
-  const int f = rest / N;
-  const int kz = kt * T + c;
-  const bool valid = kz < g.kc;
-  float2* base = w + f * g.M + (long long)x * N * g.h1 + kz;
-  float2 v[G];
-#pragma unroll
-  for (int m = 0; m < G; ++m) {
-    const int pos = j + m * S;
-    const bool rd = valid && (SIGN < 0 || kept_xy(pos, N, g.kd));
-    v[m] = rd ? base[(long long)pos * g.h1] : make_float2(0.f, 0.f);
-  }
-  fft_line<N, G, SIGN>(v, j, ColX<T>{smn, c}, tw, twlog);
-  if (valid) {
-#pragma unroll
-    for (int m = 0; m < G; ++m) {
-      const int pos = j + m * S;
-      if (SIGN > 0 || kept_xy(pos, N, g.kd)) base[(long long)pos * g.h1] = v[m];
-    }
-  }
 }
 
 // ------------------------------------------------------------- z product ---
@@ -251,11 +265,11 @@ struct NSUpdate {
 //    STAGE1: out = E (u0 + dt N)                      (out = u1)
 //    STAGE2: out = 1/2 E u0 + 1/2 (u1 + dt N)         (out = u0, in place)
 template <int N>
-__global__ void __launch_bounds__(NXCfg<N>::THREADS)
+__global__ void __launch_bounds__(NFCfg<N>::THREADS)
     k_ns_fwdx(const float2* __restrict__ nh, const float2* u0, const float2* u1, float2* out,
               NSGeom g, int ktiles, NSUpdate upd, int mode, const float2* __restrict__ tw,
               int twlog) {
-  using C = NXCfg<N>;
+  using C = NFCfg<N>;
   constexpr int G = C::G, S = C::S, T = C::T;
   extern __shared__ float2 smn[];
   const int c = threadIdx.x % T, j = threadIdx.x / T;
@@ -559,14 +573,14 @@ struct NSLaunch {
     static std::once_flag once;
     static cudaError_t err = cudaSuccess;
     std::call_once(once, [] {
-      const int sm = (int)NXCfg<N>::SMEM;
-      err = cudaFuncSetAttribute(k_ns_invx<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+      const int sx = (int)NXCfg<N>::SMEM, sf = (int)NFCfg<N>::SMEM;
+      err = cudaFuncSetAttribute(k_ns_invx<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, sf);
       if (err == cudaSuccess)
-        err = cudaFuncSetAttribute(k_ns_ypass<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        err = cudaFuncSetAttribute(k_ns_ypass<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sx);
       if (err == cudaSuccess)
-        err = cudaFuncSetAttribute(k_ns_ypass<N, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        err = cudaFuncSetAttribute(k_ns_ypass<N, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sx);
       if (err == cudaSuccess)
-        err = cudaFuncSetAttribute(k_ns_fwdx<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        err = cudaFuncSetAttribute(k_ns_fwdx<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, sf);
     });
     return err;
   }
@@ -575,19 +589,21 @@ struct NSLaunch {
   static cudaError_t rhs(fftk_plan p, const float2* u, const float2* u0, const float2* u1,
                          float2* out, const NSUpdate& upd, int mode, cudaStream_t st) {
     using X = NXCfg<N>;
+    using F = NFCfg<N>;
     using Z = NZCfg<N>;
     cudaError_t e = attrs();
     if (e != cudaSuccess) return e;
     NSWork* s = p->ns;
     const NSGeom g = s->g;
-    const int ktiles = (g.kc + X::T - 1) / X::T;
+    const int kx = (g.kc + X::T - 1) / X::T;
+    const int kf = (g.kc + F::T - 1) / F::T;
     {
       LaunchScope ls(p, KK_NS_INVX, st);
-      k_ns_invx<N><<<g.nk * ktiles, X::THREADS, X::SMEM, st>>>(u, s->w, g, ktiles, p->d_tw, p->twlog);
+      k_ns_invx<N><<<g.nk * kf, F::THREADS, F::SMEM, st>>>(u, s->w, g, kf, p->d_tw, p->twlog);
     }
     {
       LaunchScope ls(p, KK_NS_INVY, st);
-      k_ns_ypass<N, 1><<<6 * N * ktiles, X::THREADS, X::SMEM, st>>>(s->w, g, ktiles, p->d_tw, p->twlog);
+      k_ns_ypass<N, 1><<<6 * N * kx, X::THREADS, X::SMEM, st>>>(s->w, g, kx, p->d_tw, p->twlog);
     }
     {
       LaunchScope ls(p, KK_NS_Z, st);
@@ -597,12 +613,12 @@ struct NSLaunch {
     }
     {
       LaunchScope ls(p, KK_NS_FWDY, st);
-      k_ns_ypass<N, -1><<<3 * N * ktiles, X::THREADS, X::SMEM, st>>>(s->w, g, ktiles, p->d_tw, p->twlog);
+      k_ns_ypass<N, -1><<<3 * N * kx, X::THREADS, X::SMEM, st>>>(s->w, g, kx, p->d_tw, p->twlog);
     }
     {
       LaunchScope ls(p, KK_NS_FWDX, st);
-      k_ns_fwdx<N><<<g.nk * ktiles, X::THREADS, X::SMEM, st>>>(s->w, u0, u1, out, g, ktiles, upd, mode,
-                                                              p->d_tw, p->twlog);
+      k_ns_fwdx<N><<<g.nk * kf, F::THREADS, F::SMEM, st>>>(s->w, u0, u1, out, g, kf, upd, mode,
+                                                          p->d_tw, p->twlog);
     }
     return cudaGetLastError();
   }
