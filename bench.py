@@ -349,58 +349,86 @@ def run_ours(args, world, rank, local):
     return line
 
 
+def _time_pairs(fk, torch, dev, st_obj, plan, x, F, y, warm, kp):
+    st = st_obj.cuda_stream
+    for _ in range(warm):
+        fk.fftk_r2c(plan, x.data_ptr(), F.data_ptr(), 1, st)
+        fk.fftk_c2r(plan, F.data_ptr(), y.data_ptr(), 1, st)
+    torch.cuda.synchronize(dev)
+    fk.fftk_profile_enable(plan, True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st_obj)
+    for _ in range(kp):
+        fk.fftk_r2c(plan, x.data_ptr(), F.data_ptr(), 1, st)
+        fk.fftk_c2r(plan, F.data_ptr(), y.data_ptr(), 1, st)
+    e1.record(st_obj)
+    torch.cuda.synchronize(dev)
+    fk.fftk_sync(plan, st)
+    ms = e0.elapsed_time(e1) / kp
+    times = {}
+    for k in range(fk.fftk_kernel_kinds()):
+        t, cnt = fk.fftk_profile_read(plan, k)
+        if cnt:
+            times[fk.fftk_kernel_name(k)] = (t, cnt)
+    fk.fftk_profile_enable(plan, False)
+    return ms, times
+
+
 def bench_fft(fk, torch, dev, st_obj, args, hbm, peak_kind):
+    """1024^3 pair in FP32 and in split-FP16 (tensor-core radix-16 stages)."""
     n = N_FFT
     st = st_obj.cuda_stream
-    plan = fk.fftk_plan_create(n, n, n)
-    try:
-        with torch.cuda.stream(st_obj):
-            x = torch.empty((n, n, n), dtype=torch.float32, device=dev)
-            fk.fftk_fill_normal(x.data_ptr(), n**3, SEED, 0, st)
-            F = torch.empty((n, n, n // 2 + 1, 2), dtype=torch.float32, device=dev)
-            y = torch.empty_like(x)
-        for _ in range(max(3, args.warmup)):
-            fk.fftk_r2c(plan, x.data_ptr(), F.data_ptr(), 1, st)
-            fk.fftk_c2r(plan, F.data_ptr(), y.data_ptr(), 1, st)
-        torch.cuda.synchronize(dev)
-        kp = 20
-        fk.fftk_profile_enable(plan, True)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(st_obj)
-        for _ in range(kp):
-            fk.fftk_r2c(plan, x.data_ptr(), F.data_ptr(), 1, st)
-            fk.fftk_c2r(plan, F.data_ptr(), y.data_ptr(), 1, st)
-        e1.record(st_obj)
-        torch.cuda.synchronize(dev)
-        ms = e0.elapsed_time(e1) / kp
-        pb = fft_pass_bytes(n)
-        kern = {}
-        for k in range(fk.fftk_kernel_kinds()):
-            t, cnt = fk.fftk_profile_read(plan, k)
-            if cnt:
-                name = fk.fftk_kernel_name(k)
+    pb = fft_pass_bytes(n)
+    pair = sum(pb.values())
+    with torch.cuda.stream(st_obj):
+        x = torch.empty((n, n, n), dtype=torch.float32, device=dev)
+        fk.fftk_fill_normal(x.data_ptr(), n**3, SEED, 0, st)
+        F = torch.empty((n, n, n // 2 + 1, 2), dtype=torch.float32, device=dev)
+        y = torch.empty_like(x)
+    res = {}
+    F32 = None
+    for dtype, key in [(fk.FFTK_R32, "fp32"), (fk.FFTK_R32_SPLIT16, "split16")]:
+        plan = fk.fftk_plan_create(n, n, n, dtype)
+        try:
+            ms, times = _time_pairs(fk, torch, dev, st_obj, plan, x, F, y, max(3, args.warmup), 20)
+            rt = (torch.linalg.vector_norm((y - x).double()) / torch.linalg.vector_norm(x.double())).item()
+            kern = {}
+            for name, (t, cnt) in times.items():
                 avg = t / cnt
                 kern[name] = {"launches": cnt, "ms_avg": round(avg, 5),
                               "GBps": round(pb[name] / (avg * 1e-3) / 1e9, 1) if name in pb else None}
-        fk.fftk_profile_enable(plan, False)
-        rt = (torch.linalg.vector_norm((y - x).double()) / torch.linalg.vector_norm(x.double())).item()
-        pair = sum(pb.values())
-        dom = max(kern.items(), key=lambda kv: kv[1]["ms_avg"] * kv[1]["launches"])[0]
-        return {
-            "value": round(1e3 / ms, 3), "unit": "pairs/s", "ms_per_pair": round(ms, 4),
-            "config": "1024^3 FP32 real field, normal(0,1) seed 0, batch 1",
-            "pair_bytes": int(pair),
-            "frac_pair": round(pair / (ms * 1e-3) / 1e9 / hbm, 4),
-            "roofline": {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["GBps"], "peak": hbm,
-                         "unit": "GB/s", "frac": round(kern[dom]["GBps"] / hbm, 4),
-                         "traffic": measured_traffic(dom, f"fft{n}"), "peak_kind": peak_kind},
-            "kernels": kern,
-            "round_trip_rel_l2": rt,
-            "nominal_gflops": round(2 * 5 * n**3 * 3 * 10 / (ms * 1e-3) / 1e9, 1),
-        }
-    finally:
-        fk.fftk_plan_destroy(plan)
+            dom = max(kern.items(), key=lambda kv: kv[1]["ms_avg"] * kv[1]["launches"])[0]
+            r = {
+                "value": round(1e3 / ms, 3), "unit": "pairs/s", "ms_per_pair": round(ms, 4),
+                "frac_pair": round(pair / (ms * 1e-3) / 1e9 / hbm, 4),
+                "roofline": {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["GBps"], "peak": hbm,
+                             "unit": "GB/s", "frac": round(kern[dom]["GBps"] / hbm, 4),
+                             "traffic": measured_traffic(dom, f"fft{n}" if key == "fp32" else f"fft{n}s16"),
+                             "peak_kind": peak_kind},
+                "kernels": kern,
+                "round_trip_rel_l2": rt,
+            }
+            fk.fftk_r2c(plan, x.data_ptr(), F.data_ptr(), 1, st)
+            torch.cuda.synchronize(dev)
+            if key == "fp32":
+                F32 = F.clone()
+            else:
+                r["rel_l2_vs_fp32_spectrum"] = (torch.linalg.vector_norm((F - F32).double()) /
+                                                torch.linalg.vector_norm(F32.double())).item()
+            res[key] = r
+        finally:
+            fk.fftk_plan_destroy(plan)
+    del F32
+    out = dict(res["fp32"])
+    out.update({
+        "config": "1024^3 FP32 real field, normal(0,1) seed 0, batch 1",
+        "pair_bytes": int(pair),
+        "nominal_gflops": round(2 * 5 * n**3 * 3 * 10 / (out["ms_per_pair"] * 1e-3) / 1e9, 1),
+        "split16": res["split16"],
+        "split16_speedup": round(res["split16"]["value"] / res["fp32"]["value"], 4),
+    })
+    return out
 
 
 # ------------------------------------------------------ CPU oracle timing ---

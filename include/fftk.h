@@ -52,7 +52,13 @@ typedef enum {
 
 typedef enum {
   FFTK_R32 = 0,         /* FP32 data, FP32 arithmetic, FP64-built FP32 twiddles */
-  FFTK_R32_SPLIT16 = 1  /* FP32 data; radix-16 stages on tensor cores, split FP16 hi/lo operands */
+  /* FP32 data; in the y and x passes of length 256, 512, 1024 or 2048 the two
+   * radix-16 stages run on the tensor cores (tcgen05) as products of split FP16
+   * operands, x = x_hi + x_lo and W16 = W_hi + W_lo, with FP32 accumulation:
+   * (x_hi + x_lo) W_hi + x_hi W_lo (relative error ~2^-22 per stage); twiddles,
+   * power-of-two scaling, the remaining radix-2/4/8 stage and the z pass stay
+   * FP32.  Not part of the paper (it uses FFTW in double precision). */
+  FFTK_R32_SPLIT16 = 1
 } fftk_dtype;
 
 /* Human-readable name of a status code (static storage). */
@@ -180,6 +186,11 @@ fftk_status tarang_ic_random(fftk_plan p, const float *normals, void *uhat, doub
  * dev: device float[count]; seed < 2^24, field < 16, 2 count <= 2^36. */
 fftk_status fftk_fill_normal(float *dev, long long count, int seed, int field, void *cuda_stream);
 fftk_status fftk_fill_uniform(float *dev, long long count, int seed, int field, void *cuda_stream);
+
+/* Wait for the stream, then report a device-side bounded wait that expired in
+ * any kernel of this plan since the last check (FFTK_ERR_TIMEOUT; the word is
+ * cleared), or a CUDA fault (FFTK_ERR_CUDA). */
+fftk_status fftk_sync(fftk_plan p, void *cuda_stream);
 
 /* ------------------------------------------------------- instrumentation --
  * Kernel launches made by this plan since its creation. */

@@ -72,6 +72,7 @@ def lib() -> ctypes.CDLL:
             "tarang_ic_random": ([vp, vp, vp, d, d, vp], i),
             "fftk_fill_normal": ([vp, ll, i, i, vp], i),
             "fftk_fill_uniform": ([vp, ll, i, i, vp], i),
+            "fftk_sync": ([vp, vp], i),
             "fftk_launch_count": ([vp], ll),
             "fftk_profile_enable": ([vp, i], i),
             "fftk_profile_read": ([vp, i, c.POINTER(d), c.POINTER(ll)], i),
@@ -179,6 +180,10 @@ def fftk_fill_normal(dev_ptr, count: int, seed: int, field: int, stream=0) -> No
 def fftk_fill_uniform(dev_ptr, count: int, seed: int, field: int, stream=0) -> None:
     _check(lib().fftk_fill_uniform(_vp(dev_ptr), int(count), int(seed), int(field), _vp(stream)),
            "fftk_fill_uniform")
+
+
+def fftk_sync(plan: int, stream=0) -> None:
+    _check(lib().fftk_sync(_vp(plan), _vp(stream)), "fftk_sync")
 
 
 def fftk_launch_count(plan: int) -> int:

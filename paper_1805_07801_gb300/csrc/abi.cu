@@ -116,7 +116,7 @@ extern "C" const char* fftk_status_string(fftk_status s) {
 extern "C" fftk_status fftk_plan_create(int nx, int ny, int nz, fftk_dtype dtype, fftk_plan* out) {
   if (!out) return FFTK_ERR_INVALID_ARG;
   *out = nullptr;
-  if (dtype != FFTK_R32) return FFTK_ERR_INVALID_ARG;
+  if (dtype != FFTK_R32 && dtype != FFTK_R32_SPLIT16) return FFTK_ERR_INVALID_ARG;
   if (!is_pow2(nx) || !is_pow2(ny) || !is_pow2(nz) || nx > 4096 || ny > 4096 || nz > 4096 ||
       nz < 2)
     return FFTK_ERR_UNSUPPORTED_SIZE;
@@ -148,10 +148,15 @@ extern "C" fftk_status fftk_plan_create(int nx, int ny, int nz, fftk_dtype dtype
   e = cudaMalloc(&p->d_tw, sizeof(float2) * (size_t)lt);
   if (e == cudaSuccess)
     e = cudaMemcpy(p->d_tw, h.data(), sizeof(float2) * (size_t)lt, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, sizeof(int));
+  if (e == cudaSuccess && dtype == FFTK_R32_SPLIT16) e = upload_dft16_operands(p);
   if (e != cudaSuccess) {
     fftk_status s = from_cuda(e);
     cudaGetLastError();
     if (p->d_tw) cudaFree(p->d_tw);
+    if (p->d_err) cudaFree(p->d_err);
+    if (p->d_dft16) cudaFree(p->d_dft16);
     delete p;
     return s;
   }
@@ -166,6 +171,8 @@ extern "C" fftk_status fftk_plan_destroy(fftk_plan p) {
   cudaDeviceSynchronize();
   ns_free(p);
   if (p->d_tw) cudaFree(p->d_tw);
+  if (p->d_err) cudaFree(p->d_err);
+  if (p->d_dft16) cudaFree(p->d_dft16);
   if (p->ws && p->ws_owned) cudaFree(p->ws);
   delete p;
   return FFTK_OK;
@@ -188,6 +195,15 @@ extern "C" fftk_status fftk_set_workspace(fftk_plan p, void* dev_ptr, size_t byt
   return FFTK_OK;
 }
 
+// y or x pass: the split-FP16 tensor-core kernel where the plan asks for it
+// and the line length has two radix-16 stages, the FP32 kernel otherwise.
+static cudaError_t strided_pass(fftk_plan p, int L, int sign, const float2* in, float2* out,
+                                long long P, long long Q, float scale, int kind, cudaStream_t st) {
+  if (p->dtype == FFTK_R32_SPLIT16 && cpass_tc_supported(L))
+    return launch_cpass_tc(p, L, sign, in, out, P, Q, scale, kind, st);
+  return launch_cpass(p, L, sign, in, out, P, Q, scale, kind, st);
+}
+
 extern "C" fftk_status fftk_r2c(fftk_plan p, const float* in, void* out, int batch,
                                 void* cuda_stream) {
   if (!p || !in || !out || batch < 1) return FFTK_ERR_INVALID_ARG;
@@ -202,9 +218,9 @@ extern "C" fftk_status fftk_r2c(fftk_plan p, const float* in, void* out, int bat
   const bool do_y = p->ny > 1, do_x = p->nx > 1;
   cudaError_t e = launch_z_r2c(p, in, o, B * p->nx * p->ny, (do_x || do_y) ? 1.f : scale, st);
   if (e == cudaSuccess && do_y)
-    e = launch_cpass(p, p->ny, -1, o, o, B * p->nx, p->hz, do_x ? 1.f : scale, KK_Y_FWD, st);
+    e = strided_pass(p, p->ny, -1, o, o, B * p->nx, p->hz, do_x ? 1.f : scale, KK_Y_FWD, st);
   if (e == cudaSuccess && do_x)
-    e = launch_cpass(p, p->nx, -1, o, o, B, (long long)p->ny * p->hz, scale, KK_X_FWD, st);
+    e = strided_pass(p, p->nx, -1, o, o, B, (long long)p->ny * p->hz, scale, KK_X_FWD, st);
   return from_cuda(e);
 }
 
@@ -228,16 +244,30 @@ extern "C" fftk_status fftk_c2r(fftk_plan p, const void* in, float* out, int bat
       return FFTK_ERR_INVALID_ARG;
     float2* w = static_cast<float2*>(wv);
     if (do_x) {
-      e = launch_cpass(p, p->nx, +1, src, w, B, (long long)p->ny * p->hz, 1.f, KK_X_INV, st);
+      e = strided_pass(p, p->nx, +1, src, w, B, (long long)p->ny * p->hz, 1.f, KK_X_INV, st);
       src = w;
     }
     if (e == cudaSuccess && do_y) {
-      e = launch_cpass(p, p->ny, +1, src, w, B * p->nx, p->hz, 1.f, KK_Y_INV, st);
+      e = strided_pass(p, p->ny, +1, src, w, B * p->nx, p->hz, 1.f, KK_Y_INV, st);
       src = w;
     }
   }
   if (e == cudaSuccess) e = launch_z_c2r(p, src, out, B * p->nx * p->ny, st);
   return from_cuda(e);
+}
+
+extern "C" fftk_status fftk_sync(fftk_plan p, void* cuda_stream) {
+  if (!p) return FFTK_ERR_INVALID_ARG;
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(cuda_stream));
+  if (e != cudaSuccess) return from_cuda(e);
+  int err = 0;
+  e = cudaMemcpy(&err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return from_cuda(e);
+  if (err) {
+    cudaMemset(p->d_err, 0, sizeof(int));
+    return FFTK_ERR_TIMEOUT;
+  }
+  return FFTK_OK;
 }
 
 extern "C" long long fftk_launch_count(fftk_plan p) {

@@ -1,6 +1,7 @@
 // Internal declarations shared by the library's translation units.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -56,6 +57,8 @@ struct fftk_plan_s {
   int device;
   int twlog;                 // LT = 2^twlog = max(nx, ny, nz)
   float2* d_tw = nullptr;    // exp(-2 pi i m / LT), m < LT
+  __half* d_dft16 = nullptr; // split-FP16 DFT-16 operands (FFTK_R32_SPLIT16): forward, inverse
+  int* d_err = nullptr;      // device error word (bounded waits that expired)
   // c2r workspace (one complex field per batch element)
   void* ws = nullptr;
   size_t ws_bytes = 0;
@@ -91,6 +94,12 @@ cudaError_t launch_z_c2r(fftk_plan p, const float2* in, float* out, long long nl
 // in may equal out.  sign = -1 forward, +1 inverse; output multiplied by scale.
 cudaError_t launch_cpass(fftk_plan p, int L, int sign, const float2* in, float2* out, long long P,
                          long long Q, float scale, int kind, cudaStream_t st);
+
+// split-FP16 tensor-core strided pass (FFTK_R32_SPLIT16), L in {256, 512, 1024, 2048}
+bool cpass_tc_supported(int L);
+cudaError_t launch_cpass_tc(fftk_plan p, int L, int sign, const float2* in, float2* out, long long P,
+                            long long Q, float scale, int kind, cudaStream_t st);
+cudaError_t upload_dft16_operands(fftk_plan p);
 
 bool is_pow2(long long v);
 int ilog2(long long v);
