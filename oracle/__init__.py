@@ -61,6 +61,18 @@ def lib():
             L.oracle_ic_taylor_green.argtypes = [vp, c.c_int]
             L.oracle_ic_abc.argtypes = [vp, c.c_int]
             L.oracle_ic_random.argtypes = [vp, vp, c.c_int, c.c_double, c.c_double]
+            L.oracle_box_filter.argtypes = [vp, c.c_int, c.c_int, vp, vp]
+            L.oracle_gradient.argtypes = [vp, c.c_int, vp]
+            L.oracle_invariants.argtypes = [vp, vp]
+            L.oracle_invariants.restype = None
+            L.oracle_sym_eig3.argtypes = [vp, vp, vp]
+            L.oracle_sym_eig3.restype = None
+            L.oracle_mlp_forward.argtypes = [vp, vp, vp, c.c_int, c.c_int]
+            L.oracle_mlp_loss_grad.argtypes = [vp, vp, vp, c.c_int, c.c_int, vp]
+            L.oracle_mlp_loss_grad.restype = c.c_double
+            L.oracle_adam.argtypes = [vp, vp, vp, vp, c.c_int, c.c_int, c.c_double, c.c_double, c.c_double, c.c_double]
+            L.oracle_adam.restype = None
+            L.oracle_sgs_force.argtypes = [vp, c.c_int, vp]
             L.oracle_dealias.argtypes = [vp, c.c_int, c.c_int]
             L.oracle_project.argtypes = [vp, c.c_int]
             _lib = L
@@ -231,3 +243,75 @@ def project(uhat):
     u = np.array(uhat, dtype=np.complex128, order="C", copy=True)
     _check(lib().oracle_project(_ptr(u), u.shape[1]), "project")
     return u
+
+
+# ------------------------------------------------------------------ closure --
+MLP_NPARAMS = 9094
+MLP_DIMS = (5, 64, 64, 64, 6)
+
+
+def box_filter(u, factor):
+    """u: real [3][n][n][n] -> (ubar [3][m]^3, tau [6][m]^3 in order xx, yy, zz, xy, xz, yz)."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    n = u.shape[1]
+    m = n // factor
+    ubar = np.empty((3, m, m, m))
+    tau = np.empty((6, m, m, m))
+    _check(lib().oracle_box_filter(_ptr(u), n, factor, _ptr(ubar), _ptr(tau)), "box_filter")
+    return ubar, tau
+
+
+def gradient(u):
+    """A[i*3+j] = d u_i / d x_j of a real [3][m]^3 field from its 2/3-truncated spectrum."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    m = u.shape[1]
+    A = np.empty((9, m, m, m))
+    _check(lib().oracle_gradient(_ptr(u), m, _ptr(A)), "gradient")
+    return A
+
+
+def invariants(A9):
+    A9 = np.ascontiguousarray(A9, dtype=np.float64)
+    out = np.empty(5)
+    lib().oracle_invariants(_ptr(A9), _ptr(out))
+    return out
+
+
+def sym_eig3(S9):
+    S9 = np.ascontiguousarray(S9, dtype=np.float64)
+    lam = np.empty(3)
+    Q = np.empty(9)
+    lib().oracle_sym_eig3(_ptr(S9), _ptr(lam), _ptr(Q))
+    return lam, Q.reshape(3, 3)
+
+
+def mlp_forward(params, x, bf16_acts=True):
+    params = np.ascontiguousarray(params, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    B = x.shape[0]
+    y = np.empty((B, 6))
+    _check(lib().oracle_mlp_forward(_ptr(params), _ptr(x), _ptr(y), B, int(bf16_acts)), "mlp_forward")
+    return y
+
+
+def mlp_loss_grad(params, x, t, bf16_acts=True):
+    params = np.ascontiguousarray(params, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    g = np.empty(MLP_NPARAMS)
+    loss = lib().oracle_mlp_loss_grad(_ptr(params), _ptr(x), _ptr(t), x.shape[0], int(bf16_acts), _ptr(g))
+    return float(loss), g
+
+
+def adam(params, m, v, grad, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+    """In place on params, m, v (float64 arrays)."""
+    grad = np.ascontiguousarray(grad, dtype=np.float64)
+    lib().oracle_adam(_ptr(params), _ptr(m), _ptr(v), _ptr(grad), params.size, step, lr, beta1, beta2, eps)
+
+
+def sgs_force(tau):
+    tau = np.ascontiguousarray(tau, dtype=np.float64)
+    n = tau.shape[1]
+    f = np.empty((3, n, n, n // 2 + 1), dtype=np.complex128)
+    _check(lib().oracle_sgs_force(_ptr(tau), n, _ptr(f)), "sgs_force")
+    return f

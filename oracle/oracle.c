@@ -16,6 +16,7 @@
 
 #include <math.h>
 #include <stdlib.h>
+#include <stdint.h>
 #include <string.h>
 #ifdef _OPENMP
 #include <omp.h>
@@ -588,5 +589,260 @@ int oracle_ic_random(const double *normals, cplx *uhat, int n, double k0, double
   double g = sqrt(E0 / E);
   for (long m = 0; m < 3 * M; m++) uhat[m] *= g;
   free(eK);
+  return 0;
+}
+
+/* ------------------------------------------------------------ closure ---- */
+
+static const int kPairI[6] = {0, 1, 2, 0, 0, 1};
+static const int kPairJ[6] = {0, 1, 2, 1, 2, 2};
+
+int oracle_box_filter(const double *u, int n, int factor, double *ubar, double *tau) {
+  if (n < 1 || factor < 1 || n % factor) return -1;
+  const long N = n, F = factor, m = n / factor, R = N * N * N, Mc = m * m * m;
+  const double cnt = (double)(F * F * F);
+  for (long ci = 0; ci < m; ci++)
+    for (long cj = 0; cj < m; cj++)
+      for (long ck = 0; ck < m; ck++) {
+        double s[3] = {0, 0, 0}, pr[6] = {0, 0, 0, 0, 0, 0};
+        for (long a = 0; a < F; a++)
+          for (long b = 0; b < F; b++)
+            for (long c = 0; c < F; c++) {
+              const long idx = ((ci * F + a) * N + (cj * F + b)) * N + (ck * F + c);
+              for (int q = 0; q < 3; q++) s[q] += u[q * R + idx];
+              for (int p = 0; p < 6; p++) pr[p] += u[kPairI[p] * R + idx] * u[kPairJ[p] * R + idx];
+            }
+        const long cell = (ci * m + cj) * m + ck;
+        double mean[3];
+        for (int q = 0; q < 3; q++) {
+          mean[q] = s[q] / cnt;
+          ubar[q * Mc + cell] = mean[q];
+        }
+        for (int p = 0; p < 6; p++)
+          tau[p * Mc + cell] = pr[p] / cnt - mean[kPairI[p]] * mean[kPairJ[p]];
+      }
+  return 0;
+}
+
+int oracle_gradient(const double *u, int m, double *A) {
+  if (!is_pow2(m) || m < 2) return -1;
+  const long Mn = m, HZ = m / 2 + 1, M = Mn * Mn * HZ, R = Mn * Mn * Mn;
+  cplx *uh = (cplx *)malloc(sizeof(cplx) * 3 * (size_t)M);
+  cplx *g = (cplx *)malloc(sizeof(cplx) * (size_t)M);
+  if (!uh || !g) return -2;
+  for (int c = 0; c < 3; c++) oracle_rfft3(u + c * R, uh + c * M, m, m, m);
+  oracle_dealias(uh, 3, m);
+  for (int i = 0; i < 3; i++)
+    for (int j = 0; j < 3; j++) {
+      for (long a = 0; a < Mn; a++)
+        for (long b = 0; b < Mn; b++)
+          for (long c = 0; c < HZ; c++) {
+            const long idx = (a * Mn + b) * HZ + c;
+            const long k[3] = {kder(kxy(a, Mn), Mn), kder(kxy(b, Mn), Mn), kder(c, Mn)};
+            g[idx] = I * (double)k[j] * uh[i * M + idx];
+          }
+      oracle_irfft3(g, A + (i * 3 + j) * R, m, m, m);
+    }
+  free(uh);
+  free(g);
+  return 0;
+}
+
+static void mat3_mul(const double a[9], const double b[9], double c[9]) {
+  for (int i = 0; i < 3; i++)
+    for (int j = 0; j < 3; j++) {
+      double s = 0;
+      for (int k = 0; k < 3; k++) s += a[i * 3 + k] * b[k * 3 + j];
+      c[i * 3 + j] = s;
+    }
+}
+
+static double mat3_trace(const double a[9]) { return a[0] + a[4] + a[8]; }
+
+void oracle_invariants(const double A[9], double inv[5]) {
+  double S[9], R[9], S2[9], R2[9], S3[9], R2S[9], R2S2[9];
+  for (int i = 0; i < 3; i++)
+    for (int j = 0; j < 3; j++) {
+      S[i * 3 + j] = 0.5 * (A[i * 3 + j] + A[j * 3 + i]);
+      R[i * 3 + j] = 0.5 * (A[i * 3 + j] - A[j * 3 + i]);
+    }
+  mat3_mul(S, S, S2);
+  mat3_mul(R, R, R2);
+  mat3_mul(S2, S, S3);
+  mat3_mul(R2, S, R2S);
+  mat3_mul(R2, S2, R2S2);
+  inv[0] = mat3_trace(S2);
+  inv[1] = mat3_trace(R2);
+  inv[2] = mat3_trace(S3);
+  inv[3] = mat3_trace(R2S);
+  inv[4] = mat3_trace(R2S2);
+}
+
+/* Cyclic Jacobi (Golub and Van Loan, sym. Schur): zero a_pq with the rotation
+ * t = sign(theta)/(|theta| + sqrt(1 + theta^2)), theta = (a_qq - a_pp)/(2 a_pq). */
+void oracle_sym_eig3(const double S[9], double lam[3], double Q[9]) {
+  double a[9], v[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+  memcpy(a, S, sizeof(a));
+  for (int sweep = 0; sweep < 50; sweep++) {
+    const double off = a[1] * a[1] + a[2] * a[2] + a[5] * a[5];
+    if (off == 0.0) break;
+    const int pq[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+    for (int r = 0; r < 3; r++) {
+      const int p = pq[r][0], q = pq[r][1];
+      const double apq = a[p * 3 + q];
+      if (apq == 0.0) continue;
+      const double theta = (a[q * 3 + q] - a[p * 3 + p]) / (2.0 * apq);
+      const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(1.0 + theta * theta));
+      const double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+      double Jm[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1}, Jt[9], tmp[9];
+      Jm[p * 3 + p] = c;
+      Jm[q * 3 + q] = c;
+      Jm[p * 3 + q] = s;
+      Jm[q * 3 + p] = -s;
+      for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) Jt[i * 3 + j] = Jm[j * 3 + i];
+      mat3_mul(Jt, a, tmp);
+      mat3_mul(tmp, Jm, a);
+      mat3_mul(v, Jm, tmp);
+      memcpy(v, tmp, sizeof(v));
+    }
+  }
+  int order[3] = {0, 1, 2};
+  for (int i = 0; i < 3; i++)
+    for (int j = i + 1; j < 3; j++)
+      if (a[order[j] * 4] > a[order[i] * 4]) {
+        int t = order[i];
+        order[i] = order[j];
+        order[j] = t;
+      }
+  for (int k = 0; k < 3; k++) {
+    const int src = order[k];
+    lam[k] = a[src * 4];
+    int big = 0;
+    for (int i = 1; i < 3; i++)
+      if (fabs(v[i * 3 + src]) > fabs(v[big * 3 + src])) big = i;
+    const double sg = v[big * 3 + src] < 0 ? -1.0 : 1.0;
+    for (int i = 0; i < 3; i++) Q[i * 3 + k] = sg * v[i * 3 + src];
+  }
+}
+
+/* round to bfloat16 (nearest even) of the FP32 value */
+static double bf16r(double x) {
+  float f = (float)x;
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  u &= 0xFFFF0000u;
+  memcpy(&f, &u, 4);
+  return (double)f;
+}
+
+static const int kMlpDims[5] = {5, 64, 64, 64, 6};
+
+/* offsets of W_l and b_l in the flat parameter vector */
+static void mlp_offsets(int l, long *w, long *b) {
+  long o = 0;
+  for (int i = 0; i < l; i++) o += (long)kMlpDims[i + 1] * kMlpDims[i] + kMlpDims[i + 1];
+  *w = o;
+  *b = o + (long)kMlpDims[l + 1] * kMlpDims[l];
+}
+
+/* forward for one sample; acts[l] = input of layer l (as used), z[l] = pre-activation */
+static void mlp_sample(const double *prm, const double *x, int bf16, double acts[4][64], double z[4][64]) {
+  for (int i = 0; i < 5; i++) acts[0][i] = bf16 ? bf16r(x[i]) : x[i];
+  for (int l = 0; l < 4; l++) {
+    long wo, bo;
+    mlp_offsets(l, &wo, &bo);
+    const int din = kMlpDims[l], dout = kMlpDims[l + 1];
+    for (int o = 0; o < dout; o++) {
+      double s = prm[bo + o];
+      for (int i = 0; i < din; i++) s += prm[wo + (long)o * din + i] * acts[l][i];
+      z[l][o] = s;
+      if (l < 3) {
+        const double h = tanh(s);
+        acts[l + 1][o] = bf16 ? bf16r(h) : h;
+      }
+    }
+  }
+}
+
+int oracle_mlp_forward(const double *params, const double *x, double *y, int B, int bf16_acts) {
+#pragma omp parallel for schedule(static)
+  for (int b = 0; b < B; b++) {
+    double acts[4][64], z[4][64];
+    mlp_sample(params, x + 5L * b, bf16_acts, acts, z);
+    for (int o = 0; o < 6; o++) y[6L * b + o] = z[3][o];
+  }
+  return 0;
+}
+
+double oracle_mlp_loss_grad(const double *params, const double *x, const double *t, int B,
+                            int bf16_acts, double *grad) {
+  for (int i = 0; i < ORACLE_MLP_NPARAMS; i++) grad[i] = 0.0;
+  double loss = 0.0;
+  const double scale = 1.0 / (6.0 * (double)B);
+  for (int b = 0; b < B; b++) {
+    double acts[4][64], z[4][64], d[64], dn[64];
+    mlp_sample(params, x + 5L * b, bf16_acts, acts, z);
+    for (int o = 0; o < 6; o++) {
+      const double e = z[3][o] - t[6L * b + o];
+      loss += e * e * scale;
+      d[o] = 2.0 * e * scale;  /* dL/dz of the output layer */
+    }
+    for (int l = 3; l >= 0; l--) {
+      long wo, bo;
+      mlp_offsets(l, &wo, &bo);
+      const int din = kMlpDims[l], dout = kMlpDims[l + 1];
+      for (int o = 0; o < dout; o++) {
+        grad[bo + o] += d[o];
+        for (int i = 0; i < din; i++) grad[wo + (long)o * din + i] += d[o] * acts[l][i];
+      }
+      if (l > 0) {
+        /* back through the layer input acts[l] = tanh(z[l-1]); derivative from the
+           stored activation 1 - a^2 */
+        for (int i = 0; i < din; i++) {
+          double s = 0.0;
+          for (int o = 0; o < dout; o++) s += params[wo + (long)o * din + i] * d[o];
+          dn[i] = s * (1.0 - acts[l][i] * acts[l][i]);
+        }
+        memcpy(d, dn, sizeof(double) * (size_t)din);
+      }
+    }
+  }
+  return loss;
+}
+
+void oracle_adam(double *params, double *m, double *v, const double *grad, int nparam, int step,
+                 double lr, double beta1, double beta2, double eps) {
+  const double c1 = 1.0 - pow(beta1, step), c2 = 1.0 - pow(beta2, step);
+  for (int i = 0; i < nparam; i++) {
+    m[i] = beta1 * m[i] + (1.0 - beta1) * grad[i];
+    v[i] = beta2 * v[i] + (1.0 - beta2) * grad[i] * grad[i];
+    params[i] -= lr * (m[i] / c1) / (sqrt(v[i] / c2) + eps);
+  }
+}
+
+int oracle_sgs_force(const double *tau, int n, cplx *fhat) {
+  if (!is_pow2(n) || n < 2) return -1;
+  const long N = n, HZ = n / 2 + 1, M = N * N * HZ, R = N * N * N;
+  cplx *th = (cplx *)malloc(sizeof(cplx) * 6 * (size_t)M);
+  if (!th) return -2;
+  for (int p = 0; p < 6; p++) oracle_rfft3(tau + p * R, th + p * M, n, n, n);
+  /* component index of the symmetric pair (i, j) */
+  const int pidx[3][3] = {{0, 3, 4}, {3, 1, 5}, {4, 5, 2}};
+  for (long a = 0; a < N; a++)
+    for (long b = 0; b < N; b++)
+      for (long c = 0; c < HZ; c++) {
+        const long idx = (a * N + b) * HZ + c;
+        const double k[3] = {(double)kder(kxy(a, N), N), (double)kder(kxy(b, N), N), (double)kder(c, N)};
+        for (int i = 0; i < 3; i++) {
+          cplx s = 0;
+          for (int j = 0; j < 3; j++) s += k[j] * th[pidx[i][j] * M + idx];
+          fhat[i * M + idx] = -I * s;
+        }
+      }
+  oracle_dealias(fhat, 3, n);
+  oracle_project(fhat, n);
+  free(th);
   return 0;
 }

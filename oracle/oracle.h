@@ -80,6 +80,48 @@ int oracle_ic_random(const double *normals, ocplx *uhat, int n, double k0, doubl
 int oracle_dealias(ocplx *fhat, int nfields, int n);
 int oracle_project(ocplx *uhat, int n);
 
+/* ------------------------------------------------------------ closure ----
+ * Learned subgrid-stress closure (not in the paper; the task's closure
+ * workload).  Reading: the MLP maps the 5 invariants of the filtered velocity
+ * gradient to the 6 components of tau in the eigenframe of the filtered
+ * strain rate S (sorted eigenvalues, each eigenvector's largest-magnitude
+ * component positive), tau = Q tau' Q^T. */
+
+/* Box filter: means over factor^3 blocks of u_i and u_i u_j.  u: real
+ * [3][n][n][n]; ubar: [3][m][m][m]; tau: [6][m][m][m] = <u_i u_j> - ubar_i ubar_j
+ * in the order xx, yy, zz, xy, xz, yz (m = n / factor). */
+int oracle_box_filter(const double *u, int n, int factor, double *ubar, double *tau);
+
+/* Velocity gradient A[i*3+j] = d u_i / d x_j of a real field u[3][m][m][m] on
+ * the 2 pi-periodic grid, from the 2/3-truncated spectrum. A: [9][m][m][m]. */
+int oracle_gradient(const double *u, int m, double *A);
+
+/* Invariants of S = (A + A^T)/2, R = (A - A^T)/2 at one point:
+ * tr S^2, tr R^2, tr S^3, tr R^2 S, tr R^2 S^2. */
+void oracle_invariants(const double A[9], double inv[5]);
+
+/* Symmetric 3x3 eigendecomposition by cyclic Jacobi rotations: lam
+ * descending, eigenvector k in column k of Q (Q[row*3+k]), largest-magnitude
+ * component of each column positive. */
+void oracle_sym_eig3(const double S[9], double lam[3], double Q[9]);
+
+/* MLP 5 -> 64 -> 64 -> 64 -> 6, tanh on the three hidden layers.  params
+ * (9094): W1[64][5], b1[64], W2[64][64], b2[64], W3[64][64], b3[64],
+ * W4[6][64], b4[6].  bf16_acts != 0 rounds each layer's input (x, h1, h2, h3)
+ * to bfloat16 (round to nearest even of the FP32 value) before use. */
+#define ORACLE_MLP_NPARAMS 9094
+int oracle_mlp_forward(const double *params, const double *x, double *y, int B, int bf16_acts);
+/* Mean-squared-error loss (1/(6B)) sum (y - t)^2 and its gradient. */
+double oracle_mlp_loss_grad(const double *params, const double *x, const double *t, int B,
+                            int bf16_acts, double *grad);
+/* One Adam step (Kingma and Ba 2015), step counted from 1. */
+void oracle_adam(double *params, double *m, double *v, const double *grad, int nparam, int step,
+                 double lr, double beta1, double beta2, double eps);
+
+/* SGS force of a real stress tau[6][n][n][n] (order xx, yy, zz, xy, xz, yz):
+ * s_i = -i k_j tau_hat_ij, 2/3-truncated and projected.  fhat: [3][n][n][n/2+1]. */
+int oracle_sgs_force(const double *tau, int n, ocplx *fhat);
+
 #ifdef __cplusplus
 }
 #endif
