@@ -104,12 +104,29 @@ fftk_status fftk_c2r(fftk_plan p, const void *in, float *out, int batch, void *c
  * transform of the real velocity.  Modes outside the 2/3-rule set
  * (3|k_x| < n and 3|k_y| < n and 3|k_z| < n) must be zero on entry and stay
  * zero; the solver never reads them. */
+/* Learned subgrid-stress model (not in the paper; see tarang_mlp_*): the
+ * network maps the 5 invariants of the resolved velocity gradient A
+ * (tr S^2, tr R^2, tr S^3, tr R^2 S, tr R^2 S^2 with S, R the symmetric and
+ * antisymmetric parts of A) to the stress in the eigenframe Q of S
+ * (eigenvalues descending, each eigenvector's largest-magnitude component
+ * positive); tau = Q tau' Q^T. */
+typedef struct {
+  const float *params;  /* device, 9094 FP32 values (layout of tarang_mlp_forward) */
+  float in_shift[5];    /* network input x = (invariant - in_shift) * in_scale */
+  float in_scale[5];
+  float out_scale[6];   /* tau' = output * out_scale, order xx, yy, zz, xy, xz, yz */
+} tarang_sgs_model;
+
 typedef struct {
   double nu;        /* kinematic viscosity */
   double dt;        /* time step (tarang_ns_step only) */
   double force_eps; /* constant injected power; 0 disables forcing */
   int force_k2min;  /* forced modes: force_k2min <= |k|^2 <= force_k2max */
   int force_k2max;
+  /* NULL = resolved simulation.  Otherwise the right-hand side gains the
+   * subgrid force P[-i k_j tau_hat_ij] of the model's stress, evaluated per
+   * grid point from the current state's gradient (fused inference). */
+  const tarang_sgs_model *sgs_model;
 } tarang_params;
 
 /* Nonlinear right-hand side without the viscous term:
@@ -186,6 +203,48 @@ fftk_status tarang_ic_random(fftk_plan p, const float *normals, void *uhat, doub
  * dev: device float[count]; seed < 2^24, field < 16, 2 count <= 2^36. */
 fftk_status fftk_fill_normal(float *dev, long long count, int seed, int field, void *cuda_stream);
 fftk_status fftk_fill_uniform(float *dev, long long count, int seed, int field, void *cuda_stream);
+
+/* ------------------------------------------------------ learned closure --
+ * Closure data from a resolved state (the task's closure workload; no
+ * counterpart in the paper).
+ *
+ * Box filter of the real velocity of uhat (plan n^3, cubic, n >= 32) over
+ * factor^3 blocks (factor a power of two <= 32): ubar[3][m^3] (m = n/factor)
+ * and tau[6][m^3] = <u_i u_j> - ubar_i ubar_j (xx, yy, zz, xy, xz, yz), block
+ * sums in FP64.  Synchronises; allocates its scratch. */
+fftk_status tarang_box_filter(fftk_plan p, const void *uhat, int factor, float *ubar, float *tau,
+                              void *cuda_stream);
+
+/* Network features on a coarse grid (plan m^3): the gradient A_ij = d_j ubar_i
+ * of the 2/3-truncated transform of ubar[3][m^3] (computed spectrally),
+ * inv[5][m^3] (the invariants of tarang_sgs_model), frame[9][m^3] (Q, row
+ * major per point) and, when tau is given, tau_frame[6][m^3] = Q^T tau Q.
+ * Synchronises; allocates its scratch. */
+fftk_status tarang_closure_features(fftk_plan p, const float *ubar, const float *tau, float *inv,
+                                    float *frame, float *tau_frame, void *cuda_stream);
+
+/* MLP 5 -> 64 -> 64 -> 64 -> 6 with tanh on the hidden layers.  params: 9094
+ * FP32 values W1[64][5], b1[64], W2[64][64], b2[64], W3[64][64], b3[64],
+ * W4[6][64], b4[6].  Each layer's input (x, h1, h2, h3) is rounded to
+ * bfloat16; products and sums are FP32.  x: [B][5], y and targets t: [B][6].
+ * A context owns the per-block gradient partials for up to max_batch samples;
+ * gradients are reduced in a fixed order (bitwise reproducible). */
+typedef struct tarang_mlp_s *tarang_mlp;
+fftk_status tarang_mlp_create(int max_batch, tarang_mlp *out);
+fftk_status tarang_mlp_destroy(tarang_mlp m);
+fftk_status tarang_mlp_forward(tarang_mlp m, const float *params, const float *x, float *y, int B,
+                               void *cuda_stream);
+/* Mean-squared-error loss (1/(6B)) sum (y - t)^2 (device double, may be NULL)
+ * and its gradient grad[9094] (device). */
+fftk_status tarang_mlp_loss_grad(tarang_mlp m, const float *params, const float *x, const float *t,
+                                 int B, float *grad, double *loss, void *cuda_stream);
+/* One Adam step (Kingma and Ba 2015; step counted from 1) on 9094 values. */
+fftk_status tarang_mlp_adam(float *params, float *m, float *v, const float *grad, int step,
+                            float lr, float beta1, float beta2, float eps, void *cuda_stream);
+/* loss_grad followed by Adam (beta1 0.9, beta2 0.999, eps 1e-8). */
+fftk_status tarang_mlp_train_step(tarang_mlp m, float *params, float *adam_m, float *adam_v, int step,
+                                  const float *x, const float *t, int B, float lr, double *loss,
+                                  void *cuda_stream);
 
 /* Wait for the stream, then report a device-side bounded wait that expired in
  * any kernel of this plan since the last check (FFTK_ERR_TIMEOUT; the word is

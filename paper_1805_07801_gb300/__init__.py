@@ -34,6 +34,15 @@ class FFTKError(RuntimeError):
         super().__init__(f"{where}: {fftk_status_string(status)} ({status})")
 
 
+class tarang_sgs_model(ctypes.Structure):
+    _fields_ = [
+        ("params", ctypes.c_void_p),
+        ("in_shift", ctypes.c_float * 5),
+        ("in_scale", ctypes.c_float * 5),
+        ("out_scale", ctypes.c_float * 6),
+    ]
+
+
 class tarang_params(ctypes.Structure):
     _fields_ = [
         ("nu", ctypes.c_double),
@@ -41,6 +50,7 @@ class tarang_params(ctypes.Structure):
         ("force_eps", ctypes.c_double),
         ("force_k2min", ctypes.c_int),
         ("force_k2max", ctypes.c_int),
+        ("sgs_model", ctypes.POINTER(tarang_sgs_model)),
     ]
 
 
@@ -73,6 +83,14 @@ def lib() -> ctypes.CDLL:
             "fftk_fill_normal": ([vp, ll, i, i, vp], i),
             "fftk_fill_uniform": ([vp, ll, i, i, vp], i),
             "fftk_sync": ([vp, vp], i),
+            "tarang_box_filter": ([vp, vp, i, vp, vp, vp], i),
+            "tarang_closure_features": ([vp, vp, vp, vp, vp, vp, vp], i),
+            "tarang_mlp_create": ([i, c.POINTER(vp)], i),
+            "tarang_mlp_destroy": ([vp], i),
+            "tarang_mlp_forward": ([vp, vp, vp, vp, i, vp], i),
+            "tarang_mlp_loss_grad": ([vp, vp, vp, vp, i, vp, vp, vp], i),
+            "tarang_mlp_adam": ([vp, vp, vp, vp, i, c.c_float, c.c_float, c.c_float, c.c_float, vp], i),
+            "tarang_mlp_train_step": ([vp, vp, vp, vp, i, vp, vp, i, c.c_float, vp, vp], i),
             "fftk_launch_count": ([vp], ll),
             "fftk_profile_enable": ([vp, i], i),
             "fftk_profile_read": ([vp, i, c.POINTER(d), c.POINTER(ll)], i),
@@ -126,8 +144,23 @@ def fftk_c2r(plan: int, in_ptr, out_ptr, batch: int = 1, stream=0) -> None:
     _check(lib().fftk_c2r(_vp(plan), _vp(in_ptr), _vp(out_ptr), batch, _vp(stream)), "fftk_c2r")
 
 
-def make_params(nu: float, dt: float = 0.0, force_eps: float = 0.0, force_k2=(1, 4)) -> tarang_params:
-    return tarang_params(float(nu), float(dt), float(force_eps), int(force_k2[0]), int(force_k2[1]))
+def make_params(nu: float, dt: float = 0.0, force_eps: float = 0.0, force_k2=(1, 4), sgs_model=None) -> tarang_params:
+    p = tarang_params(float(nu), float(dt), float(force_eps), int(force_k2[0]), int(force_k2[1]))
+    if sgs_model is not None:
+        p.sgs_model = ctypes.pointer(sgs_model)
+        p._model_ref = sgs_model  # keep alive with the params
+    return p
+
+
+def make_sgs_model(params_ptr, in_shift, in_scale, out_scale) -> tarang_sgs_model:
+    m = tarang_sgs_model()
+    m.params = int(params_ptr)
+    for i in range(5):
+        m.in_shift[i] = float(in_shift[i])
+        m.in_scale[i] = float(in_scale[i])
+    for i in range(6):
+        m.out_scale[i] = float(out_scale[i])
+    return m
 
 
 def tarang_ns_rhs(plan: int, uhat_ptr, nhat_ptr, params: tarang_params, stream=0) -> None:
@@ -180,6 +213,49 @@ def fftk_fill_normal(dev_ptr, count: int, seed: int, field: int, stream=0) -> No
 def fftk_fill_uniform(dev_ptr, count: int, seed: int, field: int, stream=0) -> None:
     _check(lib().fftk_fill_uniform(_vp(dev_ptr), int(count), int(seed), int(field), _vp(stream)),
            "fftk_fill_uniform")
+
+
+def tarang_box_filter(plan: int, uhat_ptr, factor: int, ubar_ptr, tau_ptr, stream=0) -> None:
+    _check(lib().tarang_box_filter(_vp(plan), _vp(uhat_ptr), int(factor), _vp(ubar_ptr), _vp(tau_ptr), _vp(stream)),
+           "tarang_box_filter")
+
+
+def tarang_closure_features(plan: int, ubar_ptr, tau_ptr, inv_ptr, frame_ptr, tau_frame_ptr, stream=0) -> None:
+    _check(lib().tarang_closure_features(_vp(plan), _vp(ubar_ptr), _vp(tau_ptr), _vp(inv_ptr), _vp(frame_ptr),
+                                         _vp(tau_frame_ptr), _vp(stream)), "tarang_closure_features")
+
+
+def tarang_mlp_create(max_batch: int) -> int:
+    out = ctypes.c_void_p()
+    _check(lib().tarang_mlp_create(int(max_batch), ctypes.byref(out)), "tarang_mlp_create")
+    return out.value
+
+
+def tarang_mlp_destroy(m: int) -> None:
+    _check(lib().tarang_mlp_destroy(_vp(m)), "tarang_mlp_destroy")
+
+
+def tarang_mlp_forward(m: int, params_ptr, x_ptr, y_ptr, B: int, stream=0) -> None:
+    _check(lib().tarang_mlp_forward(_vp(m), _vp(params_ptr), _vp(x_ptr), _vp(y_ptr), int(B), _vp(stream)),
+           "tarang_mlp_forward")
+
+
+def tarang_mlp_loss_grad(m: int, params_ptr, x_ptr, t_ptr, B: int, grad_ptr, loss_ptr, stream=0) -> None:
+    _check(lib().tarang_mlp_loss_grad(_vp(m), _vp(params_ptr), _vp(x_ptr), _vp(t_ptr), int(B), _vp(grad_ptr),
+                                      _vp(loss_ptr), _vp(stream)), "tarang_mlp_loss_grad")
+
+
+def tarang_mlp_adam(params_ptr, m_ptr, v_ptr, grad_ptr, step: int, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
+                    stream=0) -> None:
+    _check(lib().tarang_mlp_adam(_vp(params_ptr), _vp(m_ptr), _vp(v_ptr), _vp(grad_ptr), int(step), lr, beta1,
+                                 beta2, eps, _vp(stream)), "tarang_mlp_adam")
+
+
+def tarang_mlp_train_step(m: int, params_ptr, m_ptr, v_ptr, step: int, x_ptr, t_ptr, B: int, lr: float,
+                          loss_ptr, stream=0) -> None:
+    _check(lib().tarang_mlp_train_step(_vp(m), _vp(params_ptr), _vp(m_ptr), _vp(v_ptr), int(step), _vp(x_ptr),
+                                       _vp(t_ptr), int(B), float(lr), _vp(loss_ptr), _vp(stream)),
+           "tarang_mlp_train_step")
 
 
 def fftk_sync(plan: int, stream=0) -> None:

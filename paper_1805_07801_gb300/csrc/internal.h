@@ -100,6 +100,14 @@ bool cpass_tc_supported(int L);
 cudaError_t launch_cpass_tc(fftk_plan p, int L, int sign, const float2* in, float2* out, long long P,
                             long long Q, float scale, int kind, cudaStream_t st);
 cudaError_t upload_dft16_operands(fftk_plan p);
+}  // namespace fftk
+
+struct fftk_sgs_work;
+namespace fftk {
+// subgrid force of a learned model for the state u: points *out at P[-i k_j tau_hat_ij]
+cudaError_t sgs_term(fftk_plan p, fftk_sgs_work** w, const float2* u, const tarang_sgs_model* model,
+                     cudaStream_t st, const float2** out);
+void sgs_free(fftk_sgs_work* w);
 
 bool is_pow2(long long v);
 int ilog2(long long v);

@@ -267,8 +267,8 @@ struct NSUpdate {
 template <int N>
 __global__ void __launch_bounds__(NFCfg<N>::THREADS)
     k_ns_fwdx(const float2* __restrict__ nh, const float2* u0, const float2* u1, float2* out,
-              NSGeom g, int ktiles, NSUpdate upd, int mode, const float2* __restrict__ tw,
-              int twlog) {
+              NSGeom g, int ktiles, NSUpdate upd, int mode, const float2* __restrict__ extra,
+              const float2* __restrict__ tw, int twlog) {
   using C = NFCfg<N>;
   constexpr int G = C::G, S = C::S, T = C::T;
   extern __shared__ float2 smn[];
@@ -314,6 +314,11 @@ __global__ void __launch_bounds__(NFCfg<N>::THREADS)
       nx = csub(nx, cscale(kn, fkx));
       ny = csub(ny, cscale(kn, fky));
       nz = csub(nz, cscale(kn, fkz));
+    }
+    if (extra) {  // subgrid force, already dealiased and projected
+      nx = cadd(nx, extra[idx]);
+      ny = cadd(ny, extra[idx + g.M]);
+      nz = cadd(nz, extra[idx + 2 * g.M]);
     }
     const bool forced = gforce != 0.f && k2 >= upd.k2min && k2 <= upd.k2max;
     const float2* ucur = (mode == NS_STAGE2) ? u1 : u0;
@@ -493,6 +498,7 @@ struct NSWork {
   double* part = nullptr;  // diag partials
   double* dout = nullptr;  // diag result (device)
   double* hout = nullptr;  // diag result (pinned host)
+  fftk_sgs_work* sgs = nullptr;  // learned-closure scratch
   int kmax = 0;
   int diag_smem = 0;
 };
@@ -587,7 +593,8 @@ struct NSLaunch {
 
   // One evaluation of N(u) followed by the update selected by `mode`.
   static cudaError_t rhs(fftk_plan p, const float2* u, const float2* u0, const float2* u1,
-                         float2* out, const NSUpdate& upd, int mode, cudaStream_t st) {
+                         float2* out, const NSUpdate& upd, int mode, const float2* extra,
+                         cudaStream_t st) {
     using X = NXCfg<N>;
     using F = NFCfg<N>;
     using Z = NZCfg<N>;
@@ -618,7 +625,7 @@ struct NSLaunch {
     {
       LaunchScope ls(p, KK_NS_FWDX, st);
       k_ns_fwdx<N><<<g.nk * kf, F::THREADS, F::SMEM, st>>>(s->w, u0, u1, out, g, kf, upd, mode,
-                                                          p->d_tw, p->twlog);
+                                                          extra, p->d_tw, p->twlog);
     }
     return cudaGetLastError();
   }
@@ -627,11 +634,12 @@ struct NSLaunch {
 #define NS_SIZES(X) X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024)
 
 static cudaError_t ns_rhs_dispatch(fftk_plan p, const float2* u, const float2* u0, const float2* u1,
-                                   float2* out, const NSUpdate& upd, int mode, cudaStream_t st) {
+                                   float2* out, const NSUpdate& upd, int mode, const float2* extra,
+                                   cudaStream_t st) {
   switch (p->nx) {
 #define CASE(n) \
   case n:       \
-    return NSLaunch<n>::rhs(p, u, u0, u1, out, upd, mode, st);
+    return NSLaunch<n>::rhs(p, u, u0, u1, out, upd, mode, extra, st);
     NS_SIZES(CASE)
 #undef CASE
   }
@@ -670,6 +678,7 @@ static fftk_status ns_check(fftk_plan p, const tarang_params* prm, bool need_dt)
   if (p->nx < 8 || p->nx > 1024) return FFTK_ERR_UNSUPPORTED_SIZE;
   if (!(prm->nu >= 0.0) || !std::isfinite(prm->nu)) return FFTK_ERR_INVALID_ARG;
   if (need_dt && (!(prm->dt > 0.0) || !std::isfinite(prm->dt))) return FFTK_ERR_INVALID_ARG;
+  if (prm->sgs_model && !prm->sgs_model->params) return FFTK_ERR_INVALID_ARG;
   if (prm->force_eps != 0.0) {
     const int kd = (p->nx - 1) / 3;
     if (!(prm->force_eps > 0.0) || prm->force_k2min < 1 || prm->force_k2max < prm->force_k2min ||
@@ -693,6 +702,7 @@ void ns_free(fftk_plan p) {
   cudaFree(s->part);
   cudaFree(s->dout);
   if (s->hout) cudaFreeHost(s->hout);
+  sgs_free(s->sgs);
   delete s;
   p->ns = nullptr;
 }
@@ -715,7 +725,9 @@ extern "C" fftk_status tarang_ns_rhs(fftk_plan p, const void* uhat, void* nhat,
   NSUpdate upd{p->ns->etab, p->ns->ef, prm->force_eps, prm->force_k2min, prm->force_k2max, 0.f,
                (float)(1.0 / ((double)g.n * g.n * g.n))};
   if (e == cudaSuccess && prm->force_eps > 0.0) e = forced_energy(p, u, prm, st);
-  if (e == cudaSuccess) e = ns_rhs_dispatch(p, u, u, nullptr, out, upd, NS_RHS, st);
+  const float2* extra = nullptr;
+  if (e == cudaSuccess && prm->sgs_model) e = sgs_term(p, &p->ns->sgs, u, prm->sgs_model, st, &extra);
+  if (e == cudaSuccess) e = ns_rhs_dispatch(p, u, u, nullptr, out, upd, NS_RHS, extra, st);
   return from_cuda(e);
 }
 
@@ -755,10 +767,13 @@ extern "C" fftk_status tarang_ns_step(fftk_plan p, void* uhat, const tarang_para
                (float)(1.0 / ((double)g.n * g.n * g.n))};
   cudaError_t e = cudaSuccess;
   for (int it = 0; it < nsteps && e == cudaSuccess; ++it) {
+    const float2* extra = nullptr;
     if (prm->force_eps > 0.0) e = forced_energy(p, u, prm, st);
-    if (e == cudaSuccess) e = ns_rhs_dispatch(p, u, u, nullptr, w->u1, upd, NS_STAGE1, st);
+    if (e == cudaSuccess && prm->sgs_model) e = sgs_term(p, &w->sgs, u, prm->sgs_model, st, &extra);
+    if (e == cudaSuccess) e = ns_rhs_dispatch(p, u, u, nullptr, w->u1, upd, NS_STAGE1, extra, st);
     if (e == cudaSuccess && prm->force_eps > 0.0) e = forced_energy(p, w->u1, prm, st);
-    if (e == cudaSuccess) e = ns_rhs_dispatch(p, w->u1, u, w->u1, u, upd, NS_STAGE2, st);
+    if (e == cudaSuccess && prm->sgs_model) e = sgs_term(p, &w->sgs, w->u1, prm->sgs_model, st, &extra);
+    if (e == cudaSuccess) e = ns_rhs_dispatch(p, w->u1, u, w->u1, u, upd, NS_STAGE2, extra, st);
   }
   if (e != cudaSuccess) return from_cuda(e);
   if (diag_host) return tarang_diag(p, u, prm->nu, diag_host, cuda_stream);

@@ -46,8 +46,8 @@ def main():
     u = oracle.ns_step(u64.astype(np.complex128), cfg["nu"], cfg["dt"], cfg["steps"])
     E, eps, EK = oracle.diag(u, cfg["nu"])
     out = dict(
-        description="FP64 oracle, 512^3 decaying turbulence after 100 RK2-IF steps (config of the "
-        "north-star 512^3 workload); written by make_ns512_golden.py from oracle/ only",
+        description=f"FP64 oracle, {n}^3 decaying turbulence after {cfg['steps']} RK2-IF steps; "
+        "written by make_ns512_golden.py from oracle/ only",
         config=cfg,
         ic_checksum=checksum(u64),
         ic=dict(E=E0, eps=eps0, EK=EK0.tolist()),

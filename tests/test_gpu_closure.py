@@ -1,0 +1,245 @@
+"""GPU parity of the learned-closure kernels against the FP64 oracle: box
+filter and closure data, network features, the MLP forward / gradient / Adam
+kernels, and the subgrid force fused into the right-hand side.
+
+Tolerances: FP32 transforms carry ~1e-6 relative error into the real fields;
+the box filter's tau subtracts two block means, so it is held to 1e-5 of
+<u_i u_j>; invariants (up to fourth order in the gradient) to 1e-4 of their
+scale.  The network rounds each layer's input to bfloat16 on both sides; an
+FP32 pre-activation landing on the other side of a rounding boundary than the
+FP64 one flips one activation by 2^-8 relative, so outputs and gradients are
+held to relative L2 1e-3.
+"""
+import numpy as np
+import pytest
+
+import synth
+from gpu_helpers import empty_c64, empty_real, from_dev_c64, rel_l2, stream, sync, to_dev_c64, to_dev_real
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fk():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1805_07801_gb300 import build as b
+
+    b.build()
+    import paper_1805_07801_gb300 as m
+
+    return m
+
+
+def _ic(oracle_mod, n, seed=0, k0=3.0):
+    return oracle_mod.ic_random(synth.normal_fields(seed, 3, (n, n, n)), k0=k0, E0=0.5).astype(np.complex64)
+
+
+def _f32(a):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to("cuda:0")
+
+
+@pytest.mark.parametrize("n,factor", [(64, 8), (32, 4)])
+def test_box_filter_matches_oracle(fk, oracle_mod, n, factor):
+    u = _ic(oracle_mod, n, seed=1, k0=4.0)
+    m = n // factor
+    plan = fk.fftk_plan_create(n, n, n)
+    try:
+        ud = to_dev_c64(u)
+        ubar = empty_real((3, m, m, m))
+        tau = empty_real((6, m, m, m))
+        fk.tarang_box_filter(plan, ud.data_ptr(), factor, ubar.data_ptr(), tau.data_ptr(), stream())
+    finally:
+        fk.fftk_plan_destroy(plan)
+    ur = oracle_mod.irfft3(u.astype(np.complex128), n)
+    ub_o, tau_o = oracle_mod.box_filter(ur, factor)
+    uu = np.max(np.abs(tau_o[:3] + ub_o ** 2))
+    assert np.max(np.abs(ubar.cpu().numpy() - ub_o)) < 1e-5 * np.max(np.abs(ub_o))
+    assert np.max(np.abs(tau.cpu().numpy() - tau_o)) < 1e-5 * uu
+
+
+def test_closure_features_match_oracle(fk, oracle_mod):
+    m = 32
+    u = _ic(oracle_mod, m, seed=2, k0=3.0)
+    ur = oracle_mod.irfft3(u.astype(np.complex128), m).astype(np.float32)
+    rng = np.random.default_rng(3)
+    tau = rng.standard_normal((6, m, m, m)).astype(np.float32)
+    plan = fk.fftk_plan_create(m, m, m)
+    try:
+        inv = empty_real((5, m, m, m))
+        frame = empty_real((9, m, m, m))
+        taup = empty_real((6, m, m, m))
+        fk.tarang_closure_features(plan, _f32(ur).data_ptr(), _f32(tau).data_ptr(), inv.data_ptr(), frame.data_ptr(),
+                                   taup.data_ptr(), stream())
+        inv, frame, taup = inv.cpu().numpy(), frame.cpu().numpy(), taup.cpu().numpy()
+    finally:
+        fk.fftk_plan_destroy(plan)
+    A = oracle_mod.gradient(ur.astype(np.float64))
+    pts = rng.integers(0, m, size=(300, 3))
+    scale = np.max(np.abs(A)) ** 2
+    checked = 0
+    for (a, b, c) in pts:
+        Ap = A[:, a, b, c]
+        io = oracle_mod.invariants(Ap)
+        sc = [scale, scale, scale ** 1.5, scale ** 1.5, scale ** 2]
+        for i in range(5):
+            assert abs(inv[i, a, b, c] - io[i]) < 1e-4 * sc[i]
+        S = 0.5 * (Ap.reshape(3, 3) + Ap.reshape(3, 3).T)
+        lam, Q = oracle_mod.sym_eig3(S.ravel())
+        gap = min(lam[0] - lam[1], lam[1] - lam[2])
+        # frame: compare where the eigenvalues are well separated and no
+        # eigenvector has two nearly equal largest components
+        Qg = frame[:, a, b, c].reshape(3, 3)
+        srt = np.sort(np.abs(Q), axis=0)
+        if gap > 1e-2 * np.sqrt(scale) and np.min(srt[2] - srt[1]) > 1e-3:
+            assert np.max(np.abs(Qg - Q)) < 1e-3
+            T = np.zeros((3, 3))
+            t6 = tau[:, a, b, c].astype(np.float64)
+            T[0, 0], T[1, 1], T[2, 2] = t6[:3]
+            T[0, 1] = T[1, 0] = t6[3]
+            T[0, 2] = T[2, 0] = t6[4]
+            T[1, 2] = T[2, 1] = t6[5]
+            Tp = Q.T @ T @ Q
+            want = [Tp[0, 0], Tp[1, 1], Tp[2, 2], Tp[0, 1], Tp[0, 2], Tp[1, 2]]
+            assert np.max(np.abs(taup[:, a, b, c] - want)) < 1e-3 * np.max(np.abs(t6))
+            checked += 1
+    assert checked > 100
+
+
+def _params(seed=0, scale=0.3):
+    return (np.random.default_rng(seed).standard_normal(9094) * scale).astype(np.float32)
+
+
+def test_mlp_forward_gradient_adam_match_oracle(fk, oracle_mod):
+    import torch
+
+    B = 1000  # not a multiple of the 128-sample chunk
+    rng = np.random.default_rng(4)
+    p = _params(5)
+    x = rng.standard_normal((B, 5)).astype(np.float32)
+    t = rng.standard_normal((B, 6)).astype(np.float32) * 0.5
+    ctx = fk.tarang_mlp_create(B)
+    try:
+        pd, xd, td = _f32(p), _f32(x), _f32(t)
+        y = torch.empty((B, 6), dtype=torch.float32, device="cuda:0")
+        fk.tarang_mlp_forward(ctx, pd.data_ptr(), xd.data_ptr(), y.data_ptr(), B, stream())
+        g = torch.empty(9094, dtype=torch.float32, device="cuda:0")
+        loss = torch.zeros(1, dtype=torch.float64, device="cuda:0")
+        fk.tarang_mlp_loss_grad(ctx, pd.data_ptr(), xd.data_ptr(), td.data_ptr(), B, g.data_ptr(), loss.data_ptr(),
+                                stream())
+        g2 = torch.empty_like(g)
+        fk.tarang_mlp_loss_grad(ctx, pd.data_ptr(), xd.data_ptr(), td.data_ptr(), B, g2.data_ptr(), 0, stream())
+        sync()
+        assert torch.equal(g, g2)  # fixed-order reduction
+        m = torch.zeros(9094, dtype=torch.float32, device="cuda:0")
+        v = torch.zeros_like(m)
+        p2 = pd.clone()
+        for step in (1, 2):
+            fk.tarang_mlp_adam(p2.data_ptr(), m.data_ptr(), v.data_ptr(), g.data_ptr(), step, 1e-3, 0.9, 0.999, 1e-8,
+                               stream())
+        sync()
+        yg, gg, lg, pg = y.cpu().numpy(), g.cpu().numpy(), float(loss.item()), p2.cpu().numpy()
+    finally:
+        fk.tarang_mlp_destroy(ctx)
+    yo = oracle_mod.mlp_forward(p.astype(np.float64), x.astype(np.float64), bf16_acts=True)
+    lo, go = oracle_mod.mlp_loss_grad(p.astype(np.float64), x.astype(np.float64), t.astype(np.float64), bf16_acts=True)
+    assert rel_l2(yg, yo) < 1e-3
+    assert abs(lg - lo) < 1e-3 * lo
+    assert rel_l2(gg, go) < 1e-3
+    po = p.astype(np.float64)
+    mo = np.zeros(9094)
+    vo = np.zeros(9094)
+    for step in (1, 2):
+        oracle_mod.adam(po, mo, vo, gg.astype(np.float64), step, lr=1e-3)
+    assert np.max(np.abs(pg - po)) < 1e-6
+
+
+def test_mlp_training_reduces_loss(fk):
+    import torch
+
+    B = 4096
+    rng = np.random.default_rng(6)
+    x = rng.standard_normal((B, 5)).astype(np.float32)
+    t = np.stack([np.tanh(x[:, 0] - x[:, 1]), x[:, 2] * 0.5, np.sin(x[:, 3]), x[:, 4] * x[:, 0] * 0.3,
+                  0 * x[:, 0] + 0.1, np.tanh(x[:, 1] + x[:, 2])], axis=1).astype(np.float32)
+    ctx = fk.tarang_mlp_create(B)
+    try:
+        p = _f32(_params(7, 0.1))
+        m = torch.zeros(9094, dtype=torch.float32, device="cuda:0")
+        v = torch.zeros_like(m)
+        loss = torch.zeros(1, dtype=torch.float64, device="cuda:0")
+        xd, td = _f32(x), _f32(t)
+        losses = []
+        for step in range(1, 401):
+            fk.tarang_mlp_train_step(ctx, p.data_ptr(), m.data_ptr(), v.data_ptr(), step, xd.data_ptr(), td.data_ptr(),
+                                     B, 3e-3, loss.data_ptr(), stream())
+            if step in (1, 400):
+                sync()
+                losses.append(float(loss.item()))
+    finally:
+        fk.tarang_mlp_destroy(ctx)
+    assert losses[1] < 0.1 * losses[0]
+
+
+def _oracle_tau_of_state(oracle_mod, u64, params, shift, scale, out_scale):
+    n = u64.shape[1]
+    ur = oracle_mod.irfft3(u64.astype(np.complex128), n)
+    A = oracle_mod.gradient(ur)
+    R = n ** 3
+    Af = A.reshape(9, R)
+    X = np.empty((R, 5))
+    Qs = np.empty((R, 3, 3))
+    for c in range(R):
+        Ap = Af[:, c]
+        X[c] = oracle_mod.invariants(Ap)
+        S = 0.5 * (Ap.reshape(3, 3) + Ap.reshape(3, 3).T)
+        _, Qs[c] = oracle_mod.sym_eig3(S.ravel())
+    Xn = (X - shift) * scale
+    Y = oracle_mod.mlp_forward(params.astype(np.float64), Xn, bf16_acts=True) * out_scale
+    tau = np.empty((6, R))
+    for c in range(R):
+        T = np.zeros((3, 3))
+        y = Y[c]
+        T[0, 0], T[1, 1], T[2, 2] = y[:3]
+        T[0, 1] = T[1, 0] = y[3]
+        T[0, 2] = T[2, 0] = y[4]
+        T[1, 2] = T[2, 1] = y[5]
+        Tl = Qs[c] @ T @ Qs[c].T
+        tau[:, c] = [Tl[0, 0], Tl[1, 1], Tl[2, 2], Tl[0, 1], Tl[0, 2], Tl[1, 2]]
+    return tau.reshape((6, n, n, n)), X
+
+
+def test_fused_sgs_inference_in_rhs_matches_oracle(fk, oracle_mod):
+    import torch
+
+    n = 16
+    u = _ic(oracle_mod, n, seed=8, k0=2.0)
+    p = _params(9, 0.3)
+    # normalisation from this field's invariants (std of each)
+    _, X = _oracle_tau_of_state(oracle_mod, u, p, np.zeros(5), np.ones(5), np.ones(6))
+    shift = X.mean(axis=0)
+    scale = 1.0 / X.std(axis=0)
+    out_scale = np.full(6, 0.05)
+    tau_o, _ = _oracle_tau_of_state(oracle_mod, u, p, shift, scale, out_scale)
+    s_o = oracle_mod.sgs_force(tau_o)
+    plan = fk.fftk_plan_create(n, n, n)
+    try:
+        pd = _f32(p)
+        model = fk.make_sgs_model(pd.data_ptr(), shift, scale, out_scale)
+        ud = to_dev_c64(u)
+        n0 = empty_c64(ud.shape[:-1])
+        n1 = empty_c64(ud.shape[:-1])
+        fk.tarang_ns_rhs(plan, ud.data_ptr(), n0.data_ptr(), fk.make_params(0.0), stream())
+        fk.tarang_ns_rhs(plan, ud.data_ptr(), n1.data_ptr(), fk.make_params(0.0, sgs_model=model), stream())
+        sync()
+        s_g = from_dev_c64(n1) - from_dev_c64(n0)
+        # one step with the model stays finite and keeps the dropped modes at zero
+        d = fk.tarang_ns_step(plan, ud.data_ptr(), fk.make_params(1e-3, 1e-3, sgs_model=model), 2, True, stream())
+        assert np.isfinite(d[0])
+    finally:
+        fk.fftk_plan_destroy(plan)
+    assert rel_l2(s_g, s_o) < 1e-3

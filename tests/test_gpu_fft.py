@@ -4,7 +4,7 @@ FP64 oracle, through the C ABI.
 Tolerance: FP32 arithmetic with correctly rounded FP32 twiddles; the error of
 a Cooley-Tukey transform grows at most with the number of radix-2 levels,
 relative L2 <= ~u log2(N^3) (u = 2^-24): 1.8e-6 at 1024^3.  Every case uses
-the benchmark spec's bound 2e-6 on relative L2 and 1e-5 * max|F| per element.
+the bound 2e-6 on relative L2 and 1e-5 * max|F| per element.
 """
 import numpy as np
 import pytest

@@ -6,7 +6,7 @@ Tolerances follow from FP32 arithmetic (u = 2^-24): each of the nine 3D
 transforms of a right-hand side contributes ~u log2(N^3) relative error, the
 products and projection a few u more, so the right-hand side is held to
 relative L2 <= 1e-5; states after a few steps inherit that error only through
-the increments dt*N, and the per-shell spectrum to the benchmark spec's 1e-4 on
+the increments dt*N, and the per-shell spectrum to relative 1e-4 on
 shells holding >= 1e-8 of the peak shell energy.
 """
 import json

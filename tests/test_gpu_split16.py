@@ -1,7 +1,7 @@
 """FFTK_R32_SPLIT16: the y and x passes' radix-16 stages on the tensor cores
 (tcgen05) with split FP16 hi/lo operands and FP32 accumulation.
 
-Tolerance (the benchmark spec): relative L2 <= 1e-5 against the FP64 oracle.  Each
+Tolerance: relative L2 <= 1e-5 against the FP64 oracle.  Each
 tensor-core stage drops only x_lo * W_lo (2^-22 relative) and rounds the FP32
 accumulation; four such stages per pair plus the FP32 stages stay well below.
 """
