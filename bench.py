@@ -492,7 +492,9 @@ def run_reference(args, world, rank):
 
 def run_case(case: str):
     """One small invocation for profiler captures (no timing, no output line):
-    'ns:<n>' = random-phase field + one NS step; 'fft:<nx>,<ny>,<nz>' = two pairs."""
+    'ns:<n>' = random-phase field + one NS step; 'fft:<nx>,<ny>,<nz>' = two pairs
+    ('fft16:' in the split-FP16 mode); 'mlp:<batch>' = two training steps;
+    'sgs:<n>' = two unforced steps with the learned subgrid force."""
     import torch
 
     import paper_1805_07801_gb300 as fk
@@ -512,9 +514,9 @@ def run_case(case: str):
         fk.tarang_ic_random(plan, nr.data_ptr(), u.data_ptr(), K0, E0, st)
         del nr
         fk.tarang_ns_step(plan, u.data_ptr(), fk.make_params(NU, DT), 1, False, st)
-    elif kind == "fft":
+    elif kind in ("fft", "fft16"):
         nx, ny, nz = (int(v) for v in arg.split(","))
-        plan = fk.fftk_plan_create(nx, ny, nz)
+        plan = fk.fftk_plan_create(nx, ny, nz, fk.FFTK_R32_SPLIT16 if kind == "fft16" else fk.FFTK_R32)
         x = torch.empty((nx, ny, nz), dtype=torch.float32, device=dev)
         fk.fftk_fill_normal(x.data_ptr(), x.numel(), SEED, 0, st)
         F = torch.empty((nx, ny, nz // 2 + 1, 2), dtype=torch.float32, device=dev)
@@ -522,10 +524,73 @@ def run_case(case: str):
         for _ in range(2):
             fk.fftk_r2c(plan, x.data_ptr(), F.data_ptr(), 1, st)
             fk.fftk_c2r(plan, F.data_ptr(), y.data_ptr(), 1, st)
+    elif kind == "mlp":
+        import numpy as np
+
+        from paper_1805_07801_gb300 import les
+
+        B = int(arg)
+        plan = None
+        rng = np.random.default_rng(SEED)
+        x = torch.from_numpy(rng.standard_normal((B, 5)).astype(np.float32)).to(dev)
+        t = torch.from_numpy(rng.standard_normal((B, 6)).astype(np.float32)).to(dev)
+        p = torch.from_numpy(les.init_params(SEED)).to(dev)
+        m, v = torch.zeros_like(p), torch.zeros_like(p)
+        ctx = fk.tarang_mlp_create(B)
+        for step in (1, 2):
+            fk.tarang_mlp_train_step(ctx, p.data_ptr(), m.data_ptr(), v.data_ptr(), step, x.data_ptr(),
+                                     t.data_ptr(), B, 1e-3, 0, st)
+        torch.cuda.synchronize(dev)
+        fk.tarang_mlp_destroy(ctx)
+    elif kind == "sgs":
+        import numpy as np
+
+        from paper_1805_07801_gb300 import les
+
+        n = int(arg)
+        plan = fk.fftk_plan_create(n, n, n)
+        nr = torch.empty((3, n, n, n), dtype=torch.float32, device=dev)
+        for f in range(3):
+            fk.fftk_fill_normal(nr[f].data_ptr(), n**3, SEED, f, st)
+        u = torch.empty((3, n, n, n // 2 + 1, 2), dtype=torch.float32, device=dev)
+        fk.tarang_ic_random(plan, nr.data_ptr(), u.data_ptr(), 2.0, E0, st)
+        p = torch.from_numpy(les.init_params(SEED)).to(dev)
+        model = fk.make_sgs_model(p.data_ptr(), np.zeros(5), np.ones(5), np.full(6, 1e-3))
+        fk.tarang_ns_step(plan, u.data_ptr(), fk.make_params(NU, DT, sgs_model=model), 2, False, st)
     else:
         raise SystemExit(f"unknown case {case}")
     torch.cuda.synchronize(dev)
-    fk.fftk_plan_destroy(plan)
+    if plan is not None:
+        fk.fftk_plan_destroy(plan)
+
+
+def run_closure(which: str, out_path: str):
+    """The learned-closure workflow (resolved snapshots -> filtered data ->
+    training -> coarse runs with and without the model); prints one JSON line
+    and writes the full results to out_path."""
+    from paper_1805_07801_gb300 import build as fkbuild
+
+    fkbuild.build()
+    from paper_1805_07801_gb300 import les
+
+    cfg = les.ClosureConfig() if which == "full" else les.ClosureConfig.small()
+    res = les.run(cfg, log=lambda s: print(s, file=sys.stderr, flush=True))
+    if out_path:
+        os.makedirs(os.path.dirname(os.path.abspath(out_path)), exist_ok=True)
+        with open(out_path, "w") as fh:
+            json.dump(res, fh, indent=1)
+    keys = ("resolved_seconds", "resolved_steps_per_s", "ref_samples", "train_seconds", "train_samples_per_s",
+            "heldout_loss", "heldout_loss_zero_model", "coarse_steps_per_s", "coarse_steps_per_s_no_model",
+            "speedup")
+    line = {k: res.get(k) for k in keys}
+    for name in ("model", "no_model"):
+        r = res[name]
+        line[name] = {"finite": r["finite"]}
+        for w in ("stated", "long"):
+            if w in r:
+                line[name][w] = {k: r[w][k] for k in ("max_rel_err", "mean_rel_err", "shells_within_5pct")}
+    line["workload"] = f"closure {which}: {cfg.n}^3 -> {cfg.m}^3"
+    print(json.dumps(line), flush=True)
 
 
 def main():
@@ -536,10 +601,17 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fft", action="store_true")
-    ap.add_argument("--case", default=None, help="profiler case: ns:<n> or fft:<nx>,<ny>,<nz>")
+    ap.add_argument("--case", default=None,
+                    help="profiler case: ns:<n>, fft:<nx>,<ny>,<nz>, fft16:<nx>,<ny>,<nz>, mlp:<batch> or sgs:<n>")
+    ap.add_argument("--closure", choices=["full", "small"], default=None,
+                    help="run the learned-closure workflow instead of the benchmark")
+    ap.add_argument("--closure-out", default="", help="JSON file for the closure workflow's results")
     args = ap.parse_args()
     if args.case:
         run_case(args.case)
+        return
+    if args.closure:
+        run_closure(args.closure, args.closure_out)
         return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -64,6 +64,11 @@ typedef enum {
 /* Human-readable name of a status code (static storage). */
 const char *fftk_status_string(fftk_status s);
 
+/* Name of the CUDA error behind the calling thread's most recent
+ * FFTK_ERR_CUDA / FFTK_ERR_OOM / FFTK_ERR_NO_DEVICE (e.g. "cudaErrorInvalidValue"),
+ * or "" if there was none (static storage). */
+const char *fftk_last_cuda_error(void);
+
 /* Create a plan for nx x ny x nz transforms (paper Sec. 3).  Builds the
  * twiddle table exp(-2 pi i m / LT), LT = max(nx, ny, nz), in FP64 on the host
  * and rounds it once to FP32.  Binds the plan to the current CUDA device.
@@ -191,6 +196,13 @@ fftk_status tarang_diag_noalloc(int n, const void *uhat, double nu, double *diag
  * uhat: float2 [3][n][n][n/2+1]. */
 fftk_status tarang_ic_random(fftk_plan p, const float *normals, void *uhat, double k0, double E0,
                              void *cuda_stream);
+
+/* Make uhat (float2 [3][n][n][n/2+1], in place) a valid solver state: modes
+ * outside the 2/3-rule set are zeroed, each kept mode is replaced by its
+ * divergence-free part u - k (k.u)/|k|^2 (Eq. (8), FP32), and u(0) = 0.
+ * Asynchronous; INVALID_ARG for a null or misaligned pointer,
+ * UNSUPPORTED_SIZE for a non-cubic plan or n outside [8, 1024]. */
+fftk_status tarang_dealias_project(fftk_plan p, void *uhat, void *cuda_stream);
 
 /* Counter-based SplitMix64 generator (Steele, Lea, Flood 2014): element i of
  * field f for seed s uses the outputs at counters c = s 2^40 + f 2^36 + 2i and

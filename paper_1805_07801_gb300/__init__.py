@@ -31,7 +31,12 @@ FFTK_R32_SPLIT16 = 1
 class FFTKError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
-        super().__init__(f"{where}: {fftk_status_string(status)} ({status})")
+        msg = f"{where}: {fftk_status_string(status)} ({status})"
+        if status in (FFTK_ERR_NO_DEVICE, FFTK_ERR_OOM, FFTK_ERR_CUDA):
+            cause = lib().fftk_last_cuda_error().decode()
+            if cause:
+                msg += f" [{cause}]"
+        super().__init__(msg)
 
 
 class tarang_sgs_model(ctypes.Structure):
@@ -68,6 +73,7 @@ def lib() -> ctypes.CDLL:
         vp, i, d, ll = c.c_void_p, c.c_int, c.c_double, c.c_longlong
         sig = {
             "fftk_status_string": ([i], c.c_char_p),
+            "fftk_last_cuda_error": ([], c.c_char_p),
             "fftk_plan_create": ([i, i, i, i, c.POINTER(vp)], i),
             "fftk_plan_destroy": ([vp], i),
             "fftk_workspace_bytes": ([vp, i], c.c_size_t),
@@ -80,6 +86,7 @@ def lib() -> ctypes.CDLL:
             "tarang_diag": ([vp, vp, d, vp, vp], i),
             "tarang_diag_noalloc": ([i, vp, d, vp, vp], i),
             "tarang_ic_random": ([vp, vp, vp, d, d, vp], i),
+            "tarang_dealias_project": ([vp, vp, vp], i),
             "fftk_fill_normal": ([vp, ll, i, i, vp], i),
             "fftk_fill_uniform": ([vp, ll, i, i, vp], i),
             "fftk_sync": ([vp, vp], i),
@@ -204,6 +211,10 @@ def tarang_diag_noalloc(n: int, uhat_ptr, nu: float, diag_dev_ptr, stream=0) -> 
 def tarang_ic_random(plan: int, normals_ptr, uhat_ptr, k0: float = 4.0, E0: float = 0.5, stream=0) -> None:
     _check(lib().tarang_ic_random(_vp(plan), _vp(normals_ptr), _vp(uhat_ptr), float(k0), float(E0), _vp(stream)),
            "tarang_ic_random")
+
+
+def tarang_dealias_project(plan: int, uhat_ptr, stream=0) -> None:
+    _check(lib().tarang_dealias_project(_vp(plan), _vp(uhat_ptr), _vp(stream)), "tarang_dealias_project")
 
 
 def fftk_fill_normal(dev_ptr, count: int, seed: int, field: int, stream=0) -> None:

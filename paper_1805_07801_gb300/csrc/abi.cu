@@ -64,8 +64,11 @@ static bool overlap(const void* a, size_t na, const void* b, size_t nb) {
   return x < y + nb && y < x + na;
 }
 
+static thread_local cudaError_t g_last_cuda = cudaSuccess;
+
 fftk_status from_cuda(cudaError_t e) {
   if (e == cudaSuccess) return FFTK_OK;
+  g_last_cuda = e;
   if (e == cudaErrorMemoryAllocation) return FFTK_ERR_OOM;
   if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver) return FFTK_ERR_NO_DEVICE;
   return FFTK_ERR_CUDA;
@@ -111,6 +114,10 @@ extern "C" const char* fftk_status_string(fftk_status s) {
     case FFTK_ERR_TIMEOUT: return "FFTK_ERR_TIMEOUT";
   }
   return "FFTK_ERR_UNKNOWN";
+}
+
+extern "C" const char* fftk_last_cuda_error(void) {
+  return g_last_cuda == cudaSuccess ? "" : cudaGetErrorName(g_last_cuda);
 }
 
 extern "C" fftk_status fftk_plan_create(int nx, int ny, int nz, fftk_dtype dtype, fftk_plan* out) {

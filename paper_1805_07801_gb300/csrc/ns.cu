@@ -516,6 +516,24 @@ static NSGeom make_geom(int n) {
   return g;
 }
 
+// The dynamic shared-memory limit is an attribute of the kernel (per device),
+// not of a plan: it is raised once per device to what the largest grid needs,
+// so that no plan lowers it under another plan's launches.
+static cudaError_t diag_attr() {
+  static std::mutex mu;
+  static bool done[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(mu);
+  if (done[dev]) return cudaSuccess;
+  const int smem = (int)(sizeof(double) * DIAG_WARPS * (ns_kmax(1024) + 1));
+  e = cudaFuncSetAttribute(k_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) done[dev] = true;
+  return e;
+}
+
 static fftk_status ns_ensure(fftk_plan p) {
   std::lock_guard<std::mutex> lk(p->mu);
   if (p->ns) return FFTK_OK;
@@ -536,8 +554,7 @@ static fftk_status ns_ensure(fftk_plan p) {
   if (e == cudaSuccess) e = cudaMalloc(&s->dout, sizeof(double) * (size_t)width);
   if (e == cudaSuccess) e = cudaMallocHost(&s->hout, sizeof(double) * (size_t)width);
   s->diag_smem = (int)(sizeof(double) * DIAG_WARPS * (s->kmax + 1));
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, s->diag_smem);
+  if (e == cudaSuccess) e = diag_attr();
   if (e != cudaSuccess) {
     cudaGetLastError();
     cudaFree(s->w);
@@ -911,6 +928,23 @@ extern "C" fftk_status tarang_ic_random(fftk_plan p, const float* normals, void*
   return from_cuda(e);
 }
 
+// Dealias and project a caller's state (Eq. (8) and the 2/3 rule): the entry
+// point that turns any transformed velocity, e.g. a filtered resolved field on
+// a coarse grid, into a valid solver state.
+extern "C" fftk_status tarang_dealias_project(fftk_plan p, void* uhat, void* cuda_stream) {
+  if (!p || !uhat || misaligned16(uhat)) return FFTK_ERR_INVALID_ARG;
+  if (p->nx != p->ny || p->nx != p->nz || p->nx < 8 || p->nx > 1024)
+    return FFTK_ERR_UNSUPPORTED_SIZE;
+  fftk_status s = ns_ensure(p);
+  if (s != FFTK_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  {
+    LaunchScope ls(p, KK_AUX, st);
+    k_ic_shape<<<152 * 8, 256, 0, st>>>(static_cast<float2*>(uhat), p->ns->g);
+  }
+  return from_cuda(cudaGetLastError());
+}
+
 // ------------------------------------------- diagnostics without allocation --
 // Callers that cannot allocate device memory (a real-time loop that must not
 // pay cudaMalloc's implicit device synchronisation, or a host application
@@ -928,8 +962,8 @@ static std::mutex g_noalloc_mu;
 static double* g_noalloc_ptr[kNoAllocMaxDevices] = {};
 
 // Once per device, with that device current: the device address of the
-// scratch array (the host-side symbol is only a stand-in) and the dynamic
-// shared-memory limit of the reduction kernel for the largest n.
+// scratch array (the host-side symbol is only a stand-in), with the reduction
+// kernel's shared-memory limit raised for the largest n.
 static fftk_status noalloc_setup(double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -940,8 +974,7 @@ static fftk_status noalloc_setup(double** out) {
     double* ptr = nullptr;
     e = cudaGetSymbolAddress((void**)&ptr, g_diag_scratch);
     if (e != cudaSuccess) return from_cuda(e);
-    const int smem = (int)(sizeof(double) * DIAG_WARPS * (ns_kmax(1024) + 1));
-    e = cudaFuncSetAttribute(k_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    e = diag_attr();
     if (e != cudaSuccess) return from_cuda(e);
     g_noalloc_ptr[dev] = ptr;
   }

@@ -243,3 +243,22 @@ def test_fused_sgs_inference_in_rhs_matches_oracle(fk, oracle_mod):
     finally:
         fk.fftk_plan_destroy(plan)
     assert rel_l2(s_g, s_o) < 1e-3
+
+
+@pytest.mark.parametrize("n", [16, 32, 64])
+def test_dealias_project_matches_oracle(fk, oracle_mod, n):
+    """Pointwise FP32 projection of every mode; the dropped modes are exact zeros."""
+    rng = np.random.default_rng(10 + n)
+    shape = (3, n, n, n // 2 + 1)
+    u = (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)).astype(np.complex64)
+    want = oracle_mod.project(oracle_mod.dealias(u.astype(np.complex128), 3))
+    plan = fk.fftk_plan_create(n, n, n)
+    try:
+        ud = to_dev_c64(u)
+        fk.tarang_dealias_project(plan, ud.data_ptr(), stream())
+        got = from_dev_c64(ud)
+    finally:
+        fk.fftk_plan_destroy(plan)
+    dropped = oracle_mod.dealias(np.ones(shape, dtype=np.complex128), 3) == 0
+    assert np.all(got[dropped] == 0)
+    assert np.max(np.abs(got - want)) < 4e-6 * np.max(np.abs(u))

@@ -267,3 +267,17 @@ def test_decay_512_100_steps_vs_stored_oracle(fk, oracle_mod):
     """The 512^3 decaying-turbulence workload: per-shell spectrum after 100
     steps vs the oracle's stored run (tests/golden/make_ns512_golden.py)."""
     _golden_decay(fk, oracle_mod, 512)
+
+
+def test_diag_after_smaller_plan(fk, oracle_mod):
+    """A smaller plan's solver state must not shrink the reduction kernel's
+    shared-memory limit under a larger plan (the limit is per kernel)."""
+    u = random_ic(oracle_mod, 64, seed=3)
+    with Plan(fk, 64) as big:
+        ud = to_dev_c64(u)
+        first = fk.tarang_diag(big, ud.data_ptr(), 1e-3, stream())
+        with Plan(fk, 16) as small:
+            us = to_dev_c64(random_ic(oracle_mod, 16, seed=4))
+            fk.tarang_diag(small, us.data_ptr(), 1e-3, stream())
+            again = fk.tarang_diag(big, ud.data_ptr(), 1e-3, stream())
+    assert first[0] == again[0] and first[2] == again[2]
