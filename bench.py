@@ -564,6 +564,50 @@ def run_case(case: str):
         fk.fftk_plan_destroy(plan)
 
 
+def run_forced(n: int, steps: int):
+    """Forced turbulence in FP32 (k0 = 2, constant power 0.1 on 1 <= |k| <= 2,
+    nu = 4e-4, dt = 2.5e-4): steps/s of the fused step with the forcing
+    reduction, and E, eps and the spectrum every 50 steps.  Prints one JSON line."""
+    import torch
+
+    import paper_1805_07801_gb300 as fk
+    from paper_1805_07801_gb300 import build as fkbuild
+
+    fkbuild.build()
+    dev = torch.device("cuda:0")
+    st = torch.cuda.current_stream(dev).cuda_stream
+    plan = fk.fftk_plan_create(n, n, n)
+    nr = torch.empty((3, n, n, n), dtype=torch.float32, device=dev)
+    for f in range(3):
+        fk.fftk_fill_normal(nr[f].data_ptr(), n**3, SEED, f, st)
+    u = torch.empty((3, n, n, n // 2 + 1, 2), dtype=torch.float32, device=dev)
+    fk.tarang_ic_random(plan, nr.data_ptr(), u.data_ptr(), 2.0, E0, st)
+    del nr
+    prm = fk.make_params(4e-4, 2.5e-4, 0.1, (1, 4))
+    fk.tarang_ns_step(plan, u.data_ptr(), prm, 3, False, st)
+    hist = []
+    secs = 0.0
+    done = 0
+    chunk = 50
+    while done < steps:
+        k = min(chunk, steps - done)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        fk.tarang_ns_step(plan, u.data_ptr(), prm, k, False, st)
+        b.record()
+        b.synchronize()
+        secs += a.elapsed_time(b) * 1e-3
+        done += k
+        E, eps, EK = fk.tarang_diag(plan, u.data_ptr(), 4e-4, st)
+        hist.append({"step": done + 3, "E": E, "eps": eps})
+    fk.fftk_plan_destroy(plan)
+    print(json.dumps({"workload": f"{n}^3 forced turbulence, FP32, k0=2, eps=0.1 on 1<=|k|<=2, nu=4e-4, "
+                                  f"dt=2.5e-4, RK2-IF, 2/3 dealiasing, seed {SEED}",
+                      "steps": steps, "steps_per_s": round(steps / secs, 3), "ms_per_step": round(1e3 * secs / steps, 3),
+                      "history": hist, "EK_final": [float(v) for v in EK[:65]]}), flush=True)
+
+
 def run_closure(which: str, out_path: str):
     """The learned-closure workflow (resolved snapshots -> filtered data ->
     training -> coarse runs with and without the model); prints one JSON line
@@ -606,12 +650,17 @@ def main():
     ap.add_argument("--closure", choices=["full", "small"], default=None,
                     help="run the learned-closure workflow instead of the benchmark")
     ap.add_argument("--closure-out", default="", help="JSON file for the closure workflow's results")
+    ap.add_argument("--forced", type=int, default=0, metavar="N",
+                    help="run N^3 forced turbulence for --steps steps and print its JSON line")
     args = ap.parse_args()
     if args.case:
         run_case(args.case)
         return
     if args.closure:
         run_closure(args.closure, args.closure_out)
+        return
+    if args.forced:
+        run_forced(args.forced, args.steps)
         return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

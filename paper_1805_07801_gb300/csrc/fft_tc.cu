@@ -1,10 +1,10 @@
 // Split-FP16 tensor-core radix-16 stages for the strided passes (dtype
 // FFTK_R32_SPLIT16).
 //
-// A line of length L = 256 * R3 (R3 in {1, 2, 4, 8}) is transformed as two
-// radix-16 Stockham stages on the 5th-generation tensor cores and, when
-// R3 > 1, one FP32 radix-R3 stage.  A radix-16 stage over a batch of DFT rows
-// is the product D = A B:
+// A line of length L = R0 * 256 (R0 in {1, 2, 4, 8}) is transformed as one
+// FP32 radix-R0 stage in registers followed by two radix-16 stages on the
+// 5th-generation tensor cores.  A radix-16 stage over a batch of DFT rows is
+// the product D = A B:
 //   A [rows x 64] FP16: for each of the row's 16 complex inputs x (already
 //     twiddled, scaled by a power of two), the four values hi.re, hi.im,
 //     lo.re, lo.im with hi = fp16(x), lo = fp16(x - hi);
@@ -12,14 +12,14 @@
 //     split W = W_hi + W_lo; B1 multiplies both hi and lo by W_hi, B2 the hi
 //     part by W_lo, so D = (x_hi + x_lo) W_hi + x_hi W_lo (FP32 accumulate in
 //     TMEM), dropping only x_lo W_lo (2^-22 relative).
-// Twiddles, scaling and the radix-R3 stage stay in FP32.
-//
-// One CTA of 128 threads owns 512 DFT rows (four M = 128 blocks, one TMEM lane
-// per thread and block); thread 0 issues tcgen05.mma (M = 128, N = 32,
-// K = 16), completion is signalled through an mbarrier, and every thread
-// reads its own rows back with tcgen05.ld.  Operands use the canonical
-// K-major layout without swizzle: 8-row x 16-byte core matrices, 128 bytes
-// apart along K (LBO) and 1024 bytes apart along M/N (SBO).
+// Twiddles, scaling and the radix-R0 stage stay in FP32.  Per stage, one
+// thread writes its A values to shared memory and, after the MMAs, reads one
+// TMEM row back with tcgen05.ld; the second stage's rows go straight to global
+// memory, so no FP32 exchange through shared memory remains.  Thread 0 issues
+// tcgen05.mma (M = 128, N = 32, K = 16) and completion is signalled through an
+// mbarrier.  Operands use the canonical K-major layout without swizzle: 8-row
+// x 16-byte core matrices, 128 bytes apart along K (LBO) and 1024 bytes apart
+// along M/N (SBO).
 #include <cuda_fp16.h>
 
 #include <cmath>
@@ -32,16 +32,11 @@
 namespace fftk {
 namespace tc {
 
-constexpr int kThreads = 128;
-constexpr int kRows = 512;               // DFT rows per stage per tile
-constexpr int kBlocks = kRows / 128;     // M blocks
 constexpr uint32_t kLBO = 128;           // bytes between core matrices along K
 constexpr uint32_t kSBO = 1024;          // bytes between 8-row groups (64 FP16 per row)
 constexpr int kBlkBytes = 16 * 1024;     // one M block of A
 constexpr int kBlkStride = kBlkBytes + 16;  // + 16 bytes: spreads blocks over banks
-constexpr int kABytes = kBlocks * kBlkStride;
 constexpr int kBBytes = 4 * 1024;        // one 32 x 64 operand
-constexpr int kTmemCols = 128;
 constexpr long long kSpinLimit = 1LL << 26;
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -117,16 +112,60 @@ __device__ __forceinline__ float pow2_scale(float m) {
 
 }  // namespace tc
 
+// Tile = T adjacent columns (contiguous index q) x the whole line.  The line
+// L = R0 * 16 * 16 is transformed as
+//   stage 0 (FP32, registers): for each a < 256 the R0-point DFT of
+//     x[a + 256 m], m < R0, times the twiddle W_L^(a r)  -> Z_r[a];
+//   stage 1 (tensor cores): for each (r, a0 < 16) the DFT-16 over a1 of
+//     Z_r[a0 + 16 a1]  -> U[k0'], times W_256^(a0 k0');
+//   stage 2 (tensor cores): for each (r, k0') the DFT-16 over a0
+//     -> X[R0 (k0' + 16 k1') + r]  (stored straight from TMEM).
+// One stage row per thread: T * L / 16 threads, 128-row M blocks, one TMEM
+// lane per thread.  Every value handed to the tensor cores is scaled by the
+// same power of two per column: s brings the column's largest stage-0 output
+// component into [2^10, 2^11); stage-1 outputs are bounded by 16 times that,
+// so stage 2 takes them times 1/16 (folded into its twiddles).
+// The CTA is persistent (one TMEM allocation for all its tiles); two CTAs
+// per SM overlap one another's loads, MMAs and stores.
 template <int L>
-struct TCCfg {
-  static constexpr int R3 = L / 256;
-  static constexpr int S1 = L / 16;            // butterflies per column in each radix-16 stage
-  static constexpr int T = tc::kRows / S1;     // columns per tile
-  static constexpr int LOGS1 = Log2<S1>::value;
+struct TC2 {
+  static constexpr int T = L <= 512 ? 16 : 8192 / L;  // columns per tile
+  static constexpr int R0 = L / 256;                   // leading FP32 radix
+  static constexpr int A1 = 16 / R0;                   // stage-0 butterflies per thread
+  static constexpr int THREADS = T * L / 16;           // DFT-16 rows per stage
+  static constexpr int BLOCKS = THREADS / 128;         // M = 128 blocks
+  static constexpr int COLS = BLOCKS * 32;             // TMEM columns (a power of two >= 32)
   static constexpr int LOGT = Log2<T>::value;
   static constexpr int LOGL = Log2<L>::value;
-  static constexpr size_t SMEM = 1024 + tc::kABytes + 2 * tc::kBBytes + sizeof(float) * T + 64;
+  static constexpr int ABYTES = BLOCKS * tc::kBlkStride;
+  static constexpr size_t SMEM = 1024 + ABYTES + 2 * tc::kBBytes + 256 * sizeof(float2) + sizeof(float) * T + 64;
+  static constexpr int MINB = 1024 / THREADS;  // 64 registers
+  static_assert(THREADS % 128 == 0 && (COLS & (COLS - 1)) == 0 && SMEM <= 227 * 1024, "tile shape");
 };
+
+// Physical stage row of logical row (jj, cc) (jj = 16 r + a0 in stage 1,
+// 16 r + k0' in stage 2; cc the column).  Thread t owns physical row t.  For
+// T = 16 bits 3 and 4 are swapped so that a half warp's 64-bit operand stores
+// cover 8 rows x 2 K slots (no bank conflicts).
+template <int T>
+__device__ __forceinline__ int phys_row(int jj, int cc) {
+  if constexpr (T == 16) {
+    return (cc & 7) | ((jj & 1) << 3) | (((cc >> 3) & 1) << 4) | ((jj >> 1) << 5);
+  } else {
+    return (jj << Log2<T>::value) | cc;
+  }
+}
+template <int T>
+__device__ __forceinline__ void thread_coords(int t, int& cc, int& jj) {
+  if constexpr (T == 16) {
+    cc = (t & 7) | (((t >> 4) & 1) << 3);
+    jj = ((t >> 3) & 1) | ((t >> 5) << 1);
+  } else {
+    cc = t & (T - 1);
+    jj = t >> Log2<T>::value;
+  }
+}
+
 
 // B operands (K-major, 32 rows of 64) for one sign: [B1 | B2] in the
 // canonical layout, built on the host in FP64 and rounded to FP16.
@@ -162,28 +201,42 @@ static void build_dft16_operands(int sign, std::vector<__half>& out) {
     }
 }
 
+
 // Strided pass [P][L][Q] along L with split-FP16 tensor-core radix-16 stages.
 template <int L, int SIGN>
-__global__ void __launch_bounds__(tc::kThreads)
+__global__ void __launch_bounds__(TC2<L>::THREADS, TC2<L>::MINB)
     k_cpass_tc(const float2* in, float2* out, long long Q, long long qtiles, long long ntiles,
                const float2* __restrict__ tw, int twlog, float out_scale,
                const __half* __restrict__ bops, int* err) {
-  using C = TCCfg<L>;
-  constexpr int T = C::T, S1 = C::S1, R3 = C::R3;
+  using C = TC2<L>;
+  constexpr int T = C::T, R0 = C::R0, A1 = C::A1, NT = C::THREADS;
   extern __shared__ __align__(1024) unsigned char smraw[];
   unsigned char* base = smraw + ((1024 - (tc::su32(smraw) & 1023)) & 1023);
-  unsigned char* As = base;                                   // A tile, reused as FP32 exchange
-  unsigned char* Bs = base + tc::kABytes;                     // B1, B2
-  float* colmax = reinterpret_cast<float*>(Bs + 2 * tc::kBBytes);
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(colmax + T + (T & 1));
+  unsigned char* As = base;                                          // A tile (both stages)
+  unsigned char* Bs = base + C::ABYTES;                              // B1, B2
+  float2* w256 = reinterpret_cast<float2*>(Bs + 2 * tc::kBBytes);   // W_256^m / 16
+  float* colmax = reinterpret_cast<float*>(w256 + 256);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(colmax + T);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
   const int t = threadIdx.x, warp = t >> 5;
 
-  for (int i = t; i < 2 * tc::kBBytes / 16; i += tc::kThreads)
+  // thread coordinates: column c; j splits into a0 (stage-0 a mod 16, stage-1
+  // row a0, stage-2 row k0') and u (stage-0 block of a1, stage row r)
+  int c, j;
+  thread_coords<T>(t, c, j);
+  const int a0 = j & 15, u = j >> 4;
+
+  for (int i = t; i < 2 * tc::kBBytes / 16; i += NT)
     reinterpret_cast<uint4*>(Bs)[i] = reinterpret_cast<const uint4*>(bops)[i];
+  for (int i = t; i < 256; i += NT) {
+    float2 w = __ldg(&tw[i << (twlog - 8)]);
+    if (SIGN > 0) w.y = -w.y;
+    w256[i] = make_float2(w.x * 0.0625f, w.y * 0.0625f);
+  }
+  if (t < T) colmax[t] = 0.f;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(tc::su32(tslot)),
-                 "r"(tc::kTmemCols));
+                 "r"(C::COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
   }
   if (t == 0) {
@@ -196,7 +249,8 @@ __global__ void __launch_bounds__(tc::kThreads)
   asm volatile("tcgen05.fence::after_thread_sync;\n");
   const uint32_t tmem = *tslot;
   const uint32_t a_sa = tc::su32(As), b1_sa = tc::su32(Bs), b2_sa = b1_sa + tc::kBBytes;
-  const uint32_t lane_base = tmem + (((uint32_t)warp * 32u) << 16);
+  // this thread's TMEM row: lane 32 (warp % 4) + lane id of M block warp / 4 = stage row t
+  const uint32_t row_addr = tmem + (((uint32_t)(warp & 3) * 32u) << 16) + 32u * (uint32_t)(warp >> 2);
   uint32_t phase = 0;
   bool failed = false;
 
@@ -207,7 +261,7 @@ __global__ void __launch_bounds__(tc::kThreads)
     asm volatile("tcgen05.fence::after_thread_sync;\n");
     if (t == 0) {
 #pragma unroll
-      for (int blk = 0; blk < tc::kBlocks; ++blk) {
+      for (int blk = 0; blk < C::BLOCKS; ++blk) {
         const uint32_t d = tmem + 32u * blk;
         const uint32_t a = a_sa + blk * tc::kBlkStride;
 #pragma unroll
@@ -218,141 +272,121 @@ __global__ void __launch_bounds__(tc::kThreads)
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
           tc::su32(mbar)));
     }
-    const bool ok = tc::mbar_wait(mbar, phase);
+    // thread 0 alone polls the mbarrier; the others wait at the barrier
+    // without taking issue slots, and the tcgen05 fences around it order their
+    // TMEM reads after the MMAs
+    bool ok = true;
+    if (t == 0) {
+      ok = tc::mbar_wait(mbar, phase);
+      asm volatile("tcgen05.fence::after_thread_sync;\n");
+      asm volatile("tcgen05.fence::before_thread_sync;\n");
+    }
     phase ^= 1;
+    const bool all = __syncthreads_and(ok) != 0;
     asm volatile("tcgen05.fence::after_thread_sync;\n");
-    return __syncthreads_and(ok) != 0;
+    return all;
   };
 
   for (long long tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
-    const long long p = tile / qtiles;
-    const long long q0 = (tile - p * qtiles) * T;
-    const float2* src = in + p * (long long)L * Q + q0;
-    float2* dst = out + p * (long long)L * Q + q0;
-    if (t < T) colmax[t] = 0.f;
-    float s1[tc::kBlocks];
-    // ---- stage 1: rows (b, c), inputs x[b + r S1][c], per-row power-of-two scale
-#pragma unroll 1
-    for (int blk = 0; blk < tc::kBlocks; ++blk) {
-      const int row = t + 128 * blk;
-      const int b = row >> C::LOGT, c = row & (T - 1);
-      const bool valid = q0 + c < Q;
-      float2 x[16];
-      float m = 0.f;
+    const long long pl = tile / qtiles;
+    const long long q0 = (tile - pl * qtiles) * T;
+    const bool valid = q0 + c < Q;
+    float2* dst = out + pl * (long long)L * Q + q0 + c;
+    // ---- stage 0: R0-point DFTs of x[a + 256 m] for a = a0 + 16 (A1 u + i)
+    float2 z[A1][R0];
+    {
+      const float2* src = in + pl * (long long)L * Q + q0 + c;
 #pragma unroll
-      for (int r = 0; r < 16; ++r) {
-        x[r] = valid ? src[(long long)(b + r * S1) * Q + c] : make_float2(0.f, 0.f);
-        m = fmaxf(m, fmaxf(fabsf(x[r].x), fabsf(x[r].y)));
+      for (int i = 0; i < A1; ++i) {
+        const int a = a0 + 16 * (A1 * u + i);
+#pragma unroll
+        for (int m = 0; m < R0; ++m) z[i][m] = valid ? src[(long long)(a + 256 * m) * Q] : make_float2(0.f, 0.f);
       }
-      const float s = tc::pow2_scale(m);
-      s1[blk] = s;
+    }
+    float mx = 0.f;
 #pragma unroll
-      for (int r = 0; r < 16; r += 2) {
-        const uint2 u0 = tc::split2(cscale(x[r], s)), u1 = tc::split2(cscale(x[r + 1], s));
-        *reinterpret_cast<uint4*>(As + tc::a_off(row, 4 * r)) = make_uint4(u0.x, u0.y, u1.x, u1.y);
+    for (int i = 0; i < A1; ++i) {
+      if constexpr (R0 > 1) {
+        const int a = a0 + 16 * (A1 * u + i);
+        dftR<R0, SIGN>(z[i]);
+#pragma unroll
+        for (int r = 1; r < R0; ++r) {
+          const float2 w = __ldg(&tw[(a * r) << (twlog - C::LOGL)]);
+          z[i][r] = SIGN < 0 ? cmul(z[i][r], w) : cmulc(z[i][r], w);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < R0; ++r) mx = fmaxf(mx, fmaxf(fabsf(z[i][r].x), fabsf(z[i][r].y)));
+    }
+    // column maximum: lanes of a warp that share the column
+    if constexpr (T == 16) {
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 8));
+    } else {
+#pragma unroll
+      for (int o = T; o < 32; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    if constexpr (T == 16) {
+      if (((t >> 3) & 1) == 0) atomicMax(reinterpret_cast<int*>(&colmax[c]), __float_as_int(mx));
+    } else {
+      if ((t & 31) < T) atomicMax(reinterpret_cast<int*>(&colmax[c]), __float_as_int(mx));
+    }
+    __syncthreads();
+    const float s = tc::pow2_scale(colmax[c]);
+    // stage-1 rows (r, a0, c); this thread fills K slots a1 = A1 u .. A1 u + A1 - 1
+#pragma unroll
+    for (int r = 0; r < R0; ++r) {
+      const int row = phys_row<T>(r * 16 + a0, c);
+#pragma unroll
+      for (int i = 0; i < A1; i += 2) {
+        const uint2 v0 = tc::split2(cscale(z[i][r], s)), v1 = tc::split2(cscale(z[i + 1][r], s));
+        *reinterpret_cast<uint4*>(As + tc::a_off(row, 4 * (A1 * u + i))) = make_uint4(v0.x, v0.y, v1.x, v1.y);
       }
     }
     if (!run_mma()) {
       failed = true;
       break;
     }
-    // ---- column maxima of the stage-1 output
-#pragma unroll 1
-    for (int blk = 0; blk < tc::kBlocks; ++blk) {
+    if (t < T) colmax[t] = 0.f;  // every thread has read it (before the barrier in run_mma)
+
+    // ---- stage 1 -> 2: row t = (r = u, a0, c) holds U[k0'] (times s); it
+    //      feeds K slot a0 of stage-2 row (u, k0', c), twiddled by W_256^(a0 k0') / 16
+    {
       float d[32];
-      tc::ld32(lane_base + 32u * blk, d);
-      float m = 0.f;
+      tc::ld32(row_addr, d);
 #pragma unroll
-      for (int i = 0; i < 32; ++i) m = fmaxf(m, fabsf(d[i]));
-      const int c = (t + 128 * blk) & (T - 1);
-      atomicMax(reinterpret_cast<int*>(&colmax[c]), __float_as_int(m / s1[blk]));
-    }
-    __syncthreads();
-    // ---- stage 2 inputs: output r' of row (b, c) sits at p = 16 b + r', which
-    //      is input r = p / S1 of butterfly b2 = p mod S1, twiddle W_256^(r (b2 mod 16))
-#pragma unroll 1
-    for (int blk = 0; blk < tc::kBlocks; ++blk) {
-      const int row = t + 128 * blk;
-      const int b = row >> C::LOGT, c = row & (T - 1);
-      const float inv = 1.f / s1[blk];
-      const float s2 = tc::pow2_scale(colmax[c]);
-      float d[32];
-      tc::ld32(lane_base + 32u * blk, d);
-#pragma unroll
-      for (int rp = 0; rp < 16; ++rp) {
-        const int pp = 16 * b + rp;
-        const int b2 = pp & (S1 - 1), r2 = pp >> C::LOGS1;
-        const int k2 = b2 & 15;
-        const float2 w = __ldg(&tw[(r2 * k2) << (twlog - 8)]);
-        float2 y = make_float2(d[2 * rp] * inv, d[2 * rp + 1] * inv);
-        y = SIGN < 0 ? cmul(y, w) : cmulc(y, w);
-        const uint2 u = tc::split2(cscale(y, s2));
-        *reinterpret_cast<uint2*>(As + tc::a_off((b2 << C::LOGT) + c, 4 * r2)) = u;
+      for (int k0 = 0; k0 < 16; ++k0) {
+        const float2 y = cmul(make_float2(d[2 * k0], d[2 * k0 + 1]), w256[a0 * k0]);
+        *reinterpret_cast<uint2*>(As + tc::a_off(phys_row<T>(u * 16 + k0, c), 4 * a0)) = tc::split2(y);
       }
     }
     if (!run_mma()) {
       failed = true;
       break;
     }
-    // ---- stage 2 outputs: row (b2, c), output r'' at (b2 - k2) 16 + k2 + 16 r''
-    float2* X = reinterpret_cast<float2*>(As);  // FP32 exchange [L][T] for the radix-R3 stage
-    if constexpr (R3 > 1) __syncthreads();
-#pragma unroll 1
-    for (int blk = 0; blk < tc::kBlocks; ++blk) {
-      const int row = t + 128 * blk;
-      const int b2 = row >> C::LOGT, c = row & (T - 1);
-      const int k2 = b2 & 15;
-      const float inv = 1.f / tc::pow2_scale(colmax[c]);
+    // ---- stage 2 output: row t = (r = u, k0' = a0, c) holds X[R0 (k0' + 16 k1') + r] (times s / 16)
+    {
+      const float f = out_scale * 16.f / s;
       float d[32];
-      tc::ld32(lane_base + 32u * blk, d);
+      tc::ld32(row_addr, d);
+      if (valid) {
 #pragma unroll
-      for (int rp = 0; rp < 16; ++rp) {
-        const int pos = (b2 - k2) * 16 + k2 + 16 * rp;
-        const float2 y = make_float2(d[2 * rp] * inv, d[2 * rp + 1] * inv);
-        if constexpr (R3 == 1) {
-          if (q0 + c < Q) dst[(long long)pos * Q + c] = cscale(y, out_scale);
-        } else {
-          X[pos * T + c] = y;
-        }
+        for (int k1 = 0; k1 < 16; ++k1)
+          dst[(long long)(R0 * (a0 + 16 * k1) + u) * Q] = make_float2(d[2 * k1] * f, d[2 * k1 + 1] * f);
       }
     }
-    if constexpr (R3 > 1) {
-      // ---- radix-R3 stage in FP32: butterfly b3 < 256 reads b3 + r 256 with
-      //      twiddle W_L^(r b3); outputs land at b3 + r' 256 (natural order)
-      __syncthreads();
-#pragma unroll 1
-      for (int i = t; i < 256 * T; i += tc::kThreads) {
-        const int b3 = i >> C::LOGT, c = i & (T - 1);
-        float2 v[R3];
-#pragma unroll
-        for (int r = 0; r < R3; ++r) {
-          v[r] = X[(b3 + 256 * r) * T + c];
-          if (r > 0) {
-            const float2 w = __ldg(&tw[(r * b3) << (twlog - C::LOGL)]);
-            v[r] = SIGN < 0 ? cmul(v[r], w) : cmulc(v[r], w);
-          }
-        }
-        dftR<R3, SIGN>(v);
-        if (q0 + c < Q) {
-#pragma unroll
-          for (int r = 0; r < R3; ++r) dst[(long long)(b3 + 256 * r) * Q + c] = cscale(v[r], out_scale);
-        }
-      }
-    }
-    __syncthreads();
   }
   if (failed && t == 0) atomicOr(err, 1);
-  if (failed) tc::mbar_wait(mbar, phase);  // let in-flight MMAs drain (bounded) before freeing TMEM
+  if (failed && t == 0) tc::mbar_wait(mbar, phase ^ 1);  // let in-flight MMAs drain (bounded) before freeing TMEM
   asm volatile("tcgen05.fence::before_thread_sync;\n");
   __syncthreads();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(tc::kTmemCols));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(C::COLS));
 }
 
 template <int L, int SIGN>
 static cudaError_t cpass_tc_l(fftk_plan p, const float2* in, float2* out, long long P, long long Q,
                               float scale, int kind, cudaStream_t st) {
-  using C = TCCfg<L>;
+  using C = TC2<L>;
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   static int per_sm = 1;
@@ -360,10 +394,10 @@ static cudaError_t cpass_tc_l(fftk_plan p, const float2* in, float2* out, long l
     attr_err = cudaFuncSetAttribute(k_cpass_tc<L, SIGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)C::SMEM);
     if (attr_err == cudaSuccess &&
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cpass_tc<L, SIGN>, tc::kThreads, C::SMEM) !=
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cpass_tc<L, SIGN>, C::THREADS, C::SMEM) !=
             cudaSuccess)
       per_sm = 1;
-    if (per_sm > 3) per_sm = 3;  // 3 x 128 TMEM columns fit in 512
+    if (per_sm > 512 / C::COLS) per_sm = 512 / C::COLS;  // TMEM: 512 columns per SM
     if (per_sm < 1) per_sm = 1;
   });
   if (attr_err != cudaSuccess) return attr_err;
@@ -376,8 +410,8 @@ static cudaError_t cpass_tc_l(fftk_plan p, const float2* in, float2* out, long l
   const int blocks = (int)(ntiles < cap ? ntiles : cap);
   const __half* bops = p->d_dft16 + (SIGN < 0 ? 0 : 2 * 32 * 64);
   LaunchScope ls(p, kind, st);
-  k_cpass_tc<L, SIGN><<<blocks, tc::kThreads, C::SMEM, st>>>(in, out, Q, qtiles, ntiles, p->d_tw, p->twlog,
-                                                           scale, bops, p->d_err);
+  k_cpass_tc<L, SIGN><<<blocks, C::THREADS, C::SMEM, st>>>(in, out, Q, qtiles, ntiles, p->d_tw, p->twlog, scale,
+                                                         bops, p->d_err);
   return cudaGetLastError();
 }
 
