@@ -114,7 +114,9 @@ fftk_status fftk_c2r(fftk_plan p, const void *in, float *out, int batch, void *c
  * (tr S^2, tr R^2, tr S^3, tr R^2 S, tr R^2 S^2 with S, R the symmetric and
  * antisymmetric parts of A) to the stress in the eigenframe Q of S
  * (eigenvalues descending, each eigenvector's largest-magnitude component
- * positive); tau = Q tau' Q^T. */
+ * positive); tau = Q tau' Q^T.  The fused inference evaluates the network on
+ * the tensor cores like tarang_mlp_forward; an expired wait is reported by
+ * fftk_sync of the solver's plan. */
 typedef struct {
   const float *params;  /* device, 9094 FP32 values (layout of tarang_mlp_forward) */
   float in_shift[5];    /* network input x = (invariant - in_shift) * in_scale */
@@ -244,8 +246,15 @@ fftk_status tarang_closure_features(fftk_plan p, const float *ubar, const float 
 typedef struct tarang_mlp_s *tarang_mlp;
 fftk_status tarang_mlp_create(int max_batch, tarang_mlp *out);
 fftk_status tarang_mlp_destroy(tarang_mlp m);
+/* Inference runs on the tensor cores (tcgen05, kind::f16 with BF16 operands):
+ * each layer's BF16 input times its weights split into two BF16 parts
+ * W = W_hi + W_lo (16 significant bits), FP32 accumulation; bias and tanh in
+ * FP32.  A bounded wait that expires inside it is reported by tarang_mlp_sync. */
 fftk_status tarang_mlp_forward(tarang_mlp m, const float *params, const float *x, float *y, int B,
                                void *cuda_stream);
+/* Wait for the stream; FFTK_ERR_TIMEOUT if a tensor-core wait of this
+ * context's inference expired since the last call (the flag is cleared). */
+fftk_status tarang_mlp_sync(tarang_mlp m, void *cuda_stream);
 /* Mean-squared-error loss (1/(6B)) sum (y - t)^2 (device double, may be NULL)
  * and its gradient grad[9094] (device). */
 fftk_status tarang_mlp_loss_grad(tarang_mlp m, const float *params, const float *x, const float *t,

@@ -95,6 +95,7 @@ def lib() -> ctypes.CDLL:
             "tarang_mlp_create": ([i, c.POINTER(vp)], i),
             "tarang_mlp_destroy": ([vp], i),
             "tarang_mlp_forward": ([vp, vp, vp, vp, i, vp], i),
+            "tarang_mlp_sync": ([vp, vp], i),
             "tarang_mlp_loss_grad": ([vp, vp, vp, vp, i, vp, vp, vp], i),
             "tarang_mlp_adam": ([vp, vp, vp, vp, i, c.c_float, c.c_float, c.c_float, c.c_float, vp], i),
             "tarang_mlp_train_step": ([vp, vp, vp, vp, i, vp, vp, i, c.c_float, vp, vp], i),
@@ -249,6 +250,10 @@ def tarang_mlp_destroy(m: int) -> None:
 def tarang_mlp_forward(m: int, params_ptr, x_ptr, y_ptr, B: int, stream=0) -> None:
     _check(lib().tarang_mlp_forward(_vp(m), _vp(params_ptr), _vp(x_ptr), _vp(y_ptr), int(B), _vp(stream)),
            "tarang_mlp_forward")
+
+
+def tarang_mlp_sync(m: int, stream=0) -> None:
+    _check(lib().tarang_mlp_sync(_vp(m), _vp(stream)), "tarang_mlp_sync")
 
 
 def tarang_mlp_loss_grad(m: int, params_ptr, x_ptr, t_ptr, B: int, grad_ptr, loss_ptr, stream=0) -> None:

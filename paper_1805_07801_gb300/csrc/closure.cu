@@ -16,6 +16,7 @@
 
 #include "fft_engine.cuh"
 #include "internal.h"
+#include "tcgen05.cuh"
 
 namespace fftk {
 
@@ -379,91 +380,261 @@ __global__ void k_adam(float* __restrict__ p, float* __restrict__ m, float* __re
   p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
 }
 
-__global__ void __launch_bounds__(kChunk) k_mlp_forward(const float* __restrict__ params, const float* __restrict__ x,
-                                                        float* __restrict__ y, int B) {
-  extern __shared__ float smem_mlp[];
-  MLPSmem& s = *reinterpret_cast<MLPSmem*>(smem_mlp);
-  const int b = threadIdx.x;
-  const int base = blockIdx.x * kChunk;
-  const int nb = min(kChunk, B - base);
-  for (int i = b; i < kNP; i += kChunk) s.w[i] = params[i];
-  __syncthreads();
-  float out[6];
-  mlp_chunk_forward(s, x, nb, base, out);
-  if (b < nb)
-#pragma unroll
-    for (int o = 0; o < 6; ++o) y[(long long)(base + b) * 6 + o] = out[o];
-}
-
-// ------------------------------------------------- fused SGS inference ------
-// At each grid point of the coarse field: the gradient A -> invariants ->
-// normalised network input -> MLP (weights in shared memory, activations in
-// registers, rounded to bfloat16 like the training kernels) -> tau' -> tau =
-// Q tau' Q^T.  Writes tau[6][n^3].
+// Constants of the learned model (normalisation of inputs and outputs).
 struct SGSConst {
   float in_shift[5], in_scale[5], out_scale[6];
 };
 
-__global__ void __launch_bounds__(128) k_sgs_pointwise(const float* __restrict__ A9, long long R,
-                                                       const float* __restrict__ params, SGSConst cst,
-                                                       float* __restrict__ tau6) {
-  __shared__ float w[kNP];
-  for (int i = threadIdx.x; i < kNP; i += blockDim.x) w[i] = params[i];
+// --------------------------------------------- MLP on the tensor cores ---
+// Inference of the 5-64-64-64-6 network for 256 points per CTA pass (two
+// M = 128 blocks, one point per thread).  Every layer is one tcgen05 MMA chain
+// D = H W_hi^T + H W_lo^T: H is the layer's input in BF16 (the rounding the
+// network is defined with), W = W_hi + W_lo its FP32 weights split into two
+// BF16 parts (16 significant bits), FP32 accumulation in TMEM.  Bias, tanh and
+// the BF16 rounding of the next layer's input run on the CUDA cores; the input
+// x is padded to K = 16, the output layer to N = 16 (6 used).  Operands are
+// K-major without swizzle (B rows = output units).
+namespace mlptc {
+constexpr int kThreads = 256;
+constexpr int kBlocks = 2;
+constexpr int kW1 = 64 * 16 * 2;  // bytes of one BF16 part of W1 as B [64 x 16]
+constexpr int kW2 = 64 * 64 * 2;  // W2, W3 as B [64 x 64]
+constexpr int kW4 = 16 * 64 * 2;  // W4 as B [16 x 64]
+constexpr int kX = 128 * 16 * 2;  // one block of inputs as A [128 x 16]
+constexpr int kH = 128 * 64 * 2;  // one block of a hidden layer as A [128 x 64]
+constexpr int oW1 = 0, oW2 = oW1 + 2 * kW1, oW3 = oW2 + 2 * kW2, oW4 = oW3 + 2 * kW2;
+constexpr int oBias = oW4 + 2 * kW4;  // b1, b2, b3 (64 each), b4 (6): FP32
+constexpr int oX = oBias + 1024;
+constexpr int oH = oX + kBlocks * kX;
+constexpr int oBar = oH + kBlocks * kH;
+constexpr int kSmem = 1024 + oBar + 64;
+constexpr int kCols = 128;  // TMEM: 64 FP32 columns per block
+constexpr uint32_t kIdN64 = tcg::idesc_f16(128, 64, true);
+constexpr uint32_t kIdN16 = tcg::idesc_f16(128, 16, true);
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+__device__ __forceinline__ void store_split(unsigned char* hi, unsigned char* lo, int off, float w) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(w);
+  const __nv_bfloat16 l = __float2bfloat16_rn(w - __bfloat162float(h));
+  *reinterpret_cast<__nv_bfloat16*>(hi + off) = h;
+  *reinterpret_cast<__nv_bfloat16*>(lo + off) = l;
+}
+
+// weights as BF16 hi/lo B operands and biases, from the FP32 parameters
+__device__ void load_weights(unsigned char* base, const float* __restrict__ params) {
+  for (int e = threadIdx.x; e < 64 * 16; e += blockDim.x) {
+    const int o = e >> 4, i = e & 15;
+    store_split(base + oW1, base + oW1 + kW1, tcg::kmajor_off<16>(o, i), i < 5 ? params[o * 5 + i] : 0.f);
+  }
+  for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) {
+    const int off = tcg::kmajor_off<64>(e >> 6, e & 63);
+    store_split(base + oW2, base + oW2 + kW2, off, params[384 + e]);
+    store_split(base + oW3, base + oW3 + kW2, off, params[4544 + e]);
+  }
+  for (int e = threadIdx.x; e < 16 * 64; e += blockDim.x) {
+    const int o = e >> 6, i = e & 63;
+    store_split(base + oW4, base + oW4 + kW4, tcg::kmajor_off<64>(o, i), o < 6 ? params[8704 + o * 64 + i] : 0.f);
+  }
+  float* bias = reinterpret_cast<float*>(base + oBias);
+  for (int e = threadIdx.x; e < 198; e += blockDim.x)
+    bias[e] = e < 64 ? params[320 + e] : e < 128 ? params[4480 + e - 64] : e < 192 ? params[8640 + e - 128]
+                                                                                  : params[9088 + e - 192];
+}
+
+// the network input of thread t's point (row t & 127 of block t >> 7), rounded to BF16
+__device__ __forceinline__ void write_x(unsigned char* base, int t, const float x[5]) {
+  unsigned char* X = base + oX + (t >> 7) * kX;
+  const int r = t & 127;
+  *reinterpret_cast<uint4*>(X + tcg::kmajor_off<16>(r, 0)) =
+      make_uint4(pack_bf16(x[0], x[1]), pack_bf16(x[2], x[3]), pack_bf16(x[4], 0.f), 0u);
+  *reinterpret_cast<uint4*>(X + tcg::kmajor_off<16>(r, 8)) = make_uint4(0u, 0u, 0u, 0u);
+}
+
+// the four layers for the CTA's 256 points (after write_x by every thread);
+// y = this thread's 6 outputs.  False if an MMA wait expired (uniform over the CTA).
+__device__ bool forward(unsigned char* base, uint32_t tmem, uint64_t* bar, uint32_t& phase, float y[6]) {
+  const int t = threadIdx.x, warp = t >> 5, blk = t >> 7, r = t & 127;
+  const uint32_t row_addr = tmem + (((uint32_t)(warp & 3) * 32u) << 16) + 64u * (uint32_t)blk;
+  const uint32_t sb = tcg::su32(base);
+  const float* bias = reinterpret_cast<const float*>(base + oBias);
+  unsigned char* H = base + oH + blk * kH;
+#pragma unroll 1
+  for (int l = 0; l < 4; ++l) {
+    tcg::fence_smem_async();
+    tcg::fence_before_sync();
+    __syncthreads();
+    tcg::fence_after_sync();
+    if (t == 0) {
+#pragma unroll
+      for (int b = 0; b < kBlocks; ++b) {
+        const uint32_t d = tmem + 64u * b;
+        if (l == 0) {
+          const uint32_t a = sb + oX + b * kX;
+          tcg::mma_f16(d, tcg::desc(a, 128, 256), tcg::desc(sb + oW1, 128, 256), kIdN64, 0);
+          tcg::mma_f16(d, tcg::desc(a, 128, 256), tcg::desc(sb + oW1 + kW1, 128, 256), kIdN64, 1);
+        } else {
+          const uint32_t a = sb + oH + b * kH;
+          const uint32_t whi = sb + (l == 1 ? oW2 : l == 2 ? oW3 : oW4);
+          const uint32_t wlo = whi + (l == 3 ? kW4 : kW2);
+          const uint32_t id = l == 3 ? kIdN16 : kIdN64;
+#pragma unroll
+          for (int s = 0; s < 4; ++s) {
+            tcg::mma_f16(d, tcg::desc(a + 256 * s, 128, 1024), tcg::desc(whi + 256 * s, 128, 1024), id, s > 0);
+            tcg::mma_f16(d, tcg::desc(a + 256 * s, 128, 1024), tcg::desc(wlo + 256 * s, 128, 1024), id, 1);
+          }
+        }
+      }
+      tcg::commit(bar);
+    }
+    bool ok = true;
+    if (t == 0) {
+      ok = tcg::mbar_wait(bar, phase);
+      tcg::fence_after_sync();
+      tcg::fence_before_sync();
+    }
+    phase ^= 1;
+    const bool all = __syncthreads_and(ok) != 0;
+    tcg::fence_after_sync();
+    if (!all) return false;
+    if (l < 3) {
+      // next layer's input, over this layer's (whose MMAs have completed)
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        float d[32];
+        tcg::ld32(row_addr + 32u * hh, d);
+        uint32_t pk[16];
+#pragma unroll
+        for (int j = 0; j < 32; j += 2) {
+          const float* bl = bias + 64 * l + 32 * hh + j;
+          pk[j / 2] = pack_bf16(tanhf(d[j] + bl[0]), tanhf(d[j + 1] + bl[1]));
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          *reinterpret_cast<uint4*>(H + tcg::kmajor_off<64>(r, 32 * hh + 8 * q)) =
+              make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+      }
+    } else {
+      float d[8];
+      tcg::ld8(row_addr, d);
+#pragma unroll
+      for (int o = 0; o < 6; ++o) y[o] = d[o] + bias[192 + o];
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ unsigned char* aligned_base(unsigned char* raw) {
+  return raw + ((1024 - (tcg::su32(raw) & 1023)) & 1023);
+}
+
+// CTA setup: weights, TMEM, mbarrier
+__device__ __forceinline__ uint32_t setup(unsigned char* base, const float* __restrict__ params) {
+  uint64_t* bar = reinterpret_cast<uint64_t*>(base + oBar);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
+  load_weights(base, params);
+  if ((threadIdx.x >> 5) == 0) tcg::tmem_alloc(tslot, kCols);
+  if (threadIdx.x == 0) tcg::mbar_init(bar);
+  tcg::fence_smem_async();
+  tcg::fence_before_sync();
   __syncthreads();
-  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < R;
-       c += (long long)gridDim.x * blockDim.x) {
+  tcg::fence_after_sync();
+  return *tslot;
+}
+
+// CTA teardown; on failure flags `err` and lets the pending MMAs drain (bounded)
+__device__ __forceinline__ void finish(unsigned char* base, uint32_t tmem, uint32_t phase, bool failed, int* err) {
+  uint64_t* bar = reinterpret_cast<uint64_t*>(base + oBar);
+  if (failed && threadIdx.x == 0) {
+    atomicOr(err, 1);
+    tcg::mbar_wait(bar, phase ^ 1);
+  }
+  tcg::fence_before_sync();
+  __syncthreads();
+  if ((threadIdx.x >> 5) == 0) tcg::tmem_dealloc(tmem, kCols);
+}
+}  // namespace mlptc
+
+// Fused SGS inference with the network on the tensor cores: per point the
+// gradient A -> invariants and strain eigenframe -> normalised input -> MLP
+// -> tau' -> tau = Q tau' Q^T.  Writes tau[6][n^3].
+__global__ void __launch_bounds__(mlptc::kThreads, 2)
+    k_sgs_pointwise_tc(const float* __restrict__ A9, long long R, const float* __restrict__ params, SGSConst cst,
+                       float* __restrict__ tau6, int* err) {
+  extern __shared__ __align__(1024) unsigned char smraw_tc[];
+  unsigned char* base = mlptc::aligned_base(smraw_tc);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(base + mlptc::oBar);
+  const uint32_t tmem = mlptc::setup(base, params);
+  const int t = threadIdx.x;
+  uint32_t phase = 0;
+  bool failed = false;
+  for (long long c0 = (long long)blockIdx.x * mlptc::kThreads; c0 < R; c0 += (long long)gridDim.x * mlptc::kThreads) {
+    const long long c = c0 + t;
+    const bool valid = c < R;
     float A[9], S[9], inv[5], Q[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) A[i] = A9[i * R + c];
+    for (int i = 0; i < 9; ++i) A[i] = valid ? A9[i * R + c] : 0.f;
     point_invariants(A, S, inv);
     point_eig3(S, Q);
-    float a[64], z[64];
+    float x[5];
 #pragma unroll
-    for (int i = 0; i < 5; ++i) a[i] = bf16r((inv[i] - cst.in_shift[i]) * cst.in_scale[i]);
-    // layer 1 (5 -> 64)
-#pragma unroll
-    for (int o = 0; o < 64; ++o) {
-      float acc = w[320 + o];
-#pragma unroll
-      for (int i = 0; i < 5; ++i) acc = fmaf(w[o * 5 + i], a[i], acc);
-      z[o] = bf16r(tanhf(acc));
-    }
-    // layers 2, 3 (64 -> 64)
-#pragma unroll 1
-    for (int l = 1; l < 3; ++l) {
-      const float* W = w + (l == 1 ? 384 : 4544);
-      const float* bias = w + (l == 1 ? 4480 : 8640);
-#pragma unroll
-      for (int i = 0; i < 64; ++i) a[i] = z[i];
-#pragma unroll 4
-      for (int o = 0; o < 64; ++o) {
-        float acc = bias[o];
-#pragma unroll
-        for (int i = 0; i < 64; ++i) acc = fmaf(W[o * 64 + i], a[i], acc);
-        z[o] = bf16r(tanhf(acc));
-      }
-    }
-    // output layer (64 -> 6): tau' in the eigenframe
+    for (int i = 0; i < 5; ++i) x[i] = (inv[i] - cst.in_shift[i]) * cst.in_scale[i];
+    mlptc::write_x(base, t, x);
     float t6[6];
-#pragma unroll
-    for (int o = 0; o < 6; ++o) {
-      float acc = w[9088 + o];
-#pragma unroll
-      for (int i = 0; i < 64; ++i) acc = fmaf(w[8704 + o * 64 + i], z[i], acc);
-      t6[o] = acc * cst.out_scale[o];
+    if (!mlptc::forward(base, tmem, bar, phase, t6)) {
+      failed = true;
+      break;
     }
-    float T[9], tmp[9], out[9], QT[9];
-    sym_from6(t6, T);
+    if (valid) {
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
+      for (int o = 0; o < 6; ++o) t6[o] *= cst.out_scale[o];
+      float T[9], tmp[9], out[9], QT[9];
+      sym_from6(t6, T);
 #pragma unroll
-      for (int j = 0; j < 3; ++j) QT[i * 3 + j] = Q[j * 3 + i];
-    m3mul(Q, T, tmp);
-    m3mul(tmp, QT, out);
-    sym_to6(out, t6);
+      for (int i = 0; i < 3; ++i)
 #pragma unroll
-    for (int i = 0; i < 6; ++i) tau6[i * R + c] = t6[i];
+        for (int j = 0; j < 3; ++j) QT[i * 3 + j] = Q[j * 3 + i];
+      m3mul(Q, T, tmp);
+      m3mul(tmp, QT, out);
+      sym_to6(out, t6);
+#pragma unroll
+      for (int i = 0; i < 6; ++i) tau6[i * R + c] = t6[i];
+    }
   }
+  mlptc::finish(base, tmem, phase, failed, err);
+}
+
+// Plain inference y[B][6] = MLP(x[B][5]) with the network on the tensor cores.
+__global__ void __launch_bounds__(mlptc::kThreads, 2)
+    k_mlp_forward_tc(const float* __restrict__ params, const float* __restrict__ x, float* __restrict__ y,
+                     long long B, int* err) {
+  extern __shared__ __align__(1024) unsigned char smraw_tc[];
+  unsigned char* base = mlptc::aligned_base(smraw_tc);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(base + mlptc::oBar);
+  const uint32_t tmem = mlptc::setup(base, params);
+  const int t = threadIdx.x;
+  uint32_t phase = 0;
+  bool failed = false;
+  for (long long c0 = (long long)blockIdx.x * mlptc::kThreads; c0 < B; c0 += (long long)gridDim.x * mlptc::kThreads) {
+    const long long c = c0 + t;
+    const bool valid = c < B;
+    float xi[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) xi[i] = valid ? x[c * 5 + i] : 0.f;
+    mlptc::write_x(base, t, xi);
+    float out[6];
+    if (!mlptc::forward(base, tmem, bar, phase, out)) {
+      failed = true;
+      break;
+    }
+    if (valid)
+#pragma unroll
+      for (int o = 0; o < 6; ++o) y[c * 6 + o] = out[o];
+  }
+  mlptc::finish(base, tmem, phase, failed, err);
 }
 
 // SGS force s_i = -i k_j tau_hat_ij on the 2/3 set, projected; written to s (3 fields)
@@ -516,15 +687,28 @@ static cudaError_t mlp_attrs() {
   std::call_once(once, [] {
     err = cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mlp_smem());
     if (err == cudaSuccess)
-      err = cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mlp_smem());
+      err = cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, mlptc::kSmem);
+    if (err == cudaSuccess)
+      err = cudaFuncSetAttribute(k_sgs_pointwise_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, mlptc::kSmem);
   });
   return err;
+}
+
+// persistent grid of the tensor-core inference kernels: two CTAs per SM
+static int mlptc_grid(long long points) {
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long need = (points + mlptc::kThreads - 1) / mlptc::kThreads;
+  const long long cap = 2LL * sms;
+  return (int)(need < cap ? need : cap);
 }
 
 }  // namespace fftk
 
 struct tarang_mlp_s {
   int max_batch = 0;
+  int* err = nullptr;           // device word: a tensor-core wait expired
   float* part = nullptr;        // [blocks][9094]
   double* loss_part = nullptr;  // [blocks]
   float* grad = nullptr;        // [9094]
@@ -632,11 +816,14 @@ extern "C" fftk_status tarang_mlp_create(int max_batch, tarang_mlp* out) {
   cudaError_t e = cudaMalloc(&m->part, sizeof(float) * (size_t)nblk * kNP);
   if (e == cudaSuccess) e = cudaMalloc(&m->loss_part, sizeof(double) * (size_t)nblk);
   if (e == cudaSuccess) e = cudaMalloc(&m->grad, sizeof(float) * kNP);
+  if (e == cudaSuccess) e = cudaMalloc(&m->err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(m->err, 0, sizeof(int));
   if (e == cudaSuccess) e = mlp_attrs();
   if (e != cudaSuccess) {
     cudaFree(m->part);
     cudaFree(m->loss_part);
     cudaFree(m->grad);
+    cudaFree(m->err);
     delete m;
     cudaGetLastError();
     return FFTK_ERR_OOM;
@@ -651,6 +838,7 @@ extern "C" fftk_status tarang_mlp_destroy(tarang_mlp m) {
   cudaFree(m->part);
   cudaFree(m->loss_part);
   cudaFree(m->grad);
+  cudaFree(m->err);
   delete m;
   return FFTK_OK;
 }
@@ -658,9 +846,24 @@ extern "C" fftk_status tarang_mlp_destroy(tarang_mlp m) {
 extern "C" fftk_status tarang_mlp_forward(tarang_mlp m, const float* params, const float* x, float* y, int B,
                                           void* cuda_stream) {
   if (!m || !params || !x || !y || B < 1) return FFTK_ERR_INVALID_ARG;
-  const int nblk = (B + kChunk - 1) / kChunk;
-  k_mlp_forward<<<nblk, kChunk, mlp_smem(), static_cast<cudaStream_t>(cuda_stream)>>>(params, x, y, B);
+  k_mlp_forward_tc<<<mlptc_grid(B), mlptc::kThreads, mlptc::kSmem, static_cast<cudaStream_t>(cuda_stream)>>>(
+      params, x, y, B, m->err);
   return from_cuda(cudaGetLastError());
+}
+
+extern "C" fftk_status tarang_mlp_sync(tarang_mlp m, void* cuda_stream) {
+  if (!m) return FFTK_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, m->err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return from_cuda(e);
+  if (h) {
+    e = cudaMemsetAsync(m->err, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? FFTK_ERR_TIMEOUT : from_cuda(e);
+  }
+  return FFTK_OK;
 }
 
 extern "C" fftk_status tarang_mlp_loss_grad(tarang_mlp m, const float* params, const float* x, const float* t,
@@ -710,6 +913,8 @@ cudaError_t sgs_term(fftk_plan p, fftk_sgs_work** wp, const float2* u, const tar
                      cudaStream_t st, const float2** out) {
   const int n = p->nx;
   const long long R = (long long)n * n * n, M = (long long)n * n * (n / 2 + 1);
+  const cudaError_t ea = mlp_attrs();
+  if (ea != cudaSuccess) return ea;
   if (!*wp) {
     fftk_sgs_work* w = new (std::nothrow) fftk_sgs_work;
     if (!w) return cudaErrorMemoryAllocation;
@@ -737,7 +942,8 @@ cudaError_t sgs_term(fftk_plan p, fftk_sgs_work** wp, const float2* u, const tar
   std::memcpy(c.out_scale, model->out_scale, sizeof(c.out_scale));
   {
     LaunchScope ls(p, KK_AUX, st);
-    k_sgs_pointwise<<<grid_for(R, 128), 128, 0, st>>>(w->A, R, model->params, c, w->tau);
+    k_sgs_pointwise_tc<<<mlptc_grid(R), mlptc::kThreads, mlptc::kSmem, st>>>(w->A, R, model->params, c, w->tau,
+                                                                            p->d_err);
   }
   if (fftk_r2c(p, w->tau, w->th, 6, st) != FFTK_OK) return cudaErrorLaunchFailure;
   {

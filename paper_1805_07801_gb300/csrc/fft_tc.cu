@@ -28,6 +28,7 @@
 
 #include "fft_engine.cuh"
 #include "internal.h"
+#include "tcgen05.cuh"
 
 namespace fftk {
 namespace tc {
@@ -37,17 +38,12 @@ constexpr uint32_t kSBO = 1024;          // bytes between 8-row groups (64 FP16 
 constexpr int kBlkBytes = 16 * 1024;     // one M block of A
 constexpr int kBlkStride = kBlkBytes + 16;  // + 16 bytes: spreads blocks over banks
 constexpr int kBBytes = 4 * 1024;        // one 32 x 64 operand
-constexpr long long kSpinLimit = 1LL << 26;
 
-__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+using tcg::su32;
+using tcg::ld32;
+using tcg::mbar_wait;
 
-__device__ __forceinline__ uint64_t desc(uint32_t addr) {
-  uint64_t d = (uint64_t)((addr >> 4) & 0x3FFF);
-  d |= (uint64_t)((kLBO >> 4) & 0x3FFF) << 16;
-  d |= (uint64_t)((kSBO >> 4) & 0x3FFF) << 32;
-  d |= (uint64_t)1 << 46;  // tcgen05 descriptor version; no swizzle
-  return d;
-}
+__device__ __forceinline__ uint64_t desc(uint32_t addr) { return tcg::desc(addr, kLBO, kSBO); }
 
 // byte offset of element (row, k) inside the A tile
 __device__ __forceinline__ int a_off(int row, int k) {
@@ -56,42 +52,10 @@ __device__ __forceinline__ int a_off(int row, int k) {
 }
 
 // D = F32, A = B = F16, both K-major, N = 32, M = 128
-constexpr uint32_t kIdesc = (1u << 4) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+constexpr uint32_t kIdesc = tcg::idesc_f16(128, 32, false);
 
 __device__ __forceinline__ void mma(uint32_t dtm, uint64_t ad, uint64_t bd, uint32_t acc) {
-  asm volatile(
-      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtm),
-      "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc));
-}
-
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
-  uint32_t done = 0;
-  for (long long it = 0; it < kSpinLimit; ++it) {
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        "selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(su32(bar)), "r"(phase));
-    if (done) return true;
-  }
-  return false;
-}
-
-__device__ __forceinline__ void ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
-      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
-        "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
-        "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+  tcg::mma_f16(dtm, ad, bd, kIdesc, acc);
 }
 
 // hi/lo split of one complex value, packed (hi.re, hi.im, lo.re, lo.im)
