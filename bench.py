@@ -89,6 +89,7 @@ def fft_pass_bytes(n):
 KERNEL_SOURCES = {
     "ns": ["ns.cu", "fft_engine.cuh", "internal.h"],
     "fft": ["fft_passes.cu", "fft_engine.cuh", "internal.h"],
+    "fft16": ["fft_tc.cu", "tcgen05.cuh", "fft_passes.cu", "fft_engine.cuh", "internal.h"],
 }
 
 
@@ -113,7 +114,7 @@ def measured_traffic(kernel: str, workload: str):
     for line in open(path):
         parts = line.split()
         if len(parts) >= 4 and not line.startswith("#") and parts[0] == kernel and parts[1] == workload:
-            group = "ns" if kernel.startswith("ns_") else "fft"
+            group = "ns" if kernel.startswith("ns_") else ("fft16" if workload.endswith("s16") else "fft")
             if parts[3] == source_hash(group):
                 return int(float(parts[2]))
     return None

@@ -146,7 +146,8 @@ __device__ void point_eig3(const float S[9], float Q[9]) {
 #pragma unroll
   for (int i = 0; i < 9; ++i) a[i] = S[i];
   for (int sweep = 0; sweep < 12; ++sweep) {
-    if (a[1] == 0.f && a[2] == 0.f && a[5] == 0.f) break;
+    // converged to FP32 resolution: off-diagonal mass below 1e-7 of the diagonal's
+    if (fabsf(a[1]) + fabsf(a[2]) + fabsf(a[5]) <= 1e-7f * (fabsf(a[0]) + fabsf(a[4]) + fabsf(a[8]))) break;
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
       const int p = r == 2 ? 1 : 0, q = r == 0 ? 1 : 2;
@@ -391,7 +392,8 @@ struct SGSConst {
 // D = H W_hi^T + H W_lo^T: H is the layer's input in BF16 (the rounding the
 // network is defined with), W = W_hi + W_lo its FP32 weights split into two
 // BF16 parts (16 significant bits), FP32 accumulation in TMEM.  Bias, tanh and
-// the BF16 rounding of the next layer's input run on the CUDA cores; the input
+// the BF16 rounding of the next layer's input run on the CUDA cores (tanh as
+// a rational function accurate to the BF16 rounding, tanh_to_bf16); the input
 // x is padded to K = 16, the output layer to N = 16 (6 used).  Operands are
 // K-major without swizzle (B rows = output units).
 namespace mlptc {
@@ -415,6 +417,20 @@ constexpr uint32_t kIdN16 = tcg::idesc_f16(128, 16, true);
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// tanh x for a value that is rounded to BF16 next: the convergent of Lambert's
+// continued fraction tanh x = x / (1 + x^2 / (3 + x^2 / (5 + ...))) through the
+// term 17, x P(y) / Q(y) with y = x^2,
+//   P = 34459425 + 4729725 y + 135135 y^2 + 990 y^3 + y^4,
+//   Q = 34459425 + 16216200 y + 945945 y^2 + 13860 y^3 + 45 y^4
+// (both divided by 34459425 below); relative error below 3e-7 in FP32 for
+// |x| < 3.5.  For |x| >= 3.5 the BF16 rounding of tanh x is exactly +-1.
+__device__ __forceinline__ float tanh_to_bf16(float x) {
+  const float y = x * x;
+  const float p = fmaf(fmaf(fmaf(fmaf(1.f / 34459425.f, y, 2.f / 69615.f), y, 1.f / 255.f), y, 7.f / 51.f), y, 1.f);
+  const float q = fmaf(fmaf(fmaf(fmaf(1.f / 765765.f, y, 4.f / 9945.f), y, 7.f / 255.f), y, 8.f / 17.f), y, 1.f);
+  return fabsf(x) >= 3.5f ? copysignf(1.f, x) : x * __fdividef(p, q);
 }
 
 __device__ __forceinline__ void store_split(unsigned char* hi, unsigned char* lo, int off, float w) {
@@ -510,7 +526,7 @@ __device__ bool forward(unsigned char* base, uint32_t tmem, uint64_t* bar, uint3
 #pragma unroll
         for (int j = 0; j < 32; j += 2) {
           const float* bl = bias + 64 * l + 32 * hh + j;
-          pk[j / 2] = pack_bf16(tanhf(d[j] + bl[0]), tanhf(d[j + 1] + bl[1]));
+          pk[j / 2] = pack_bf16(tanh_to_bf16(d[j] + bl[0]), tanh_to_bf16(d[j + 1] + bl[1]));
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q)
