@@ -627,6 +627,82 @@ def run_forced(n: int, steps: int):
                       "history": hist, "EK_final": [float(v) for v in EK[:65]]}), flush=True)
 
 
+def run_fft_sweep(args):
+    """Batched R2C + C2R pairs with B * N^3 = 2^30 reals: 256^3 x 64, 512^3 x 8,
+    1024^3 and 2048^3, each in FP32 and in split-FP16.  Pairs/s (CUDA events,
+    20 pairs after 3), the fraction of the pair roofline (8R + 80M bytes per
+    field) of measured HBM, the round-trip error, and the split-FP16 spectrum
+    against the FP32 GPU spectrum (the comparison prescribed at 2048^3; parity
+    with the oracle up to 1024^3 is the tests').  Prints one JSON line."""
+    import torch
+
+    import paper_1805_07801_gb300 as fk
+    from paper_1805_07801_gb300 import build as fkbuild
+
+    fkbuild.build()
+    dev = torch.device("cuda:0")
+    st_obj = torch.cuda.Stream(dev)
+    st = st_obj.cuda_stream
+    hbm, peak_kind = peaks()
+
+    def rel_l2(a, b):  # ||a - b|| / ||b||, FP64 sums over slices (no full-size temporaries)
+        a2, b2 = a.reshape(-1, a.shape[-1]), b.reshape(-1, b.shape[-1])
+        num = den = 0.0
+        for i in range(0, a2.shape[0], 1 << 16):
+            d = (a2[i:i + (1 << 16)].double() - b2[i:i + (1 << 16)].double())
+            num += float((d * d).sum())
+            den += float((b2[i:i + (1 << 16)].double() ** 2).sum())
+        return (num / den) ** 0.5
+
+    out = []
+    for n, B in ((256, 64), (512, 8), (1024, 1), (2048, 1)):
+        R, M = n**3, n * n * (n // 2 + 1)
+        pair = B * (8 * R + 80 * M)
+        with torch.cuda.stream(st_obj):
+            x = torch.empty((B, n, n, n), dtype=torch.float32, device=dev)
+            fk.fftk_fill_normal(x.data_ptr(), B * R, SEED, 0, st)
+            F = torch.empty((B, n, n, n // 2 + 1, 2), dtype=torch.float32, device=dev)
+            y = torch.empty_like(x)
+        row = {"n": n, "batch": B, "pair_bytes": pair}
+        F32 = None
+        for dtype, key in ((fk.FFTK_R32, "fp32"), (fk.FFTK_R32_SPLIT16, "split16")):
+            plan = fk.fftk_plan_create(n, n, n, dtype)
+            try:
+                for _ in range(3):
+                    fk.fftk_r2c(plan, x.data_ptr(), F.data_ptr(), B, st)
+                    fk.fftk_c2r(plan, F.data_ptr(), y.data_ptr(), B, st)
+                torch.cuda.synchronize(dev)
+                kp = 20
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(st_obj)
+                for _ in range(kp):
+                    fk.fftk_r2c(plan, x.data_ptr(), F.data_ptr(), B, st)
+                    fk.fftk_c2r(plan, F.data_ptr(), y.data_ptr(), B, st)
+                e1.record(st_obj)
+                torch.cuda.synchronize(dev)
+                fk.fftk_sync(plan, st)
+                ms = e0.elapsed_time(e1) / kp
+                rt = rel_l2(y, x)
+                r = {"pairs_s": round(B * 1e3 / ms, 3), "ms_per_batch": round(ms, 4),
+                     "frac_pair": round(pair / (ms * 1e-3) / 1e9 / hbm, 4), "round_trip_rel_l2": rt}
+                fk.fftk_r2c(plan, x.data_ptr(), F.data_ptr(), B, st)
+                torch.cuda.synchronize(dev)
+                if key == "fp32":
+                    F32 = F.clone()
+                else:
+                    r["rel_l2_vs_fp32_spectrum"] = rel_l2(F, F32)
+                row[key] = r
+            finally:
+                fk.fftk_plan_destroy(plan)
+        row["split16_speedup"] = round(row["split16"]["pairs_s"] / row["fp32"]["pairs_s"], 4)
+        out.append(row)
+        del x, F, y, F32
+        torch.cuda.empty_cache()
+    print(json.dumps({"workload": "batched R2C+C2R pairs of normal(0,1) fields, seed 0, B*N^3 = 2^30",
+                      "peak_GBps": hbm, "peak_kind": peak_kind, "sizes": out}), flush=True)
+
+
 def run_closure(which: str, out_path: str):
     """The learned-closure workflow (resolved snapshots -> filtered data ->
     training -> coarse runs with and without the model); prints one JSON line
@@ -669,6 +745,7 @@ def main():
     ap.add_argument("--closure", choices=["full", "small"], default=None,
                     help="run the learned-closure workflow instead of the benchmark")
     ap.add_argument("--closure-out", default="", help="JSON file for the closure workflow's results")
+    ap.add_argument("--fft-sweep", action="store_true", help="batched pair sweep 256^3 x 64 ... 2048^3")
     ap.add_argument("--forced", type=int, default=0, metavar="N",
                     help="run N^3 forced turbulence for --steps steps and print its JSON line")
     args = ap.parse_args()
@@ -680,6 +757,9 @@ def main():
         return
     if args.forced:
         run_forced(args.forced, args.steps)
+        return
+    if args.fft_sweep:
+        run_fft_sweep(args)
         return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
