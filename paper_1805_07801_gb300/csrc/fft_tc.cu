@@ -102,7 +102,8 @@ struct TC2 {
   static constexpr int LOGT = Log2<T>::value;
   static constexpr int LOGL = Log2<L>::value;
   static constexpr int ABYTES = BLOCKS * tc::kBlkStride;
-  static constexpr size_t SMEM = 1024 + ABYTES + 2 * tc::kBBytes + 256 * sizeof(float2) + sizeof(float) * T + 64;
+  static constexpr size_t SMEM =
+      1024 + ABYTES + 2 * tc::kBBytes + (256 + L) * sizeof(float2) + sizeof(float) * T + 64;
   static constexpr int MINB = 1024 / THREADS;  // 64 registers
   static_assert(THREADS % 128 == 0 && (COLS & (COLS - 1)) == 0 && SMEM <= 227 * 1024, "tile shape");
 };
@@ -179,7 +180,8 @@ __global__ void __launch_bounds__(TC2<L>::THREADS, TC2<L>::MINB)
   unsigned char* As = base;                                          // A tile (both stages)
   unsigned char* Bs = base + C::ABYTES;                              // B1, B2
   float2* w256 = reinterpret_cast<float2*>(Bs + 2 * tc::kBBytes);   // W_256^m / 16
-  float* colmax = reinterpret_cast<float*>(w256 + 256);
+  float2* wL = w256 + 256;                                            // W_L^m (conjugated for SIGN > 0)
+  float* colmax = reinterpret_cast<float*>(wL + L);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(colmax + T);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
   const int t = threadIdx.x, warp = t >> 5;
@@ -196,6 +198,11 @@ __global__ void __launch_bounds__(TC2<L>::THREADS, TC2<L>::MINB)
     float2 w = __ldg(&tw[i << (twlog - 8)]);
     if (SIGN > 0) w.y = -w.y;
     w256[i] = make_float2(w.x * 0.0625f, w.y * 0.0625f);
+  }
+  for (int i = t; i < L; i += NT) {
+    float2 w = __ldg(&tw[i << (twlog - C::LOGL)]);
+    if (SIGN > 0) w.y = -w.y;
+    wL[i] = w;
   }
   if (t < T) colmax[t] = 0.f;
   if (warp == 0) {
@@ -274,10 +281,7 @@ __global__ void __launch_bounds__(TC2<L>::THREADS, TC2<L>::MINB)
         const int a = a0 + 16 * (A1 * u + i);
         dftR<R0, SIGN>(z[i]);
 #pragma unroll
-        for (int r = 1; r < R0; ++r) {
-          const float2 w = __ldg(&tw[(a * r) << (twlog - C::LOGL)]);
-          z[i][r] = SIGN < 0 ? cmul(z[i][r], w) : cmulc(z[i][r], w);
-        }
+        for (int r = 1; r < R0; ++r) z[i][r] = cmul(z[i][r], wL[a * r]);
       }
 #pragma unroll
       for (int r = 0; r < R0; ++r) mx = fmaxf(mx, fmaxf(fabsf(z[i][r].x), fabsf(z[i][r].y)));
