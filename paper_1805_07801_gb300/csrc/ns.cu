@@ -175,28 +175,33 @@ struct NZCfg {
   static constexpr int H = N / 2;
   static constexpr int G = H < 8 ? H : 8;
   static constexpr int S = H / G;
-  static constexpr int LPC = S >= 256 ? 1 : 256 / S;
+  static constexpr int LPC = S >= 128 ? 1 : 128 / S;
   static constexpr int THREADS = LPC * S;
   static constexpr bool WARP = S <= 32;
+  static constexpr size_t SMEM = sizeof(float2) * (size_t)LPC * H * 4;  // exchange + 3 parked fields
 };
 
 // 3. per (x, y) line: the six c2r transforms, the product n = u x omega and
 //    the three r2c transforms.  Reads k_z < kc of fields 0..5, writes k_z < kc
 //    of fields 0..2 (in place: a line is fully read before it is written).
+//    The three velocity components are parked in real space in shared memory;
+//    each vorticity component is then transformed and folded into the
+//    accumulators of n, so at most 3 fields are held in registers.
 template <int N>
-__global__ void __launch_bounds__(NZCfg<N>::THREADS)
+__global__ void __launch_bounds__(NZCfg<N>::THREADS, 3)
     k_ns_z(float2* w, NSGeom g, const float2* __restrict__ tw, int twlog) {
   using C = NZCfg<N>;
   constexpr int H = C::H, G = C::G, S = C::S;
   constexpr int LOGN = Log2<N>::value;
-  __shared__ float2 sm[C::LPC * H];
+  extern __shared__ float2 smz[];
   const int li = threadIdx.x / S, j = threadIdx.x % S;
   const long long line = (long long)blockIdx.x * C::LPC + li;
   const bool valid = line < (long long)N * N;
-  const LineX<C::WARP> xc{sm + li * H};
-  float2 U[6][G];
-#pragma unroll
-  for (int f = 0; f < 6; ++f) {
+  const LineX<C::WARP> xc{smz + li * H};
+  float2* park = smz + C::LPC * H + li * 3 * H + j;  // [3][G][S] per line, this thread's column
+
+  // inverse z transform of field f (half-complex -> N real points, two per slot)
+  auto c2r = [&](int f, float2 (&U)[G]) {
     const float2* src = w + f * g.M + line * g.h1;
 #pragma unroll
     for (int m = 0; m < G; ++m) {
@@ -212,30 +217,31 @@ __global__ void __launch_bounds__(NZCfg<N>::THREADS)
       const float2 E = cadd(A, Bc);
       const float2 W = __ldg(&tw[k << (twlog - LOGN)]);
       const float2 O = cmulc(csub(A, Bc), W);
-      U[f][m] = make_float2(E.x - O.y, E.y + O.x);
+      U[m] = make_float2(E.x - O.y, E.y + O.x);
     }
-    fft_line<H, G, +1>(U[f], j, xc, tw, twlog);
+    fft_line<H, G, +1>(U, j, xc, tw, twlog);
+  };
+
+  {
+    float2 U[G];
+#pragma unroll 1
+    for (int f = 0; f < 3; ++f) {
+      c2r(f, U);
+#pragma unroll
+      for (int m = 0; m < G; ++m) park[(f * G + m) * S] = U[m];
+    }
   }
-  // n = u x omega at the two real points held by each complex slot
+  // forward z transforms of n (N real points -> half-complex), k_z < kc written
+  auto r2c = [&](int f, float2 (&U)[G]) {
+    fft_line<H, G, -1>(U, j, xc, tw, twlog);
 #pragma unroll
-  for (int m = 0; m < G; ++m) {
-    const float2 ux = U[0][m], uy = U[1][m], uz = U[2][m];
-    const float2 wx = U[3][m], wy = U[4][m], wz = U[5][m];
-    U[0][m] = make_float2(uy.x * wz.x - uz.x * wy.x, uy.y * wz.y - uz.y * wy.y);
-    U[1][m] = make_float2(uz.x * wx.x - ux.x * wz.x, uz.y * wx.y - ux.y * wz.y);
-    U[2][m] = make_float2(ux.x * wy.x - uy.x * wx.x, ux.y * wy.y - uy.y * wx.y);
-  }
-#pragma unroll
-  for (int f = 0; f < 3; ++f) {
-    fft_line<H, G, -1>(U[f], j, xc, tw, twlog);
-#pragma unroll
-    for (int m = 0; m < G; ++m) xc.st(j + m * S, U[f][m]);
+    for (int m = 0; m < G; ++m) xc.st(j + m * S, U[m]);
     xc.sync();
     float2* dst = w + f * g.M + line * g.h1;
 #pragma unroll
     for (int m = 0; m < G; ++m) {
       const int k = j + m * S;
-      const float2 A = U[f][m];
+      const float2 A = U[m];
       const float2 Bc = cconj(xc.ld((H - k) & (H - 1)));
       const float2 E = cscale(cadd(A, Bc), 0.5f);
       const float2 D = csub(A, Bc);
@@ -244,7 +250,44 @@ __global__ void __launch_bounds__(NZCfg<N>::THREADS)
       if (valid && k < g.kc) dst[k] = cadd(E, cmul(W, O));
     }
     xc.sync();
+  };
+  // n = u x omega at the two real points held by each slot:
+  //   n_x = u_y w_z - u_z w_y,  n_y = u_z w_x - u_x w_z,  n_z = u_x w_y - u_y w_x
+  // n_z is complete after omega_y and is transformed before omega_z is loaded.
+  float2 Ny[G], Nx[G];
+  {
+    float2 Nz[G];
+    {
+      float2 W[G];
+      c2r(3, W);  // omega_x
+#pragma unroll
+      for (int m = 0; m < G; ++m) {
+        const float2 uy = park[(1 * G + m) * S], uz = park[(2 * G + m) * S];
+        Ny[m] = make_float2(uz.x * W[m].x, uz.y * W[m].y);
+        Nz[m] = make_float2(-uy.x * W[m].x, -uy.y * W[m].y);
+      }
+      c2r(4, W);  // omega_y
+#pragma unroll
+      for (int m = 0; m < G; ++m) {
+        const float2 ux = park[(0 * G + m) * S], uz = park[(2 * G + m) * S];
+        Nx[m] = make_float2(-uz.x * W[m].x, -uz.y * W[m].y);
+        Nz[m] = make_float2(fmaf(ux.x, W[m].x, Nz[m].x), fmaf(ux.y, W[m].y, Nz[m].y));
+      }
+    }
+    r2c(2, Nz);
   }
+  {
+    float2 W[G];
+    c2r(5, W);  // omega_z
+#pragma unroll
+    for (int m = 0; m < G; ++m) {
+      const float2 ux = park[(0 * G + m) * S], uy = park[(1 * G + m) * S];
+      Nx[m] = make_float2(fmaf(uy.x, W[m].x, Nx[m].x), fmaf(uy.y, W[m].y, Nx[m].y));
+      Ny[m] = make_float2(fmaf(-ux.x, W[m].x, Ny[m].x), fmaf(-ux.y, W[m].y, Ny[m].y));
+    }
+  }
+  r2c(0, Nx);
+  r2c(1, Ny);
 }
 
 // ----------------------------------------------------- x pass + update -----
@@ -604,6 +647,9 @@ struct NSLaunch {
         err = cudaFuncSetAttribute(k_ns_ypass<N, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sx);
       if (err == cudaSuccess)
         err = cudaFuncSetAttribute(k_ns_fwdx<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, sf);
+      if (err == cudaSuccess)
+        err = cudaFuncSetAttribute(k_ns_z<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)NZCfg<N>::SMEM);
     });
     return err;
   }
@@ -632,8 +678,8 @@ struct NSLaunch {
     {
       LaunchScope ls(p, KK_NS_Z, st);
       const long long lines = (long long)N * N;
-      k_ns_z<N><<<(unsigned)((lines + Z::LPC - 1) / Z::LPC), Z::THREADS, 0, st>>>(s->w, g, p->d_tw,
-                                                                                 p->twlog);
+      k_ns_z<N><<<(unsigned)((lines + Z::LPC - 1) / Z::LPC), Z::THREADS, Z::SMEM, st>>>(s->w, g, p->d_tw,
+                                                                                       p->twlog);
     }
     {
       LaunchScope ls(p, KK_NS_FWDY, st);
