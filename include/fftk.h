@@ -108,7 +108,13 @@ fftk_status fftk_c2r(fftk_plan p, const void *in, float *out, int batch, void *c
  * Velocity: float2 uhat[3][n][n][n/2+1] (component outermost), the forward
  * transform of the real velocity.  Modes outside the 2/3-rule set
  * (3|k_x| < n and 3|k_y| < n and 3|k_z| < n) must be zero on entry and stay
- * zero; the solver never reads them. */
+ * zero; the solver never reads them.
+ * FP32 plans run the right-hand side in five fused kernels (inverse x with
+ * the curl, inverse y, z transforms with u x omega, forward y, forward x with
+ * projection and update).  FFTK_R32_SPLIT16 plans run it unfused through
+ * fftk_c2r / fftk_r2c of the plan (radix-16 stages on the tensor cores, split
+ * FP16 operands): curl, c2r of six fields, u x omega, r2c of three fields,
+ * update; they use six more real fields of device memory. */
 /* Learned subgrid-stress model (not in the paper; see tarang_mlp_*): the
  * network maps the 5 invariants of the resolved velocity gradient A
  * (tr S^2, tr R^2, tr S^3, tr R^2 S, tr R^2 S^2 with S, R the symmetric and

@@ -66,12 +66,15 @@ __device__ __forceinline__ uint2 split2(float2 a) {
   return make_uint2(*reinterpret_cast<const uint32_t*>(&hi), *reinterpret_cast<const uint32_t*>(&lo));
 }
 
-// power of two that brings max |v| to [2^10, 2^11)
+// power of two that brings max |v| to [2^10, 2^11), at most 2^100 (columns
+// whose largest value is below 2^-89, e.g. far dissipation-range modes, keep
+// a finite scale and a finite inverse; their operands then sit among FP16's
+// subnormals, an absolute error far below the rest of the column)
 __device__ __forceinline__ float pow2_scale(float m) {
   if (!(m > 0.f)) return 1.f;
   int e;
   frexpf(m, &e);
-  return ldexpf(1.f, 11 - e);
+  return ldexpf(1.f, 11 - e < 100 ? 11 - e : 100);
 }
 
 }  // namespace tc

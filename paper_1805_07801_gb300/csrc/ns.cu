@@ -302,6 +302,66 @@ struct NSUpdate {
   float scale;         // 1 / n^3
 };
 
+// One kept mode (k_x, k_y, k_z) at index idx of each field: N = P[n] (Eq. (8)),
+// + subgrid force, + forcing, then
+//   RHS:    out = N
+//   STAGE1: out = E (u0 + dt N)                      (out = u1)
+//   STAGE2: out = 1/2 E u0 + 1/2 (u1 + dt N)         (out = u0, in place)
+__device__ __forceinline__ void ns_mode_update(float2 nx, float2 ny, float2 nz, int kx, int ky, int kz,
+                                               long long idx, long long M, const NSUpdate& upd, int mode,
+                                               float gforce, const float2* u0, const float2* u1,
+                                               const float2* __restrict__ extra, float2* out) {
+  const int k2 = kx * kx + ky * ky + kz * kz;
+  if (k2 == 0) {
+    nx = ny = nz = make_float2(0.f, 0.f);
+  } else {
+    const float fkx = (float)kx, fky = (float)ky, fkz = (float)kz;
+    const float inv = 1.f / (float)k2;
+    const float2 kn = make_float2((fkx * nx.x + fky * ny.x + fkz * nz.x) * inv,
+                                  (fkx * nx.y + fky * ny.y + fkz * nz.y) * inv);
+    nx = csub(nx, cscale(kn, fkx));
+    ny = csub(ny, cscale(kn, fky));
+    nz = csub(nz, cscale(kn, fkz));
+  }
+  if (extra) {  // subgrid force, already dealiased and projected
+    nx = cadd(nx, extra[idx]);
+    ny = cadd(ny, extra[idx + M]);
+    nz = cadd(nz, extra[idx + 2 * M]);
+  }
+  const bool forced = gforce != 0.f && k2 >= upd.k2min && k2 <= upd.k2max;
+  const float2* ucur = (mode == NS_STAGE2) ? u1 : u0;
+  if (forced) {
+    nx = cadd(nx, cscale(ucur[idx], gforce));
+    ny = cadd(ny, cscale(ucur[idx + M], gforce));
+    nz = cadd(nz, cscale(ucur[idx + 2 * M], gforce));
+  }
+  if (mode == NS_RHS) {
+    out[idx] = nx;
+    out[idx + M] = ny;
+    out[idx + 2 * M] = nz;
+    return;
+  }
+  // E = hi + lo carries the factor to ~2^-48; v * E is formed as
+  // fma(v, hi, v * lo), one rounding, so repeated steps do not bias the decay.
+  const float2 E = __ldg(&upd.etab[k2]);
+  const float dt = upd.dt;
+  const float2 n3[3] = {nx, ny, nz};
+#pragma unroll
+  for (int f = 0; f < 3; ++f) {
+    const float2 a = u0[idx + f * M];
+    float2 r;
+    if (mode == NS_STAGE1) {
+      const float sx = a.x + dt * n3[f].x, sy = a.y + dt * n3[f].y;
+      r = make_float2(fmaf(sx, E.x, sx * E.y), fmaf(sy, E.x, sy * E.y));
+    } else {
+      const float2 b = u1[idx + f * M];
+      const float ex = fmaf(a.x, E.x, a.x * E.y), ey = fmaf(a.y, E.x, a.y * E.y);
+      r = make_float2(0.5f * (ex + (b.x + dt * n3[f].x)), 0.5f * (ey + (b.y + dt * n3[f].y)));
+    }
+    out[idx + f * M] = r;
+  }
+}
+
 // 5. forward x pass of the 3 nonlinear fields, then on every kept mode:
 //    N = P[n] (Eq. (8)), + forcing, and
 //    RHS:    out = N
@@ -342,59 +402,8 @@ __global__ void __launch_bounds__(NFCfg<N>::THREADS)
   for (int m = 0; m < G; ++m) {
     const int pos = j + m * S;
     if (!kept_xy(pos, N, g.kd)) continue;
-    const int kx = kwav(pos, N);
-    const int k2 = kx * kx + ky * ky + kz * kz;
-    const long long idx = pos * rs + q;
-    float2 nx = cscale(V[0][m], upd.scale), ny = cscale(V[1][m], upd.scale),
-           nz = cscale(V[2][m], upd.scale);
-    if (k2 == 0) {
-      nx = ny = nz = make_float2(0.f, 0.f);
-    } else {
-      const float fkx = (float)kx, fky = (float)ky, fkz = (float)kz;
-      const float inv = 1.f / (float)k2;
-      const float2 kn = make_float2((fkx * nx.x + fky * ny.x + fkz * nz.x) * inv,
-                                    (fkx * nx.y + fky * ny.y + fkz * nz.y) * inv);
-      nx = csub(nx, cscale(kn, fkx));
-      ny = csub(ny, cscale(kn, fky));
-      nz = csub(nz, cscale(kn, fkz));
-    }
-    if (extra) {  // subgrid force, already dealiased and projected
-      nx = cadd(nx, extra[idx]);
-      ny = cadd(ny, extra[idx + g.M]);
-      nz = cadd(nz, extra[idx + 2 * g.M]);
-    }
-    const bool forced = gforce != 0.f && k2 >= upd.k2min && k2 <= upd.k2max;
-    const float2* ucur = (mode == NS_STAGE2) ? u1 : u0;
-    if (forced) {
-      nx = cadd(nx, cscale(ucur[idx], gforce));
-      ny = cadd(ny, cscale(ucur[idx + g.M], gforce));
-      nz = cadd(nz, cscale(ucur[idx + 2 * g.M], gforce));
-    }
-    if (mode == NS_RHS) {
-      out[idx] = nx;
-      out[idx + g.M] = ny;
-      out[idx + 2 * g.M] = nz;
-    } else {
-      // E = hi + lo carries the factor to ~2^-48; v * E is formed as
-      // fma(v, hi, v * lo), one rounding, so repeated steps do not bias the decay.
-      const float2 E = __ldg(&upd.etab[k2]);
-      const float dt = upd.dt;
-      const float2 n3[3] = {nx, ny, nz};
-#pragma unroll
-      for (int f = 0; f < 3; ++f) {
-        const float2 a = u0[idx + f * g.M];
-        float2 r;
-        if (mode == NS_STAGE1) {
-          const float sx = a.x + dt * n3[f].x, sy = a.y + dt * n3[f].y;
-          r = make_float2(fmaf(sx, E.x, sx * E.y), fmaf(sy, E.x, sy * E.y));
-        } else {
-          const float2 b = u1[idx + f * g.M];
-          const float ex = fmaf(a.x, E.x, a.x * E.y), ey = fmaf(a.y, E.x, a.y * E.y);
-          r = make_float2(0.5f * (ex + (b.x + dt * n3[f].x)), 0.5f * (ey + (b.y + dt * n3[f].y)));
-        }
-        out[idx + f * g.M] = r;
-      }
-    }
+    ns_mode_update(cscale(V[0][m], upd.scale), cscale(V[1][m], upd.scale), cscale(V[2][m], upd.scale),
+                   kwav(pos, N), ky, kz, pos * rs + q, g.M, upd, mode, gforce, u0, u1, extra, out);
   }
 }
 
@@ -542,6 +551,7 @@ struct NSWork {
   double* dout = nullptr;  // diag result (device)
   double* hout = nullptr;  // diag result (pinned host)
   fftk_sgs_work* sgs = nullptr;  // learned-closure scratch
+  float* r6 = nullptr;     // 6 real fields (unfused split-precision right-hand side)
   int kmax = 0;
   int diag_smem = 0;
 };
@@ -694,11 +704,96 @@ struct NSLaunch {
   }
 };
 
+// ---------------------------------------------- split-precision NS step ----
+// Plans of dtype FFTK_R32_SPLIT16 evaluate the right-hand side unfused through
+// the library's own transforms, whose radix-16 stages then run on the tensor
+// cores: u and omega = i k x u on the spectrum, c2r of the six fields, n = u x
+// omega in real space, r2c of n, and the per-mode update of the fused path.
+
+// w6 = (u, i k x u); the derivative of the Nyquist wavenumber is 0
+__global__ void k_curl_full(const float2* __restrict__ u, float2* __restrict__ w6, NSGeom g) {
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < g.M;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(idx % g.h1);
+    const long long ab = idx / g.h1;
+    const int b = (int)(ab % g.n), a = (int)(ab / g.n);
+    const int ka = kwav(a, g.n), kb = kwav(b, g.n);
+    const float kx = (2 * abs(ka) == g.n) ? 0.f : (float)ka, ky = (2 * abs(kb) == g.n) ? 0.f : (float)kb;
+    const float kz = (2 * c == g.n) ? 0.f : (float)c;
+    const float2 ux = u[idx], uy = u[idx + g.M], uz = u[idx + 2 * g.M];
+    w6[idx] = ux;
+    w6[idx + g.M] = uy;
+    w6[idx + 2 * g.M] = uz;
+    w6[idx + 3 * g.M] = csub(mul_i(uz, ky), mul_i(uy, kz));
+    w6[idx + 4 * g.M] = csub(mul_i(ux, kz), mul_i(uz, kx));
+    w6[idx + 5 * g.M] = csub(mul_i(uy, kx), mul_i(ux, ky));
+  }
+}
+
+// n = u x omega in place of u (fields 0..2 of the six real fields)
+__global__ void k_cross_real(float* __restrict__ r6, long long R) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < R;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float ux = r6[i], uy = r6[R + i], uz = r6[2 * R + i];
+    const float wx = r6[3 * R + i], wy = r6[4 * R + i], wz = r6[5 * R + i];
+    r6[i] = uy * wz - uz * wy;
+    r6[R + i] = uz * wx - ux * wz;
+    r6[2 * R + i] = ux * wy - uy * wx;
+  }
+}
+
+// the update of every kept mode from n_hat (already scaled by the transform)
+__global__ void k_update_full(const float2* __restrict__ nh, const float2* u0, const float2* u1, float2* out,
+                              NSGeom g, NSUpdate upd, int mode, const float2* __restrict__ extra) {
+  float gforce = 0.f;
+  if (upd.feps > 0.0) {
+    const double ef = *upd.ef;
+    gforce = ef > 0.0 ? (float)(upd.feps / (2.0 * ef)) : 0.f;
+  }
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < g.M;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(idx % g.h1);
+    const long long ab = idx / g.h1;
+    const int b = (int)(ab % g.n), a = (int)(ab / g.n);
+    if (!(kept_xy(a, g.n, g.kd) && kept_xy(b, g.n, g.kd) && c < g.kc)) continue;
+    ns_mode_update(nh[idx], nh[idx + g.M], nh[idx + 2 * g.M], kwav(a, g.n), kwav(b, g.n), c, idx, g.M, upd, mode,
+                   gforce, u0, u1, extra, out);
+  }
+}
+
+static cudaError_t ns_rhs_split(fftk_plan p, const float2* u, const float2* u0, const float2* u1, float2* out,
+                                const NSUpdate& upd, int mode, const float2* extra, cudaStream_t st) {
+  NSWork* s = p->ns;
+  const NSGeom g = s->g;
+  const long long R = (long long)g.n * g.n * g.n;
+  if (!s->r6) {
+    cudaError_t e = cudaMalloc(&s->r6, sizeof(float) * 6 * (size_t)R);
+    if (e != cudaSuccess) return e;
+  }
+  const unsigned grid = 152 * 8;
+  {
+    LaunchScope ls(p, KK_AUX, st);
+    k_curl_full<<<grid, 256, 0, st>>>(u, s->w, g);
+  }
+  if (fftk_c2r(p, s->w, s->r6, 6, st) != FFTK_OK) return cudaErrorLaunchFailure;
+  {
+    LaunchScope ls(p, KK_AUX, st);
+    k_cross_real<<<grid, 256, 0, st>>>(s->r6, R);
+  }
+  if (fftk_r2c(p, s->r6, s->w, 3, st) != FFTK_OK) return cudaErrorLaunchFailure;
+  {
+    LaunchScope ls(p, KK_AUX, st);
+    k_update_full<<<grid, 256, 0, st>>>(s->w, u0, u1, out, g, upd, mode, extra);
+  }
+  return cudaGetLastError();
+}
+
 #define NS_SIZES(X) X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024)
 
 static cudaError_t ns_rhs_dispatch(fftk_plan p, const float2* u, const float2* u0, const float2* u1,
                                    float2* out, const NSUpdate& upd, int mode, const float2* extra,
                                    cudaStream_t st) {
+  if (p->dtype == FFTK_R32_SPLIT16) return ns_rhs_split(p, u, u0, u1, out, upd, mode, extra, st);
   switch (p->nx) {
 #define CASE(n) \
   case n:       \
@@ -765,6 +860,7 @@ void ns_free(fftk_plan p) {
   cudaFree(s->part);
   cudaFree(s->dout);
   if (s->hout) cudaFreeHost(s->hout);
+  cudaFree(s->r6);
   sgs_free(s->sgs);
   delete s;
   p->ns = nullptr;

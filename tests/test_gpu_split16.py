@@ -115,3 +115,29 @@ def test_split16_full_size_1024_pair(fk, oracle_mod):
     for (a, b, c) in [(0, 0, 0), (3, 1000, 7), (512, 512, 512), (77, 5, 300)]:
         want = oracle_mod.rfft3_coeff(f, a, b, c)
         assert abs(Fh[a, b, c] - want) < 5e-5 * rms
+
+
+def test_split16_tiny_and_mixed_magnitude_columns(fk, oracle_mod):
+    """Columns whose values lie near FP32's smallest normals (and columns that
+    mix 1 and 1e-38) keep a finite power-of-two scale: the transforms stay
+    finite and within the split mode's error of the FP64 oracle."""
+    shape = (256, 256, 8)
+    f = synth.uniform_pm1(7, 0, shape).astype(np.float64)
+    f[:, :, :4] *= 1e-38
+    f[:128] *= 1e-30
+    hs = (shape[0], shape[1], shape[2] // 2 + 1)
+    plan = _plan(fk, shape)
+    try:
+        x = to_dev_real(f.astype(np.float32))
+        F = empty_c64(hs)
+        fk.fftk_r2c(plan, x.data_ptr(), F.data_ptr(), 1, stream())
+        y = empty_real(shape)
+        fk.fftk_c2r(plan, F.data_ptr(), y.data_ptr(), 1, stream())
+        sync()
+        Fg, yg = from_dev_c64(F), y.cpu().numpy()
+    finally:
+        fk.fftk_plan_destroy(plan)
+    assert np.all(np.isfinite(Fg)) and np.all(np.isfinite(yg))
+    Fo = oracle_mod.rfft3(f.astype(np.float32).astype(np.float64))
+    assert rel_l2(Fg, Fo) < 1e-5
+    assert rel_l2(yg, f.astype(np.float32)) < 1e-5
