@@ -584,9 +584,13 @@ def run_case(case: str):
 
 
 def run_forced(n: int, steps: int):
-    """Forced turbulence in FP32 (k0 = 2, constant power 0.1 on 1 <= |k| <= 2,
-    nu = 4e-4, dt = 2.5e-4): steps/s of the fused step with the forcing
-    reduction, and E, eps and the spectrum every 50 steps.  Prints one JSON line."""
+    """Forced turbulence (k0 = 2, constant power 0.1 on 1 <= |k| <= 2,
+    nu = 4e-4, dt = 2.5e-4) from the same seeded field, once with an FP32
+    plan (fused step) and once with a split-FP16 plan (unfused step, radix-16
+    stages on the tensor cores); energy and dissipation reduced in FP64 every
+    50 steps.  Prints one JSON line: steps/s of each run, their histories and
+    the per-shell relative difference of the final spectra."""
+    import numpy as np
     import torch
 
     import paper_1805_07801_gb300 as fk
@@ -595,36 +599,49 @@ def run_forced(n: int, steps: int):
     fkbuild.build()
     dev = torch.device("cuda:0")
     st = torch.cuda.current_stream(dev).cuda_stream
-    plan = fk.fftk_plan_create(n, n, n)
-    nr = torch.empty((3, n, n, n), dtype=torch.float32, device=dev)
-    for f in range(3):
-        fk.fftk_fill_normal(nr[f].data_ptr(), n**3, SEED, f, st)
-    u = torch.empty((3, n, n, n // 2 + 1, 2), dtype=torch.float32, device=dev)
-    fk.tarang_ic_random(plan, nr.data_ptr(), u.data_ptr(), 2.0, E0, st)
-    del nr
-    prm = fk.make_params(4e-4, 2.5e-4, 0.1, (1, 4))
-    fk.tarang_ns_step(plan, u.data_ptr(), prm, 3, False, st)
-    hist = []
-    secs = 0.0
-    done = 0
-    chunk = 50
-    while done < steps:
-        k = min(chunk, steps - done)
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record()
-        fk.tarang_ns_step(plan, u.data_ptr(), prm, k, False, st)
-        b.record()
-        b.synchronize()
-        secs += a.elapsed_time(b) * 1e-3
-        done += k
-        E, eps, EK = fk.tarang_diag(plan, u.data_ptr(), 4e-4, st)
-        hist.append({"step": done + 3, "E": E, "eps": eps})
-    fk.fftk_plan_destroy(plan)
-    print(json.dumps({"workload": f"{n}^3 forced turbulence, FP32, k0=2, eps=0.1 on 1<=|k|<=2, nu=4e-4, "
-                                  f"dt=2.5e-4, RK2-IF, 2/3 dealiasing, seed {SEED}",
-                      "steps": steps, "steps_per_s": round(steps / secs, 3), "ms_per_step": round(1e3 * secs / steps, 3),
-                      "history": hist, "EK_final": [float(v) for v in EK[:65]]}), flush=True)
+    runs = {}
+    for key, dtype in (("fp32", fk.FFTK_R32), ("split16", fk.FFTK_R32_SPLIT16)):
+        plan = fk.fftk_plan_create(n, n, n, dtype)
+        nr = torch.empty((3, n, n, n), dtype=torch.float32, device=dev)
+        for f in range(3):
+            fk.fftk_fill_normal(nr[f].data_ptr(), n**3, SEED, f, st)
+        u = torch.empty((3, n, n, n // 2 + 1, 2), dtype=torch.float32, device=dev)
+        fk.tarang_ic_random(plan, nr.data_ptr(), u.data_ptr(), 2.0, E0, st)
+        del nr
+        prm = fk.make_params(4e-4, 2.5e-4, 0.1, (1, 4))
+        hist = []
+        secs = 0.0
+        done = 0
+        while done < steps:
+            k = min(50, steps - done)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            fk.tarang_ns_step(plan, u.data_ptr(), prm, k, False, st)
+            b.record()
+            b.synchronize()
+            secs += a.elapsed_time(b) * 1e-3
+            done += k
+            E, eps, EK = fk.tarang_diag(plan, u.data_ptr(), 4e-4, st)
+            hist.append({"step": done, "E": E, "eps": eps})
+        fk.fftk_sync(plan, st)
+        fk.fftk_plan_destroy(plan)
+        del u
+        torch.cuda.empty_cache()
+        runs[key] = {"steps_per_s": round(steps / secs, 3), "ms_per_step": round(1e3 * secs / steps, 3),
+                     "history": hist, "EK": np.asarray(EK)}
+    ek32, ek16 = runs["fp32"].pop("EK"), runs["split16"].pop("EK")
+    res = ek32 >= 1e-8 * ek32.max()
+    rel = np.abs(ek16[res] - ek32[res]) / ek32[res]
+    f32, f16 = runs["fp32"]["history"][-1], runs["split16"]["history"][-1]
+    print(json.dumps({"workload": f"{n}^3 forced turbulence, k0=2, eps=0.1 on 1<=|k|<=2, nu=4e-4, dt=2.5e-4, "
+                                  f"RK2-IF, 2/3 dealiasing, seed {SEED}, {steps} steps",
+                      "fp32": runs["fp32"], "split16": runs["split16"],
+                      "split16_vs_fp32": {"dE_over_E": abs(f16["E"] - f32["E"]) / f32["E"],
+                                          "deps_over_eps": abs(f16["eps"] - f32["eps"]) / f32["eps"],
+                                          "max_shell_rel_diff": float(rel.max()),
+                                          "shells_compared": int(res.sum()),
+                                          "cutoff_shell": int(np.nonzero(res)[0].max())}}), flush=True)
 
 
 def run_fft_sweep(args):
