@@ -258,6 +258,19 @@ fftk_status tarang_mlp_destroy(tarang_mlp m);
  * FP32.  A bounded wait that expires inside it is reported by tarang_mlp_sync. */
 fftk_status tarang_mlp_forward(tarang_mlp m, const float *params, const float *x, float *y, int B,
                                void *cuda_stream);
+/* Training of the closure network: `steps` Adam steps numbered first_step,
+ * first_step + 1, ... (lr, beta1 0.9, beta2 0.999, eps 1e-8) on the device
+ * data set x [nsamples][5], t [nsamples][6].  The batch of step s is the
+ * contiguous window of `batch` samples at offset
+ *   splitmix64(seed * 2^32 + s) mod (nsamples - batch + 1)
+ * (SplitMix64 output number c of the stream from state 0; shuffle the set once
+ * beforehand).  With loss_log (device, steps / log_every doubles), the loss
+ * of every log_every-th step is recorded.  Equivalent to the same sequence of
+ * tarang_mlp_train_step calls; asynchronous. */
+fftk_status tarang_sgs_train(tarang_mlp m, float *params, float *adam_m, float *adam_v, int first_step,
+                             int steps, const float *x, const float *t, long long nsamples, int batch,
+                             float lr, unsigned long long seed, double *loss_log, int log_every,
+                             void *cuda_stream);
 /* Wait for the stream; FFTK_ERR_TIMEOUT if a tensor-core wait of this
  * context's inference expired since the last call (the flag is cleared). */
 fftk_status tarang_mlp_sync(tarang_mlp m, void *cuda_stream);

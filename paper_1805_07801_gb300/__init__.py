@@ -96,6 +96,7 @@ def lib() -> ctypes.CDLL:
             "tarang_mlp_destroy": ([vp], i),
             "tarang_mlp_forward": ([vp, vp, vp, vp, i, vp], i),
             "tarang_mlp_sync": ([vp, vp], i),
+            "tarang_sgs_train": ([vp, vp, vp, vp, i, i, vp, vp, ll, i, c.c_float, c.c_ulonglong, vp, i, vp], i),
             "tarang_mlp_loss_grad": ([vp, vp, vp, vp, i, vp, vp, vp], i),
             "tarang_mlp_adam": ([vp, vp, vp, vp, i, c.c_float, c.c_float, c.c_float, c.c_float, vp], i),
             "tarang_mlp_train_step": ([vp, vp, vp, vp, i, vp, vp, i, c.c_float, vp, vp], i),
@@ -250,6 +251,14 @@ def tarang_mlp_destroy(m: int) -> None:
 def tarang_mlp_forward(m: int, params_ptr, x_ptr, y_ptr, B: int, stream=0) -> None:
     _check(lib().tarang_mlp_forward(_vp(m), _vp(params_ptr), _vp(x_ptr), _vp(y_ptr), int(B), _vp(stream)),
            "tarang_mlp_forward")
+
+
+def tarang_sgs_train(m: int, params_ptr, m_ptr, v_ptr, first_step: int, steps: int, x_ptr, t_ptr, nsamples: int,
+                     batch: int, lr: float, seed: int, loss_log_ptr=0, log_every: int = 1, stream=0) -> None:
+    _check(lib().tarang_sgs_train(_vp(m), _vp(params_ptr), _vp(m_ptr), _vp(v_ptr), int(first_step), int(steps),
+                                  _vp(x_ptr), _vp(t_ptr), int(nsamples), int(batch), float(lr),
+                                  ctypes.c_ulonglong(int(seed)), _vp(loss_log_ptr), int(log_every), _vp(stream)),
+           "tarang_sgs_train")
 
 
 def tarang_mlp_sync(m: int, stream=0) -> None:

@@ -911,6 +911,34 @@ extern "C" fftk_status tarang_mlp_train_step(tarang_mlp m, float* params, float*
   return tarang_mlp_adam(params, mom, var, m->grad, step, lr, 0.9f, 0.999f, 1e-8f, cuda_stream);
 }
 
+// SplitMix64 (Steele, Lea & Flood 2014): output number c of the stream that
+// starts from state 0
+static uint64_t splitmix64_at(uint64_t c) {
+  uint64_t z = (c + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+extern "C" fftk_status tarang_sgs_train(tarang_mlp m, float* params, float* mom, float* var, int first_step,
+                                        int steps, const float* x, const float* t, long long nsamples, int batch,
+                                        float lr, unsigned long long seed, double* loss_log, int log_every,
+                                        void* cuda_stream) {
+  if (!m || !params || !mom || !var || !x || !t || first_step < 1 || steps < 0 || batch < 1 ||
+      batch > m->max_batch || nsamples < batch || (loss_log && log_every < 1) || !(lr > 0.f))
+    return FFTK_ERR_INVALID_ARG;
+  const unsigned long long windows = (unsigned long long)(nsamples - batch + 1);
+  for (int k = 0; k < steps; ++k) {
+    const int step = first_step + k;
+    const long long off = (long long)(splitmix64_at((seed << 32) + (unsigned long long)step) % windows);
+    double* lp = (loss_log && (k + 1) % log_every == 0) ? loss_log + ((k + 1) / log_every - 1) : nullptr;
+    const fftk_status s =
+        tarang_mlp_train_step(m, params, mom, var, step, x + off * 5, t + off * 6, batch, lr, lp, cuda_stream);
+    if (s != FFTK_OK) return s;
+  }
+  return FFTK_OK;
+}
+
 // -------------------------------------------- SGS term for the solver ------
 namespace fftk {
 

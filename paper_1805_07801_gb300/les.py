@@ -17,7 +17,7 @@ keeps small host-side statistics):
    in that frame Q^T tau Q come from tarang_closure_features.
 3. Training.  The 5 -> 64 -> 64 -> 64 -> 6 tanh network maps normalised
    invariants to the normalised frame stress (MSE, Adam), through
-   tarang_mlp_train_step; the last snapshot is held out.
+   tarang_sgs_train; the last snapshot is held out.
 4. Coarse run.  The coarse solver steps the first filtered snapshot with the
    model's subgrid force P[-i k_j tau_ij] fused into its right-hand side; the
    same run without the model is the baseline.  Their time-averaged spectra
@@ -37,8 +37,8 @@ import torch
 
 from . import (FFTKError, fftk_fill_normal, fftk_plan_create, fftk_plan_destroy, fftk_r2c, make_params,
                make_sgs_model, tarang_box_filter, tarang_closure_features, tarang_dealias_project, tarang_diag,
-               tarang_ic_random, tarang_mlp_create, tarang_mlp_destroy, tarang_mlp_forward, tarang_mlp_train_step,
-               tarang_ns_step)
+               tarang_ic_random, tarang_mlp_create, tarang_mlp_destroy, tarang_mlp_forward, tarang_ns_step,
+               tarang_sgs_train)
 
 NPARAMS = 9094
 DIMS = (5, 64, 64, 64, 6)
@@ -200,43 +200,35 @@ def init_params(seed: int) -> np.ndarray:
 
 
 def train(x: np.ndarray, t: np.ndarray, cfg: ClosureConfig, log=None):
-    """Train on x [S][5], t [S][6] (normalised).  Batches are windows at random
-    offsets of one shuffled copy of the set (the first `batch` samples are
-    appended so every window is contiguous).  Returns (params on the device,
-    loss history, seconds, samples/s)."""
+    """Train on x [S][5], t [S][6] (normalised) with tarang_sgs_train: one
+    shuffle of the set, then batches that are windows at SplitMix64 offsets.
+    Returns (params on the device, loss history, seconds, samples/s)."""
     S = x.shape[0]
     B = min(cfg.batch, S)
     rng = np.random.default_rng(cfg.init_seed + 1)
     perm = rng.permutation(S)
-    xs = np.concatenate([x[perm], x[perm[:B]]]).astype(np.float32)
-    ts = np.concatenate([t[perm], t[perm[:B]]]).astype(np.float32)
-    xd = torch.from_numpy(np.ascontiguousarray(xs)).to(DEV)
-    td = torch.from_numpy(np.ascontiguousarray(ts)).to(DEV)
+    xd = torch.from_numpy(np.ascontiguousarray(x[perm], dtype=np.float32)).to(DEV)
+    td = torch.from_numpy(np.ascontiguousarray(t[perm], dtype=np.float32)).to(DEV)
     p = torch.from_numpy(init_params(cfg.init_seed)).to(DEV)
     mom = torch.zeros(NPARAMS, dtype=torch.float32, device=DEV)
     var = torch.zeros_like(mom)
-    loss = torch.zeros(1, dtype=torch.float64, device=DEV)
-    starts = rng.integers(0, S, size=cfg.train_steps)
+    every = max(1, cfg.train_steps // 20)
+    nlog = cfg.train_steps // every
+    losses = torch.zeros(max(nlog, 1), dtype=torch.float64, device=DEV)
     ctx = tarang_mlp_create(B)
-    hist = []
     try:
-        every = max(1, cfg.train_steps // 20)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for step in range(1, cfg.train_steps + 1):
-            off = int(starts[step - 1])
-            want = step % every == 0 or step == 1
-            tarang_mlp_train_step(ctx, p.data_ptr(), mom.data_ptr(), var.data_ptr(), step,
-                                  xd.data_ptr() + off * 5 * 4, td.data_ptr() + off * 6 * 4, B, cfg.lr,
-                                  loss.data_ptr() if want else 0, _stream())
-            if want:
-                hist.append((step, float(loss.item())))
-                if log:
-                    log(f"  train step {step}: loss {hist[-1][1]:.5f}")
+        tarang_sgs_train(ctx, p.data_ptr(), mom.data_ptr(), var.data_ptr(), 1, cfg.train_steps, xd.data_ptr(),
+                         td.data_ptr(), S, B, cfg.lr, cfg.init_seed + 2, losses.data_ptr(), every, _stream())
         torch.cuda.synchronize()
         secs = time.perf_counter() - t0
     finally:
         tarang_mlp_destroy(ctx)
+    hist = [((i + 1) * every, float(v)) for i, v in enumerate(losses.cpu().numpy()[:nlog])]
+    if log:
+        for step, v in hist:
+            log(f"  train step {step}: loss {v:.5f}")
     return p, hist, secs, cfg.train_steps * B / secs
 
 

@@ -262,3 +262,35 @@ def test_dealias_project_matches_oracle(fk, oracle_mod, n):
     dropped = oracle_mod.dealias(np.ones(shape, dtype=np.complex128), 3) == 0
     assert np.all(got[dropped] == 0)
     assert np.max(np.abs(got - want)) < 4e-6 * np.max(np.abs(u))
+
+
+def test_sgs_train_equals_single_steps(fk):
+    """tarang_sgs_train = the same sequence of tarang_mlp_train_step calls on
+    windows at SplitMix64 offsets (bitwise: fixed-order reductions)."""
+    import torch
+
+    S, B, steps, seed, lr = 3000, 512, 6, 77, 2e-3
+    rng = np.random.default_rng(21)
+    x = _f32(rng.standard_normal((S, 5)))
+    t = _f32(rng.standard_normal((S, 6)) * 0.5)
+    p0 = _params(22, 0.2)
+    ctx = fk.tarang_mlp_create(B)
+    try:
+        pa, pb = _f32(p0), _f32(p0)
+        ma, va = torch.zeros_like(pa), torch.zeros_like(pa)
+        mb, vb = torch.zeros_like(pb), torch.zeros_like(pb)
+        log = torch.zeros(3, dtype=torch.float64, device="cuda:0")
+        fk.tarang_sgs_train(ctx, pa.data_ptr(), ma.data_ptr(), va.data_ptr(), 1, steps, x.data_ptr(), t.data_ptr(), S,
+                            B, lr, seed, log.data_ptr(), 2, stream())
+        offs = synth.splitmix64(np.uint64(seed) * np.uint64(2**32) + np.arange(1, steps + 1, dtype=np.uint64))
+        offs = (offs % np.uint64(S - B + 1)).astype(np.int64)
+        lb = torch.zeros(1, dtype=torch.float64, device="cuda:0")
+        for k, off in enumerate(offs):
+            fk.tarang_mlp_train_step(ctx, pb.data_ptr(), mb.data_ptr(), vb.data_ptr(), k + 1,
+                                     x.data_ptr() + int(off) * 5 * 4, t.data_ptr() + int(off) * 6 * 4, B, lr,
+                                     lb.data_ptr() if k == steps - 1 else 0, stream())
+        sync()
+        assert torch.equal(pa, pb) and torch.equal(ma, mb) and torch.equal(va, vb)
+        assert float(log[2].item()) == float(lb.item())
+    finally:
+        fk.tarang_mlp_destroy(ctx)
