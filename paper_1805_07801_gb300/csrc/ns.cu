@@ -105,6 +105,7 @@ struct NFCfg {
   static constexpr int T = S >= 32 ? (S == 32 ? 16 : (S == 64 ? 8 : 4)) : 16;
   static constexpr int THREADS = T * S;
   static constexpr size_t SMEM = sizeof(float2) * (size_t)N * T;
+  static constexpr size_t SMEM_FWD = SMEM + sizeof(float2) * 2 * G * THREADS;  // + two parked fields (forward x)
 };
 
 // 1. inverse x pass with the curl.  Columns: kept (k_y, k_z); rows: k_x.
@@ -368,7 +369,7 @@ __device__ __forceinline__ void ns_mode_update(float2 nx, float2 ny, float2 nz, 
 //    STAGE1: out = E (u0 + dt N)                      (out = u1)
 //    STAGE2: out = 1/2 E u0 + 1/2 (u1 + dt N)         (out = u0, in place)
 template <int N>
-__global__ void __launch_bounds__(NFCfg<N>::THREADS)
+__global__ void __launch_bounds__(NFCfg<N>::THREADS, 2)
     k_ns_fwdx(const float2* __restrict__ nh, const float2* u0, const float2* u1, float2* out,
               NSGeom g, int ktiles, NSUpdate upd, int mode, const float2* __restrict__ extra,
               const float2* __restrict__ tw, int twlog) {
@@ -383,13 +384,20 @@ __global__ void __launch_bounds__(NFCfg<N>::THREADS)
   const long long q = (long long)ay * g.h1 + kz;
   const long long rs = (long long)N * g.h1;
   const ColX<T> xc{smn, c};
-  float2 V[3][G];
-#pragma unroll
+  // fields 0 and 1 are parked in shared memory after their transforms (this
+  // thread's slots only), so one field at a time is held in registers
+  float2* park = smn + (size_t)N * T + threadIdx.x;
+  float2 V[G];
+#pragma unroll 1
   for (int f = 0; f < 3; ++f) {
 #pragma unroll
     for (int m = 0; m < G; ++m)
-      V[f][m] = valid ? nh[f * g.M + (j + m * S) * rs + q] : make_float2(0.f, 0.f);
-    fft_line<N, G, -1>(V[f], j, xc, tw, twlog);
+      V[m] = valid ? nh[f * g.M + (j + m * S) * rs + q] : make_float2(0.f, 0.f);
+    fft_line<N, G, -1>(V, j, xc, tw, twlog);
+    if (f < 2) {
+#pragma unroll
+      for (int m = 0; m < G; ++m) park[(f * G + m) * C::THREADS] = V[m];
+    }
   }
   if (!valid) return;
   const int ky = kwav(ay, N);
@@ -402,8 +410,9 @@ __global__ void __launch_bounds__(NFCfg<N>::THREADS)
   for (int m = 0; m < G; ++m) {
     const int pos = j + m * S;
     if (!kept_xy(pos, N, g.kd)) continue;
-    ns_mode_update(cscale(V[0][m], upd.scale), cscale(V[1][m], upd.scale), cscale(V[2][m], upd.scale),
-                   kwav(pos, N), ky, kz, pos * rs + q, g.M, upd, mode, gforce, u0, u1, extra, out);
+    ns_mode_update(cscale(park[m * C::THREADS], upd.scale), cscale(park[(G + m) * C::THREADS], upd.scale),
+                   cscale(V[m], upd.scale), kwav(pos, N), ky, kz, pos * rs + q, g.M, upd, mode, gforce, u0, u1,
+                   extra, out);
   }
 }
 
@@ -649,14 +658,16 @@ struct NSLaunch {
     static std::once_flag once;
     static cudaError_t err = cudaSuccess;
     std::call_once(once, [] {
-      const int sx = (int)NXCfg<N>::SMEM, sf = (int)NFCfg<N>::SMEM;
-      err = cudaFuncSetAttribute(k_ns_invx<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, sf);
+      const int sx = (int)NXCfg<N>::SMEM;
+      err = cudaFuncSetAttribute(k_ns_invx<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)NFCfg<N>::SMEM);
       if (err == cudaSuccess)
         err = cudaFuncSetAttribute(k_ns_ypass<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sx);
       if (err == cudaSuccess)
         err = cudaFuncSetAttribute(k_ns_ypass<N, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sx);
       if (err == cudaSuccess)
-        err = cudaFuncSetAttribute(k_ns_fwdx<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, sf);
+        err = cudaFuncSetAttribute(k_ns_fwdx<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)NFCfg<N>::SMEM_FWD);
       if (err == cudaSuccess)
         err = cudaFuncSetAttribute(k_ns_z<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)NZCfg<N>::SMEM);
@@ -697,7 +708,7 @@ struct NSLaunch {
     }
     {
       LaunchScope ls(p, KK_NS_FWDX, st);
-      k_ns_fwdx<N><<<g.nk * kf, F::THREADS, F::SMEM, st>>>(s->w, u0, u1, out, g, kf, upd, mode,
+      k_ns_fwdx<N><<<g.nk * kf, F::THREADS, F::SMEM_FWD, st>>>(s->w, u0, u1, out, g, kf, upd, mode,
                                                           extra, p->d_tw, p->twlog);
     }
     return cudaGetLastError();
