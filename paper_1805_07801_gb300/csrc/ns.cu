@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(NXCfg<N>::THREADS, NXCfg<N>::MINB)
 #pragma unroll
   for (int m = 0; m < G; ++m) {
     const int pos = j + m * S;
-    const bool rd = valid && (SIGN < 0 || kept_xy(pos, N, g.kd));
+    const bool rd = valid && (SIGN < 0 || kept_xy(pos, N, (N - 1) / 3));
     v[m] = rd ? base[(long long)pos * g.h1] : make_float2(0.f, 0.f);
   }
   fft_line<N, G, SIGN>(v, j, ColX<T>{smn, c}, tw, twlog);
@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(NXCfg<N>::THREADS, NXCfg<N>::MINB)
 #pragma unroll
     for (int m = 0; m < G; ++m) {
       const int pos = j + m * S;
-      if (SIGN > 0 || kept_xy(pos, N, g.kd)) base[(long long)pos * g.h1] = v[m];
+      if (SIGN > 0 || kept_xy(pos, N, (N - 1) / 3)) base[(long long)pos * g.h1] = v[m];
     }
   }
 }
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(NFCfg<N>::THREADS)
     for (int m = 0; m < G; ++m) {
       const int pos = j + m * S;
       float2 a = make_float2(0.f, 0.f);
-      if (valid && kept_xy(pos, N, g.kd)) a = u[f * g.M + pos * rs + q];
+      if (valid && kept_xy(pos, N, (N - 1) / 3)) a = u[f * g.M + pos * rs + q];
       v[m] = ikx ? mul_i(a, (float)kwav(pos, N)) : a;
     }
   };
@@ -409,7 +409,7 @@ __global__ void __launch_bounds__(NFCfg<N>::THREADS, 2)
 #pragma unroll
   for (int m = 0; m < G; ++m) {
     const int pos = j + m * S;
-    if (!kept_xy(pos, N, g.kd)) continue;
+    if (!kept_xy(pos, N, (N - 1) / 3)) continue;
     ns_mode_update(cscale(park[m * C::THREADS], upd.scale), cscale(park[(G + m) * C::THREADS], upd.scale),
                    cscale(V[m], upd.scale), kwav(pos, N), ky, kz, pos * rs + q, g.M, upd, mode, gforce, u0, u1,
                    extra, out);
