@@ -194,6 +194,7 @@ __global__ void __launch_bounds__(NZCfg<N>::THREADS, 3)
   using C = NZCfg<N>;
   constexpr int H = C::H, G = C::G, S = C::S;
   constexpr int LOGN = Log2<N>::value;
+  constexpr int KC = (N - 1) / 3 + 1;  // kept k_z count (2/3 rule)
   extern __shared__ float2 smz[];
   const int li = threadIdx.x / S, j = threadIdx.x % S;
   const long long line = (long long)blockIdx.x * C::LPC + li;
@@ -208,8 +209,8 @@ __global__ void __launch_bounds__(NZCfg<N>::THREADS, 3)
     for (int m = 0; m < G; ++m) {
       const int k = j + m * S;
       float2 A = make_float2(0.f, 0.f), B = make_float2(0.f, 0.f);
-      if (valid && k < g.kc) A = src[k];
-      if (valid && H - k < g.kc) B = src[H - k];
+      if (valid && k < KC) A = src[k];
+      if (valid && H - k < KC) B = src[H - k];
       if (k == 0) {
         A.y = 0.f;
         B.y = 0.f;
@@ -248,7 +249,7 @@ __global__ void __launch_bounds__(NZCfg<N>::THREADS, 3)
       const float2 D = csub(A, Bc);
       const float2 O = make_float2(0.5f * D.y, -0.5f * D.x);
       const float2 W = __ldg(&tw[k << (twlog - LOGN)]);
-      if (valid && k < g.kc) dst[k] = cadd(E, cmul(W, O));
+      if (valid && k < KC) dst[k] = cadd(E, cmul(W, O));
     }
     xc.sync();
   };
