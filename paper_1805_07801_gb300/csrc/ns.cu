@@ -69,6 +69,8 @@ struct NXCfg {
 template <int N, int SIGN>
 __global__ void __launch_bounds__(NXCfg<N>::THREADS, NXCfg<N>::MINB)
     k_ns_ypass(float2* w, NSGeom g, int ktiles, const float2* __restrict__ tw, int twlog) {
+  constexpr long long H1 = N / 2 + 1, MM = (long long)N * N * H1;  // geometry of the n^3 grid
+  constexpr int KD = (N - 1) / 3;                                  // largest kept |k| (2/3 rule)
   using C = NXCfg<N>;
   constexpr int G = C::G, S = C::S, T = C::T;
   extern __shared__ float2 smn[];
@@ -78,21 +80,21 @@ __global__ void __launch_bounds__(NXCfg<N>::THREADS, NXCfg<N>::MINB)
   const int x = rest % N;
   const int f = rest / N;
   const int kz = kt * T + c;
-  const bool valid = kz < g.kc;
-  float2* base = w + f * g.M + (long long)x * N * g.h1 + kz;
+  const bool valid = kz < (KD + 1);
+  float2* base = w + f * MM + (long long)x * N * H1 + kz;
   float2 v[G];
 #pragma unroll
   for (int m = 0; m < G; ++m) {
     const int pos = j + m * S;
-    const bool rd = valid && (SIGN < 0 || kept_xy(pos, N, (N - 1) / 3));
-    v[m] = rd ? base[(long long)pos * g.h1] : make_float2(0.f, 0.f);
+    const bool rd = valid && (SIGN < 0 || kept_xy(pos, N, KD));
+    v[m] = rd ? base[(long long)pos * H1] : make_float2(0.f, 0.f);
   }
   fft_line<N, G, SIGN>(v, j, ColX<T>{smn, c}, tw, twlog);
   if (valid) {
 #pragma unroll
     for (int m = 0; m < G; ++m) {
       const int pos = j + m * S;
-      if (SIGN > 0 || kept_xy(pos, N, (N - 1) / 3)) base[(long long)pos * g.h1] = v[m];
+      if (SIGN > 0 || kept_xy(pos, N, KD)) base[(long long)pos * H1] = v[m];
     }
   }
 }
@@ -117,16 +119,18 @@ template <int N>
 __global__ void __launch_bounds__(NFCfg<N>::THREADS)
     k_ns_invx(const float2* __restrict__ u, float2* __restrict__ w, NSGeom g, int ktiles,
               const float2* __restrict__ tw, int twlog) {
+  constexpr long long H1 = N / 2 + 1, MM = (long long)N * N * H1;  // geometry of the n^3 grid
+  constexpr int KD = (N - 1) / 3;                                  // largest kept |k| (2/3 rule)
   using C = NFCfg<N>;
   constexpr int G = C::G, S = C::S, T = C::T;
   extern __shared__ float2 smn[];
   const int c = threadIdx.x % T, j = threadIdx.x / T;
   const int dky = blockIdx.x / ktiles;
   const int kz = (blockIdx.x - dky * ktiles) * T + c;
-  const bool valid = kz < g.kc;
-  const int ay = dense_to_a(dky, N, g.kd);
-  const long long q = (long long)ay * g.h1 + kz;
-  const long long rs = (long long)N * g.h1;
+  const bool valid = kz < (KD + 1);
+  const int ay = dense_to_a(dky, N, KD);
+  const long long q = (long long)ay * H1 + kz;
+  const long long rs = (long long)N * H1;
   const float ky = (float)kwav(ay, N), kzf = (float)kz;
   const ColX<T> xc{smn, c};
   auto load = [&](int f, float2(&v)[G], bool ikx) {
@@ -134,14 +138,14 @@ __global__ void __launch_bounds__(NFCfg<N>::THREADS)
     for (int m = 0; m < G; ++m) {
       const int pos = j + m * S;
       float2 a = make_float2(0.f, 0.f);
-      if (valid && kept_xy(pos, N, (N - 1) / 3)) a = u[f * g.M + pos * rs + q];
+      if (valid && kept_xy(pos, N, KD)) a = u[f * MM + pos * rs + q];
       v[m] = ikx ? mul_i(a, (float)kwav(pos, N)) : a;
     }
   };
   auto store = [&](int f, const float2(&v)[G]) {
     if (valid) {
 #pragma unroll
-      for (int m = 0; m < G; ++m) w[f * g.M + (j + m * S) * rs + q] = v[m];
+      for (int m = 0; m < G; ++m) w[f * MM + (j + m * S) * rs + q] = v[m];
     }
   };
   float2 a[G], b[G];
@@ -191,10 +195,12 @@ struct NZCfg {
 template <int N>
 __global__ void __launch_bounds__(NZCfg<N>::THREADS, 3)
     k_ns_z(float2* w, NSGeom g, const float2* __restrict__ tw, int twlog) {
+  constexpr long long H1 = N / 2 + 1, MM = (long long)N * N * H1;  // geometry of the n^3 grid
+  constexpr int KD = (N - 1) / 3;                                  // largest kept |k| (2/3 rule)
   using C = NZCfg<N>;
   constexpr int H = C::H, G = C::G, S = C::S;
   constexpr int LOGN = Log2<N>::value;
-  constexpr int KC = (N - 1) / 3 + 1;  // kept k_z count (2/3 rule)
+  constexpr int KC = KD + 1;  // kept k_z count
   extern __shared__ float2 smz[];
   const int li = threadIdx.x / S, j = threadIdx.x % S;
   const long long line = (long long)blockIdx.x * C::LPC + li;
@@ -204,7 +210,7 @@ __global__ void __launch_bounds__(NZCfg<N>::THREADS, 3)
 
   // inverse z transform of field f (half-complex -> N real points, two per slot)
   auto c2r = [&](int f, float2 (&U)[G]) {
-    const float2* src = w + f * g.M + line * g.h1;
+    const float2* src = w + f * MM + line * H1;
 #pragma unroll
     for (int m = 0; m < G; ++m) {
       const int k = j + m * S;
@@ -239,7 +245,7 @@ __global__ void __launch_bounds__(NZCfg<N>::THREADS, 3)
 #pragma unroll
     for (int m = 0; m < G; ++m) xc.st(j + m * S, U[m]);
     xc.sync();
-    float2* dst = w + f * g.M + line * g.h1;
+    float2* dst = w + f * MM + line * H1;
 #pragma unroll
     for (int m = 0; m < G; ++m) {
       const int k = j + m * S;
@@ -374,16 +380,18 @@ __global__ void __launch_bounds__(NFCfg<N>::THREADS, 2)
     k_ns_fwdx(const float2* __restrict__ nh, const float2* u0, const float2* u1, float2* out,
               NSGeom g, int ktiles, NSUpdate upd, int mode, const float2* __restrict__ extra,
               const float2* __restrict__ tw, int twlog) {
+  constexpr long long H1 = N / 2 + 1, MM = (long long)N * N * H1;  // geometry of the n^3 grid
+  constexpr int KD = (N - 1) / 3;                                  // largest kept |k| (2/3 rule)
   using C = NFCfg<N>;
   constexpr int G = C::G, S = C::S, T = C::T;
   extern __shared__ float2 smn[];
   const int c = threadIdx.x % T, j = threadIdx.x / T;
   const int dky = blockIdx.x / ktiles;
   const int kz = (blockIdx.x - dky * ktiles) * T + c;
-  const bool valid = kz < g.kc;
-  const int ay = dense_to_a(dky, N, g.kd);
-  const long long q = (long long)ay * g.h1 + kz;
-  const long long rs = (long long)N * g.h1;
+  const bool valid = kz < (KD + 1);
+  const int ay = dense_to_a(dky, N, KD);
+  const long long q = (long long)ay * H1 + kz;
+  const long long rs = (long long)N * H1;
   const ColX<T> xc{smn, c};
   // fields 0 and 1 are parked in shared memory after their transforms (this
   // thread's slots only), so one field at a time is held in registers
@@ -393,7 +401,7 @@ __global__ void __launch_bounds__(NFCfg<N>::THREADS, 2)
   for (int f = 0; f < 3; ++f) {
 #pragma unroll
     for (int m = 0; m < G; ++m)
-      V[m] = valid ? nh[f * g.M + (j + m * S) * rs + q] : make_float2(0.f, 0.f);
+      V[m] = valid ? nh[f * MM + (j + m * S) * rs + q] : make_float2(0.f, 0.f);
     fft_line<N, G, -1>(V, j, xc, tw, twlog);
     if (f < 2) {
 #pragma unroll
@@ -410,9 +418,9 @@ __global__ void __launch_bounds__(NFCfg<N>::THREADS, 2)
 #pragma unroll
   for (int m = 0; m < G; ++m) {
     const int pos = j + m * S;
-    if (!kept_xy(pos, N, (N - 1) / 3)) continue;
+    if (!kept_xy(pos, N, KD)) continue;
     ns_mode_update(cscale(park[m * C::THREADS], upd.scale), cscale(park[(G + m) * C::THREADS], upd.scale),
-                   cscale(V[m], upd.scale), kwav(pos, N), ky, kz, pos * rs + q, g.M, upd, mode, gforce, u0, u1,
+                   cscale(V[m], upd.scale), kwav(pos, N), ky, kz, pos * rs + q, MM, upd, mode, gforce, u0, u1,
                    extra, out);
   }
 }
