@@ -459,15 +459,23 @@ __global__ void k_forced_energy(const float2* __restrict__ u, NSGeom g, int kr, 
   if (threadIdx.x == 0) *ef = red[0];
 }
 
-constexpr int DIAG_BLOCKS = 256;
 constexpr int DIAG_WARPS = 8;
+constexpr size_t kNoAllocScratchDoubles = 262144;  // 2 MiB of partials for tarang_diag_noalloc
+
+// Blocks of the diagnostics reduction for a result of `width` doubles: up to
+// eight per SM of 152, as many as the no-allocation scratch holds partials
+// for (the same count on both paths, so both sum in the same order).
+static int diag_blocks(int width) {
+  const long long cap = (long long)(kNoAllocScratchDoubles / (size_t)width);
+  return (int)(cap < 152 * 8 ? cap : 152 * 8);
+}
 
 // Deterministic FP64 diagnostics over the kept modes.  A work item is 32
 // consecutive k_z of one (k_x, k_y) line; along a line the shell index is
 // non-decreasing, so a warp sums each shell's run with a segmented shuffle
 // reduction (fixed order) and one lane adds it to the warp's histogram.
-// Items are assigned to warps by a fixed grid stride; partials per block are
-// summed in block order by k_diag_final.
+// Items are assigned to warps by a fixed grid stride over diag_blocks(width)
+// blocks; partials per block are summed in block order by k_diag_final.
 __global__ void __launch_bounds__(DIAG_WARPS * 32)
     k_diag(const float2* __restrict__ u, NSGeom g, double nu, int kmax, double* part) {
   extern __shared__ double hist[];  // [DIAG_WARPS][kmax+1]
@@ -501,7 +509,7 @@ __global__ void __launch_bounds__(DIAG_WARPS * 32)
       e = 0.5 * w * s;
       const long long kx = kwav(ax, g.n), ky = kwav(ay, g.n);
       const long long k2 = kx * kx + ky * ky + (long long)kz * kz;
-      long long K = (long long)floor(sqrt((double)k2));
+      long long K = (long long)floorf(sqrtf((float)k2));  // exact after the two corrections below
       while (K * K > k2) --K;
       while ((K + 1) * (K + 1) <= k2) ++K;
       if (k2 >= K * K + K + 1) ++K;  // nint(|k|): |k| >= K + 1/2
@@ -621,7 +629,7 @@ static fftk_status ns_ensure(fftk_plan p) {
   if (e == cudaSuccess) e = cudaMalloc(&s->etab, sizeof(float2) * (size_t)s->etab_len);
   if (e == cudaSuccess) e = cudaMalloc(&s->ef, sizeof(double));
   if (e == cudaSuccess) e = cudaMemset(s->ef, 0, sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&s->part, sizeof(double) * (size_t)DIAG_BLOCKS * width);
+  if (e == cudaSuccess) e = cudaMalloc(&s->part, sizeof(double) * (size_t)diag_blocks(width) * width);
   if (e == cudaSuccess) e = cudaMalloc(&s->dout, sizeof(double) * (size_t)width);
   if (e == cudaSuccess) e = cudaMallocHost(&s->hout, sizeof(double) * (size_t)width);
   s->diag_smem = (int)(sizeof(double) * DIAG_WARPS * (s->kmax + 1));
@@ -839,11 +847,11 @@ static cudaError_t diag_launch(fftk_plan p, const float2* u, double nu, cudaStre
   const int width = 2 + s->kmax + 1;
   {
     LaunchScope ls(p, KK_NS_REDUCE, st);
-    k_diag<<<DIAG_BLOCKS, DIAG_WARPS * 32, s->diag_smem, st>>>(u, s->g, nu, s->kmax, s->part);
+    k_diag<<<diag_blocks(width), DIAG_WARPS * 32, s->diag_smem, st>>>(u, s->g, nu, s->kmax, s->part);
   }
   {
     LaunchScope ls(p, KK_NS_REDUCE, st);
-    k_diag_final<<<(width + 127) / 128, 128, 0, st>>>(s->part, width, DIAG_BLOCKS, s->dout);
+    k_diag_final<<<(width + 127) / 128, 128, 0, st>>>(s->part, width, diag_blocks(width), s->dout);
   }
   return cudaGetLastError();
 }
@@ -1116,7 +1124,6 @@ extern "C" fftk_status tarang_dealias_project(fftk_plan p, void* uhat, void* cud
 // process on every device that loads the library.
 namespace fftk {
 
-constexpr size_t kNoAllocScratchDoubles = 262144;  // 2 MiB: DIAG_BLOCKS x (2 + kmax + 1) for n <= 1024
 static __device__ __align__(256) double g_diag_scratch[kNoAllocScratchDoubles];
 
 constexpr int kNoAllocMaxDevices = 64;
@@ -1154,7 +1161,7 @@ extern "C" fftk_status tarang_diag_noalloc(int n, const void* uhat, double nu, d
   if (!is_pow2(n) || n < 8 || n > 1024) return FFTK_ERR_UNSUPPORTED_SIZE;
   const int kmax = ns_kmax(n);
   const int width = 2 + kmax + 1;
-  if ((size_t)DIAG_BLOCKS * (size_t)width > kNoAllocScratchDoubles) return FFTK_ERR_UNSUPPORTED_SIZE;
+  if ((size_t)diag_blocks(width) * (size_t)width > kNoAllocScratchDoubles) return FFTK_ERR_UNSUPPORTED_SIZE;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) {
     cudaGetLastError();
@@ -1168,8 +1175,8 @@ extern "C" fftk_status tarang_diag_noalloc(int n, const void* uhat, double nu, d
   // Every entry of the partials that k_diag_final reads is written by k_diag
   // in the same call, so nothing in the shared scratch needs clearing.
   const int smem = (int)(sizeof(double) * DIAG_WARPS * (kmax + 1));
-  k_diag<<<DIAG_BLOCKS, DIAG_WARPS * 32, smem, st>>>(static_cast<const float2*>(uhat), g, nu, kmax,
+  k_diag<<<diag_blocks(width), DIAG_WARPS * 32, smem, st>>>(static_cast<const float2*>(uhat), g, nu, kmax,
                                                    scratch);
-  k_diag_final<<<(width + 127) / 128, 128, 0, st>>>(scratch, width, DIAG_BLOCKS, diag_dev);
+  k_diag_final<<<(width + 127) / 128, 128, 0, st>>>(scratch, width, diag_blocks(width), diag_dev);
   return from_cuda(cudaGetLastError());
 }
