@@ -110,18 +110,29 @@ struct NFCfg {
   static constexpr size_t SMEM_FWD = SMEM + sizeof(float2) * 2 * G * THREADS;  // + two parked fields (forward x)
 };
 
+// Inverse x pass (two fields held at once): at n = 512, 16 values per thread
+// and 16 columns per tile (128-byte row segments); otherwise as NFCfg.
+template <int N>
+struct NICfg {
+  static constexpr int G = N == 512 ? 16 : NFCfg<N>::G;
+  static constexpr int S = N / G;
+  static constexpr int T = N == 512 ? 16 : NFCfg<N>::T;
+  static constexpr int THREADS = T * S;
+  static constexpr size_t SMEM = sizeof(float2) * (size_t)N * T;
+};
+
 // 1. inverse x pass with the curl.  Columns: kept (k_y, k_z); rows: k_x.
 //    U_c = F^-1_x(u_c), D_c = F^-1_x(i k_x u_c), then
 //    omega_x = i (k_y U_z - k_z U_y), omega_y = i k_z U_x - D_z,
 //    omega_z = D_y - i k_y U_x   (five transforms instead of six).
 //    Output field order: u_x, u_y, u_z, omega_x, omega_y, omega_z.
 template <int N>
-__global__ void __launch_bounds__(NFCfg<N>::THREADS)
+__global__ void __launch_bounds__(NICfg<N>::THREADS)
     k_ns_invx(const float2* __restrict__ u, float2* __restrict__ w, NSGeom g, int ktiles,
               const float2* __restrict__ tw, int twlog) {
   constexpr long long H1 = N / 2 + 1, MM = (long long)N * N * H1;  // geometry of the n^3 grid
   constexpr int KD = (N - 1) / 3;                                  // largest kept |k| (2/3 rule)
-  using C = NFCfg<N>;
+  using C = NICfg<N>;
   constexpr int G = C::G, S = C::S, T = C::T;
   extern __shared__ float2 smn[];
   const int c = threadIdx.x % T, j = threadIdx.x / T;
@@ -677,7 +688,7 @@ struct NSLaunch {
     std::call_once(once, [] {
       const int sx = (int)NXCfg<N>::SMEM;
       err = cudaFuncSetAttribute(k_ns_invx<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)NFCfg<N>::SMEM);
+                                 (int)NICfg<N>::SMEM);
       if (err == cudaSuccess)
         err = cudaFuncSetAttribute(k_ns_ypass<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sx);
       if (err == cudaSuccess)
@@ -705,9 +716,11 @@ struct NSLaunch {
     const NSGeom g = s->g;
     const int kx = (g.kc + X::T - 1) / X::T;
     const int kf = (g.kc + F::T - 1) / F::T;
+    using I = NICfg<N>;
+    const int ki = (g.kc + I::T - 1) / I::T;
     {
       LaunchScope ls(p, KK_NS_INVX, st);
-      k_ns_invx<N><<<g.nk * kf, F::THREADS, F::SMEM, st>>>(u, s->w, g, kf, p->d_tw, p->twlog);
+      k_ns_invx<N><<<g.nk * ki, I::THREADS, I::SMEM, st>>>(u, s->w, g, ki, p->d_tw, p->twlog);
     }
     {
       LaunchScope ls(p, KK_NS_INVY, st);
