@@ -107,7 +107,6 @@ struct NFCfg {
   static constexpr int T = S >= 32 ? (S == 32 ? 16 : (S == 64 ? 8 : 4)) : 16;
   static constexpr int THREADS = T * S;
   static constexpr size_t SMEM = sizeof(float2) * (size_t)N * T;
-  static constexpr size_t SMEM_FWD = SMEM + sizeof(float2) * 2 * G * THREADS;  // + two parked fields (forward x)
 };
 
 // Inverse x pass (two fields held at once): at n = 512, 16 values per thread
@@ -119,6 +118,18 @@ struct NICfg {
   static constexpr int T = N == 512 ? 16 : NFCfg<N>::T;
   static constexpr int THREADS = T * S;
   static constexpr size_t SMEM = sizeof(float2) * (size_t)N * T;
+};
+
+// Forward x pass (one field in registers, two parked): at n = 512, 16 columns
+// per tile (128-byte row segments) with 8 values per thread, 1024 threads.
+template <int N>
+struct NUCfg {
+  static constexpr int G = NFCfg<N>::G;
+  static constexpr int S = N / G;
+  static constexpr int T = N == 512 ? 16 : NFCfg<N>::T;
+  static constexpr int THREADS = T * S;
+  static constexpr size_t SMEM = sizeof(float2) * ((size_t)N * T + 2 * G * THREADS);
+  static constexpr int MINB = 1024 / THREADS < 16 ? 1024 / THREADS : 16;  // 64 registers
 };
 
 // 1. inverse x pass with the curl.  Columns: kept (k_y, k_z); rows: k_x.
@@ -387,13 +398,13 @@ __device__ __forceinline__ void ns_mode_update(float2 nx, float2 ny, float2 nz, 
 //    STAGE1: out = E (u0 + dt N)                      (out = u1)
 //    STAGE2: out = 1/2 E u0 + 1/2 (u1 + dt N)         (out = u0, in place)
 template <int N>
-__global__ void __launch_bounds__(NFCfg<N>::THREADS, 2)
+__global__ void __launch_bounds__(NUCfg<N>::THREADS, NUCfg<N>::MINB)
     k_ns_fwdx(const float2* __restrict__ nh, const float2* u0, const float2* u1, float2* out,
               NSGeom g, int ktiles, NSUpdate upd, int mode, const float2* __restrict__ extra,
               const float2* __restrict__ tw, int twlog) {
   constexpr long long H1 = N / 2 + 1, MM = (long long)N * N * H1;  // geometry of the n^3 grid
   constexpr int KD = (N - 1) / 3;                                  // largest kept |k| (2/3 rule)
-  using C = NFCfg<N>;
+  using C = NUCfg<N>;
   constexpr int G = C::G, S = C::S, T = C::T;
   extern __shared__ float2 smn[];
   const int c = threadIdx.x % T, j = threadIdx.x / T;
@@ -695,7 +706,7 @@ struct NSLaunch {
         err = cudaFuncSetAttribute(k_ns_ypass<N, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sx);
       if (err == cudaSuccess)
         err = cudaFuncSetAttribute(k_ns_fwdx<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)NFCfg<N>::SMEM_FWD);
+                                   (int)NUCfg<N>::SMEM);
       if (err == cudaSuccess)
         err = cudaFuncSetAttribute(k_ns_z<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)NZCfg<N>::SMEM);
@@ -718,6 +729,8 @@ struct NSLaunch {
     const int kf = (g.kc + F::T - 1) / F::T;
     using I = NICfg<N>;
     const int ki = (g.kc + I::T - 1) / I::T;
+    using U = NUCfg<N>;
+    const int ku = (g.kc + U::T - 1) / U::T;
     {
       LaunchScope ls(p, KK_NS_INVX, st);
       k_ns_invx<N><<<g.nk * ki, I::THREADS, I::SMEM, st>>>(u, s->w, g, ki, p->d_tw, p->twlog);
@@ -738,7 +751,7 @@ struct NSLaunch {
     }
     {
       LaunchScope ls(p, KK_NS_FWDX, st);
-      k_ns_fwdx<N><<<g.nk * kf, F::THREADS, F::SMEM_FWD, st>>>(s->w, u0, u1, out, g, kf, upd, mode,
+      k_ns_fwdx<N><<<g.nk * ku, U::THREADS, U::SMEM, st>>>(s->w, u0, u1, out, g, ku, upd, mode,
                                                           extra, p->d_tw, p->twlog);
     }
     return cudaGetLastError();
