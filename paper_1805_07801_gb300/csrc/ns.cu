@@ -109,24 +109,25 @@ struct NFCfg {
   static constexpr size_t SMEM = sizeof(float2) * (size_t)N * T;
 };
 
-// Inverse x pass (two fields held at once): at n = 512, 16 values per thread
-// and 16 columns per tile (128-byte row segments); otherwise as NFCfg.
+// Inverse x pass (two fields held at once): 16 values per thread for
+// n >= 512, 16 columns per tile (128-byte row segments) at n = 512 and 8 at
+// n = 1024; smaller grids as NFCfg.
 template <int N>
 struct NICfg {
-  static constexpr int G = N == 512 ? 16 : NFCfg<N>::G;
+  static constexpr int G = N >= 512 ? 16 : NFCfg<N>::G;
   static constexpr int S = N / G;
-  static constexpr int T = N == 512 ? 16 : NFCfg<N>::T;
+  static constexpr int T = N == 512 ? 16 : (N == 1024 ? 8 : NFCfg<N>::T);
   static constexpr int THREADS = T * S;
   static constexpr size_t SMEM = sizeof(float2) * (size_t)N * T;
 };
 
-// Forward x pass (one field in registers, two parked): at n = 512, 16 columns
-// per tile (128-byte row segments) with 8 values per thread, 1024 threads.
+// Forward x pass (one field in registers, two parked): 1024 threads, 8 values
+// per thread, 16 columns per tile at n = 512 and 8 at n = 1024.
 template <int N>
 struct NUCfg {
   static constexpr int G = NFCfg<N>::G;
   static constexpr int S = N / G;
-  static constexpr int T = N == 512 ? 16 : NFCfg<N>::T;
+  static constexpr int T = N == 512 ? 16 : (N == 1024 ? 8 : NFCfg<N>::T);
   static constexpr int THREADS = T * S;
   static constexpr size_t SMEM = sizeof(float2) * ((size_t)N * T + 2 * G * THREADS);
   static constexpr int MINB = 1024 / THREADS < 16 ? 1024 / THREADS : 16;  // 64 registers
