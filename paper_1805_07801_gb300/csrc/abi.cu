@@ -145,16 +145,18 @@ extern "C" fftk_status fftk_plan_create(int nx, int ny, int nz, fftk_dtype dtype
   if (ny > lt) lt = ny;
   if (nz > lt) lt = nz;
   p->twlog = ilog2(lt);
-  // Twiddles in FP64 (host libm), rounded once to FP32.
-  std::vector<float2> h((size_t)lt);
+  // Twiddle tables in FP64 (host libm), rounded once to FP32: for every
+  // power of two L <= LT, exp(-2 pi i m / L), m < L, at offset L (2 LT values).
+  std::vector<float2> h(2 * (size_t)lt, make_float2(1.f, 0.f));
   const double two_pi = 6.283185307179586476925286766559;
-  for (int m = 0; m < lt; ++m) {
-    const double ang = two_pi * (double)m / (double)lt;
-    h[(size_t)m] = make_float2((float)std::cos(ang), (float)(-std::sin(ang)));
-  }
-  e = cudaMalloc(&p->d_tw, sizeof(float2) * (size_t)lt);
+  for (int L = 1; L <= lt; L *= 2)
+    for (int m = 0; m < L; ++m) {
+      const double ang = two_pi * (double)m / (double)L;
+      h[(size_t)L + m] = make_float2((float)std::cos(ang), (float)(-std::sin(ang)));
+    }
+  e = cudaMalloc(&p->d_tw, sizeof(float2) * h.size());
   if (e == cudaSuccess)
-    e = cudaMemcpy(p->d_tw, h.data(), sizeof(float2) * (size_t)lt, cudaMemcpyHostToDevice);
+    e = cudaMemcpy(p->d_tw, h.data(), sizeof(float2) * h.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_err, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, sizeof(int));
   if (e == cudaSuccess && dtype == FFTK_R32_SPLIT16) e = upload_dft16_operands(p);

@@ -196,8 +196,11 @@ struct LineX {
 };
 
 // ---------------------------------------------------------------- engine ---
-// Twiddle table: tw[m] = exp(-2 pi i m / LT), m < LT, LT = 2^twlog >= L,
-// computed in FP64 on the host and rounded once to FP32.
+// Twiddle tables: the plan holds, for every power of two L' <= LT, the table
+// exp(-2 pi i m / L'), m < L', at offset L' of one array (entries computed in
+// FP64 on the host and rounded once to FP32).  A kernel gets the table of
+// size 2^TL >= L; the engine's index shift TL - log2(stage span) is a
+// compile-time constant.
 template <int L, int G>
 struct Shape {
   static_assert(L >= 1 && (L & (L - 1)) == 0, "L must be a power of two");
@@ -209,11 +212,11 @@ __host__ __device__ constexpr int fftk_min3(int a, int b, int c) {
   return a < b ? (a < c ? a : c) : (b < c ? b : c);
 }
 
-template <int L, int G, int SIGN, int NS>
+template <int L, int G, int SIGN, int NS, int TL>
 struct Stage {
   template <class X>
   __device__ __forceinline__ static void run(float2 (&v)[G], int j, const X& xc,
-                                             const float2* __restrict__ tw, int twlog) {
+                                             const float2* __restrict__ tw) {
     if constexpr (NS < L) {
       constexpr int REM = L / NS;
       constexpr int R = fftk_min3(16, G, REM);
@@ -232,7 +235,7 @@ struct Stage {
 #pragma unroll
           for (int r = 1; r < R; ++r) {
             // exp(SIGN 2 pi i r k / (NS R))
-            const float2 w = __ldg(&tw[(r * k) << (twlog - LOG_NSR)]);
+            const float2 w = __ldg(&tw[(r * k) << (TL - LOG_NSR)]);
             a[r] = SIGN < 0 ? cmul(a[r], w) : cmulc(a[r], w);
           }
         }
@@ -251,7 +254,7 @@ struct Stage {
 #pragma unroll
         for (int m = 0; m < G; ++m) v[m] = xc.ld(j + m * S);
         xc.sync();
-        Stage<L, G, SIGN, NS * R>::run(v, j, xc, tw, twlog);
+        Stage<L, G, SIGN, NS * R, TL>::run(v, j, xc, tw);
       }
     }
   }
@@ -259,10 +262,11 @@ struct Stage {
 
 // Full L-point transform of the line held in v (natural pattern in and out).
 // The exchange buffer must be free on entry; it is free again on exit.
-template <int L, int G, int SIGN, class X>
-__device__ __forceinline__ void fft_line(float2 (&v)[G], int j, const X& xc,
-                                         const float2* __restrict__ tw, int twlog) {
-  Stage<L, G, SIGN, 1>::run(v, j, xc, tw, twlog);
+// tw: the twiddle table of size 2^TL (TL >= log2 L; by default the size-L one).
+template <int L, int G, int SIGN, int TL = Log2<L>::value, class X>
+__device__ __forceinline__ void fft_line(float2 (&v)[G], int j, const X& xc, const float2* __restrict__ tw) {
+  static_assert((1 << TL) >= L, "twiddle table too short");
+  Stage<L, G, SIGN, 1, TL>::run(v, j, xc, tw);
 }
 
 // Elements per thread used by the passes for a line of length L.

@@ -29,7 +29,7 @@ struct ZCfg {
 template <int N>
 __global__ void __launch_bounds__(ZCfg<N>::THREADS, ZCfg<N>::MINB)
     k_z_r2c(const float* __restrict__ in, float2* __restrict__ out, long long nlines,
-            const float2* __restrict__ tw, int twlog, float scale) {
+            const float2* __restrict__ tw, float scale) {  // tw: size-N table
   using C = ZCfg<N>;
   constexpr int H = C::H, G = C::G, S = C::S;
   constexpr int LOGN = Log2<N>::value;
@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(ZCfg<N>::THREADS, ZCfg<N>::MINB)
   const float2* src = reinterpret_cast<const float2*>(in + line * N);
 #pragma unroll
   for (int m = 0; m < G; ++m) v[m] = valid ? src[j + m * S] : make_float2(0.f, 0.f);
-  fft_line<H, G, -1>(v, j, xc, tw, twlog);
+  fft_line<H, G, -1, LOGN>(v, j, xc, tw);
 #pragma unroll
   for (int m = 0; m < G; ++m) xc.st(j + m * S, v[m]);
   xc.sync();
@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(ZCfg<N>::THREADS, ZCfg<N>::MINB)
       const float2 E = cscale(cadd(A, Bc), 0.5f);
       const float2 D = csub(A, Bc);
       const float2 O = make_float2(0.5f * D.y, -0.5f * D.x);  // D / (2i)
-      const float2 W = __ldg(&tw[k << (twlog - LOGN)]);       // exp(-2 pi i k / N)
+      const float2 W = __ldg(&tw[k]);                          // exp(-2 pi i k / N)
       dst[k] = cscale(cadd(E, cmul(W, O)), scale);
     }
     if (j == 0) dst[H] = make_float2((v[0].x - v[0].y) * scale, 0.f);
@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(ZCfg<N>::THREADS, ZCfg<N>::MINB)
 template <int N>
 __global__ void __launch_bounds__(ZCfg<N>::THREADS, ZCfg<N>::MINB)
     k_z_c2r(const float2* __restrict__ in, float* __restrict__ out, long long nlines,
-            const float2* __restrict__ tw, int twlog) {
+            const float2* __restrict__ tw) {  // tw: size-N table
   using C = ZCfg<N>;
   constexpr int H = C::H, G = C::G, S = C::S;
   constexpr int LOGN = Log2<N>::value;
@@ -95,11 +95,11 @@ __global__ void __launch_bounds__(ZCfg<N>::THREADS, ZCfg<N>::MINB)
     }
     const float2 Bc = cconj(B);
     const float2 E = cadd(A, Bc);
-    const float2 W = __ldg(&tw[k << (twlog - LOGN)]);
+    const float2 W = __ldg(&tw[k]);
     const float2 O = cmulc(csub(A, Bc), W);
     v[m] = make_float2(E.x - O.y, E.y + O.x);
   }
-  fft_line<H, G, +1>(v, j, xc, tw, twlog);
+  fft_line<H, G, +1, LOGN>(v, j, xc, tw);
   if (valid) {
     float2* dst = reinterpret_cast<float2*>(out + line * N);
 #pragma unroll
@@ -126,7 +126,7 @@ struct CCfg {
 template <int L, int SIGN>
 __global__ void __launch_bounds__(CCfg<L>::THREADS, CCfg<L>::MINB)
     k_cpass(const float2* in, float2* out, long long Q, long long qtiles,
-            const float2* __restrict__ tw, int twlog, float scale) {
+            const float2* __restrict__ tw, float scale) {  // tw: size-L table
   using C = CCfg<L>;
   constexpr int G = C::G, S = C::S, T = C::T;
   extern __shared__ float2 smc[];
@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(CCfg<L>::THREADS, CCfg<L>::MINB)
 #pragma unroll
   for (int m = 0; m < G; ++m)
     v[m] = valid ? in[base + (long long)(j + m * S) * Q] : make_float2(0.f, 0.f);
-  fft_line<L, G, SIGN>(v, j, ColX<T>{smc, c}, tw, twlog);
+  fft_line<L, G, SIGN>(v, j, ColX<T>{smc, c}, tw);
   if (valid) {
 #pragma unroll
     for (int m = 0; m < G; ++m) out[base + (long long)(j + m * S) * Q] = cscale(v[m], scale);
@@ -154,7 +154,7 @@ static cudaError_t z_r2c_n(fftk_plan p, const float* in, float2* out, long long 
   using C = ZCfg<N>;
   const long long blocks = (nl + C::LPC - 1) / C::LPC;
   LaunchScope ls(p, KK_Z_R2C, st);
-  k_z_r2c<N><<<(unsigned)blocks, C::THREADS, 0, st>>>(in, out, nl, p->d_tw, p->twlog, scale);
+  k_z_r2c<N><<<(unsigned)blocks, C::THREADS, 0, st>>>(in, out, nl, twiddles(p, N), scale);
   return cudaGetLastError();
 }
 
@@ -164,7 +164,7 @@ static cudaError_t z_c2r_n(fftk_plan p, const float2* in, float* out, long long 
   using C = ZCfg<N>;
   const long long blocks = (nl + C::LPC - 1) / C::LPC;
   LaunchScope ls(p, KK_Z_C2R, st);
-  k_z_c2r<N><<<(unsigned)blocks, C::THREADS, 0, st>>>(in, out, nl, p->d_tw, p->twlog);
+  k_z_c2r<N><<<(unsigned)blocks, C::THREADS, 0, st>>>(in, out, nl, twiddles(p, N));
   return cudaGetLastError();
 }
 
@@ -182,8 +182,7 @@ static cudaError_t cpass_l(fftk_plan p, const float2* in, float2* out, long long
   const long long qtiles = (Q + C::T - 1) / C::T;
   const long long blocks = P * qtiles;
   LaunchScope ls(p, kind, st);
-  k_cpass<L, SIGN><<<(unsigned)blocks, C::THREADS, C::SMEM, st>>>(in, out, Q, qtiles, p->d_tw,
-                                                                   p->twlog, scale);
+  k_cpass<L, SIGN><<<(unsigned)blocks, C::THREADS, C::SMEM, st>>>(in, out, Q, qtiles, twiddles(p, L), scale);
   return cudaGetLastError();
 }
 

@@ -174,7 +174,7 @@ static void build_dft16_operands(int sign, std::vector<__half>& out) {
 template <int L, int SIGN>
 __global__ void __launch_bounds__(TC2<L>::THREADS, TC2<L>::MINB)
     k_cpass_tc(const float2* in, float2* out, long long Q, long long qtiles, long long ntiles,
-               const float2* __restrict__ tw, int twlog, float out_scale,
+               const float2* __restrict__ tw, float out_scale,  // tw: size-L table
                const __half* __restrict__ bops, int* err) {
   using C = TC2<L>;
   constexpr int T = C::T, R0 = C::R0, A1 = C::A1, NT = C::THREADS;
@@ -198,12 +198,12 @@ __global__ void __launch_bounds__(TC2<L>::THREADS, TC2<L>::MINB)
   for (int i = t; i < 2 * tc::kBBytes / 16; i += NT)
     reinterpret_cast<uint4*>(Bs)[i] = reinterpret_cast<const uint4*>(bops)[i];
   for (int i = t; i < 256; i += NT) {
-    float2 w = __ldg(&tw[i << (twlog - 8)]);
+    float2 w = __ldg(&tw[i * (L / 256)]);
     if (SIGN > 0) w.y = -w.y;
     w256[i] = make_float2(w.x * 0.0625f, w.y * 0.0625f);
   }
   for (int i = t; i < L; i += NT) {
-    float2 w = __ldg(&tw[i << (twlog - C::LOGL)]);
+    float2 w = __ldg(&tw[i]);
     if (SIGN > 0) w.y = -w.y;
     wL[i] = w;
   }
@@ -381,7 +381,7 @@ static cudaError_t cpass_tc_l(fftk_plan p, const float2* in, float2* out, long l
   const int blocks = (int)(ntiles < cap ? ntiles : cap);
   const __half* bops = p->d_dft16 + (SIGN < 0 ? 0 : 2 * 32 * 64);
   LaunchScope ls(p, kind, st);
-  k_cpass_tc<L, SIGN><<<blocks, C::THREADS, C::SMEM, st>>>(in, out, Q, qtiles, ntiles, p->d_tw, p->twlog, scale,
+  k_cpass_tc<L, SIGN><<<blocks, C::THREADS, C::SMEM, st>>>(in, out, Q, qtiles, ntiles, twiddles(p, L), scale,
                                                          bops, p->d_err);
   return cudaGetLastError();
 }

@@ -56,7 +56,7 @@ struct fftk_plan_s {
   fftk_dtype dtype;
   int device;
   int twlog;                 // LT = 2^twlog = max(nx, ny, nz)
-  float2* d_tw = nullptr;    // exp(-2 pi i m / LT), m < LT
+  float2* d_tw = nullptr;    // twiddle tables: at offset L (L = 1, 2, 4, ..., LT), exp(-2 pi i m / L), m < L
   __half* d_dft16 = nullptr; // split-FP16 DFT-16 operands (FFTK_R32_SPLIT16): forward, inverse
   int* d_err = nullptr;      // device error word (bounded waits that expired)
   // c2r workspace (one complex field per batch element)
@@ -72,6 +72,9 @@ struct fftk_plan_s {
 };
 
 namespace fftk {
+
+// The plan's twiddle table of size L (a power of two <= LT): exp(-2 pi i m / L), m < L.
+inline const float2* twiddles(const fftk_plan_s* p, int L) { return p->d_tw + L; }
 
 // Launch bracketing: counts the launch and records profiling events.
 struct LaunchScope {

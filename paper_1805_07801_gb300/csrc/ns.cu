@@ -68,7 +68,7 @@ struct NXCfg {
 //    SIGN=-1: every y row is read, only kept k_y rows are written.
 template <int N, int SIGN>
 __global__ void __launch_bounds__(NXCfg<N>::THREADS, NXCfg<N>::MINB)
-    k_ns_ypass(float2* w, NSGeom g, int ktiles, const float2* __restrict__ tw, int twlog) {
+    k_ns_ypass(float2* w, NSGeom g, int ktiles, const float2* __restrict__ tw) {
   constexpr long long H1 = N / 2 + 1, MM = (long long)N * N * H1;  // geometry of the n^3 grid
   constexpr int KD = (N - 1) / 3;                                  // largest kept |k| (2/3 rule)
   using C = NXCfg<N>;
@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(NXCfg<N>::THREADS, NXCfg<N>::MINB)
     const bool rd = valid && (SIGN < 0 || kept_xy(pos, N, KD));
     v[m] = rd ? base[(long long)pos * H1] : make_float2(0.f, 0.f);
   }
-  fft_line<N, G, SIGN>(v, j, ColX<T>{smn, c}, tw, twlog);
+  fft_line<N, G, SIGN>(v, j, ColX<T>{smn, c}, tw);
   if (valid) {
 #pragma unroll
     for (int m = 0; m < G; ++m) {
@@ -141,7 +141,7 @@ struct NUCfg {
 template <int N>
 __global__ void __launch_bounds__(NICfg<N>::THREADS)
     k_ns_invx(const float2* __restrict__ u, float2* __restrict__ w, NSGeom g, int ktiles,
-              const float2* __restrict__ tw, int twlog) {
+              const float2* __restrict__ tw) {
   constexpr long long H1 = N / 2 + 1, MM = (long long)N * N * H1;  // geometry of the n^3 grid
   constexpr int KD = (N - 1) / 3;                                  // largest kept |k| (2/3 rule)
   using C = NICfg<N>;
@@ -173,23 +173,23 @@ __global__ void __launch_bounds__(NICfg<N>::THREADS)
   };
   float2 a[G], b[G];
   load(1, a, true);
-  fft_line<N, G, +1>(a, j, xc, tw, twlog);  // D_y
+  fft_line<N, G, +1>(a, j, xc, tw);  // D_y
   load(0, b, false);
-  fft_line<N, G, +1>(b, j, xc, tw, twlog);  // U_x
+  fft_line<N, G, +1>(b, j, xc, tw);  // U_x
   store(0, b);
 #pragma unroll
   for (int m = 0; m < G; ++m) a[m] = csub(a[m], mul_i(b[m], ky));  // omega_z
   store(5, a);
   load(2, a, true);
-  fft_line<N, G, +1>(a, j, xc, tw, twlog);  // D_z
+  fft_line<N, G, +1>(a, j, xc, tw);  // D_z
 #pragma unroll
   for (int m = 0; m < G; ++m) a[m] = csub(mul_i(b[m], kzf), a[m]);  // omega_y
   store(4, a);
   load(1, a, false);
-  fft_line<N, G, +1>(a, j, xc, tw, twlog);  // U_y
+  fft_line<N, G, +1>(a, j, xc, tw);  // U_y
   store(1, a);
   load(2, b, false);
-  fft_line<N, G, +1>(b, j, xc, tw, twlog);  // U_z
+  fft_line<N, G, +1>(b, j, xc, tw);  // U_z
   store(2, b);
 #pragma unroll
   for (int m = 0; m < G; ++m)
@@ -217,7 +217,7 @@ struct NZCfg {
 //    accumulators of n, so at most 3 fields are held in registers.
 template <int N>
 __global__ void __launch_bounds__(NZCfg<N>::THREADS, 3)
-    k_ns_z(float2* w, NSGeom g, const float2* __restrict__ tw, int twlog) {
+    k_ns_z(float2* w, NSGeom g, const float2* __restrict__ tw) {
   constexpr long long H1 = N / 2 + 1, MM = (long long)N * N * H1;  // geometry of the n^3 grid
   constexpr int KD = (N - 1) / 3;                                  // largest kept |k| (2/3 rule)
   using C = NZCfg<N>;
@@ -246,11 +246,11 @@ __global__ void __launch_bounds__(NZCfg<N>::THREADS, 3)
       }
       const float2 Bc = cconj(B);
       const float2 E = cadd(A, Bc);
-      const float2 W = __ldg(&tw[k << (twlog - LOGN)]);
+      const float2 W = __ldg(&tw[k]);
       const float2 O = cmulc(csub(A, Bc), W);
       U[m] = make_float2(E.x - O.y, E.y + O.x);
     }
-    fft_line<H, G, +1>(U, j, xc, tw, twlog);
+    fft_line<H, G, +1, LOGN>(U, j, xc, tw);
   };
 
   {
@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(NZCfg<N>::THREADS, 3)
   }
   // forward z transforms of n (N real points -> half-complex), k_z < kc written
   auto r2c = [&](int f, float2 (&U)[G]) {
-    fft_line<H, G, -1>(U, j, xc, tw, twlog);
+    fft_line<H, G, -1, LOGN>(U, j, xc, tw);
 #pragma unroll
     for (int m = 0; m < G; ++m) xc.st(j + m * S, U[m]);
     xc.sync();
@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(NZCfg<N>::THREADS, 3)
       const float2 E = cscale(cadd(A, Bc), 0.5f);
       const float2 D = csub(A, Bc);
       const float2 O = make_float2(0.5f * D.y, -0.5f * D.x);
-      const float2 W = __ldg(&tw[k << (twlog - LOGN)]);
+      const float2 W = __ldg(&tw[k]);
       if (valid && k < KC) dst[k] = cadd(E, cmul(W, O));
     }
     xc.sync();
@@ -402,7 +402,7 @@ template <int N>
 __global__ void __launch_bounds__(NUCfg<N>::THREADS, NUCfg<N>::MINB)
     k_ns_fwdx(const float2* __restrict__ nh, const float2* u0, const float2* u1, float2* out,
               NSGeom g, int ktiles, NSUpdate upd, int mode, const float2* __restrict__ extra,
-              const float2* __restrict__ tw, int twlog) {
+              const float2* __restrict__ tw) {
   constexpr long long H1 = N / 2 + 1, MM = (long long)N * N * H1;  // geometry of the n^3 grid
   constexpr int KD = (N - 1) / 3;                                  // largest kept |k| (2/3 rule)
   using C = NUCfg<N>;
@@ -425,7 +425,7 @@ __global__ void __launch_bounds__(NUCfg<N>::THREADS, NUCfg<N>::MINB)
 #pragma unroll
     for (int m = 0; m < G; ++m)
       V[m] = valid ? nh[f * MM + (j + m * S) * rs + q] : make_float2(0.f, 0.f);
-    fft_line<N, G, -1>(V, j, xc, tw, twlog);
+    fft_line<N, G, -1>(V, j, xc, tw);
     if (f < 2) {
 #pragma unroll
       for (int m = 0; m < G; ++m) park[(f * G + m) * C::THREADS] = V[m];
@@ -734,26 +734,26 @@ struct NSLaunch {
     const int ku = (g.kc + U::T - 1) / U::T;
     {
       LaunchScope ls(p, KK_NS_INVX, st);
-      k_ns_invx<N><<<g.nk * ki, I::THREADS, I::SMEM, st>>>(u, s->w, g, ki, p->d_tw, p->twlog);
+      k_ns_invx<N><<<g.nk * ki, I::THREADS, I::SMEM, st>>>(u, s->w, g, ki, twiddles(p, N));
     }
     {
       LaunchScope ls(p, KK_NS_INVY, st);
-      k_ns_ypass<N, 1><<<6 * N * kx, X::THREADS, X::SMEM, st>>>(s->w, g, kx, p->d_tw, p->twlog);
+      k_ns_ypass<N, 1><<<6 * N * kx, X::THREADS, X::SMEM, st>>>(s->w, g, kx, twiddles(p, N));
     }
     {
       LaunchScope ls(p, KK_NS_Z, st);
       const long long lines = (long long)N * N;
-      k_ns_z<N><<<(unsigned)((lines + Z::LPC - 1) / Z::LPC), Z::THREADS, Z::SMEM, st>>>(s->w, g, p->d_tw,
-                                                                                       p->twlog);
+      k_ns_z<N><<<(unsigned)((lines + Z::LPC - 1) / Z::LPC), Z::THREADS, Z::SMEM, st>>>(s->w, g,
+                                                                                       twiddles(p, N));
     }
     {
       LaunchScope ls(p, KK_NS_FWDY, st);
-      k_ns_ypass<N, -1><<<3 * N * kx, X::THREADS, X::SMEM, st>>>(s->w, g, kx, p->d_tw, p->twlog);
+      k_ns_ypass<N, -1><<<3 * N * kx, X::THREADS, X::SMEM, st>>>(s->w, g, kx, twiddles(p, N));
     }
     {
       LaunchScope ls(p, KK_NS_FWDX, st);
       k_ns_fwdx<N><<<g.nk * ku, U::THREADS, U::SMEM, st>>>(s->w, u0, u1, out, g, ku, upd, mode,
-                                                          extra, p->d_tw, p->twlog);
+                                                          extra, twiddles(p, N));
     }
     return cudaGetLastError();
   }
