@@ -58,6 +58,7 @@ def lib():
             L.oracle_diag.argtypes = [vp, c.c_int, c.c_double, dp, dp, vp, c.c_int]
             L.oracle_transfer.argtypes = [vp, vp, c.c_int]
             L.oracle_transfer.restype = c.c_double
+            L.oracle_transfer_spectrum.argtypes = [vp, vp, c.c_int, vp, c.c_int]
             L.oracle_ic_taylor_green.argtypes = [vp, c.c_int]
             L.oracle_ic_abc.argtypes = [vp, c.c_int]
             L.oracle_ic_random.argtypes = [vp, vp, c.c_int, c.c_double, c.c_double]
@@ -209,6 +210,17 @@ def transfer(uhat, nhat) -> float:
     uhat = np.ascontiguousarray(uhat, dtype=np.complex128)
     nhat = np.ascontiguousarray(nhat, dtype=np.complex128)
     return float(lib().oracle_transfer(_ptr(uhat), _ptr(nhat), uhat.shape[1]))
+
+
+def transfer_spectrum(uhat, nhat, kmax=None) -> np.ndarray:
+    """T(K) = sum over shell K of w Re(conj(u) . N), K = 0..kmax."""
+    uhat = np.ascontiguousarray(uhat, dtype=np.complex128)
+    nhat = np.ascontiguousarray(nhat, dtype=np.complex128)
+    n = uhat.shape[1]
+    kmax = kmax_shell(n) if kmax is None else kmax
+    T = np.zeros(kmax + 1, dtype=np.float64)
+    _check(lib().oracle_transfer_spectrum(_ptr(uhat), _ptr(nhat), n, _ptr(T), kmax), "transfer_spectrum")
+    return T
 
 
 def ic_taylor_green(n: int) -> np.ndarray:

@@ -486,6 +486,26 @@ double oracle_transfer(const cplx *u, const cplx *nh, int n) {
   return t;
 }
 
+/* Energy transfer spectrum of the nonlinear term (the scale-by-scale
+ * analysis of Sec. 1 / Sec. 7): T(K) = sum over the shell K = nint|k| of
+ * w Re(conj(u) . N), w = 1 on k_z = 0 and k_z = n/2, else 2.  The flux
+ * through K is Pi(K) = -sum_{K' <= K} T(K'). */
+int oracle_transfer_spectrum(const cplx *u, const cplx *nh, int n, double *T, int kmax) {
+  const long N = n, HZ = n / 2 + 1, M = N * N * HZ;
+  for (int K = 0; K <= kmax; K++) T[K] = 0.0;
+  for (long a = 0; a < N; a++)
+    for (long b = 0; b < N; b++)
+      for (long c = 0; c < HZ; c++) {
+        long idx = (a * N + b) * HZ + c;
+        long kx = kxy(a, N), ky = kxy(b, N), k2 = kx * kx + ky * ky + c * c;
+        double t = 0.0;
+        for (int f = 0; f < 3; f++) t += creal(conj(u[f * M + idx]) * nh[f * M + idx]);
+        long K = shell_of(k2);
+        if (K <= kmax) T[K] += mode_weight(c, N) * t;
+      }
+  return 0;
+}
+
 /* ----------------------------------------------------- initial fields ---- */
 
 static int ic_from_real(const double *ur, cplx *uhat, int n) {

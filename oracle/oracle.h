@@ -67,6 +67,8 @@ int oracle_diag(const ocplx *uhat, int n, double nu, double *E, double *eps,
                 double *EK, int kmax);
 /* Energy transfer sum w Re(conj(u).N); zero for the rotational form. */
 double oracle_transfer(const ocplx *uhat, const ocplx *nhat, int n);
+/* T(K), K = 0..kmax: per-shell sum of w Re(conj(u) . N) (shell nint|k|). */
+int oracle_transfer_spectrum(const ocplx *uhat, const ocplx *nhat, int n, double *T, int kmax);
 
 /* Initial conditions. */
 int oracle_ic_taylor_green(ocplx *uhat, int n);  /* u = (sin x cos y, -cos x sin y, 0) */

@@ -187,3 +187,65 @@ def test_diag_energy_is_parseval_on_untruncated_field(oracle_mod):
     assert np.max(np.abs(u[:, :, :, n // 2])) > 0.01
     E = oracle_mod.diag(u)[0]
     assert abs(E - 0.5 * np.mean(np.sum(ur**2, axis=0))) < 1e-14
+
+
+def _shell_index(n):
+    KX, KY, KZ = _kvec(n)
+    return np.floor(np.sqrt(KX**2 + KY**2 + KZ**2) + 0.5).astype(int)
+
+
+def test_transfer_spectrum_is_shell_filtered_power(oracle_mod):
+    # Parseval per shell: T(K) = <u_K . N> over the box, u_K the real field of
+    # the modes of shell K, computed here on the full complex spectrum (numpy
+    # FFT, no Hermitian weights) instead of the half spectrum with w = 1 or 2.
+    n = 16
+    u = _random_uhat(oracle_mod, n, seed=5, k0=3.0)
+    N = oracle_mod.ns_rhs(u)
+    T = oracle_mod.transfer_spectrum(u, N)
+    ur = np.fft.irfftn(u * n**3, s=(n, n, n), axes=(-3, -2, -1))
+    Nr = np.fft.irfftn(N * n**3, s=(n, n, n), axes=(-3, -2, -1))
+    U = np.fft.fftn(ur, axes=(-3, -2, -1)) / n**3
+    a = np.arange(n)
+    k = np.where(2 * a < n, a, a - n)
+    KX, KY, KZ = np.meshgrid(k, k, k, indexing="ij")
+    shell = np.floor(np.sqrt(KX**2 + KY**2 + KZ**2) + 0.5).astype(int)
+    want = np.zeros_like(T)
+    for K in range(len(T)):
+        uK = np.real(np.fft.ifftn(np.where(shell == K, U, 0), axes=(-3, -2, -1))) * n**3
+        want[K] = np.mean(np.sum(uK * Nr, axis=0))
+    scale = np.max(np.abs(want))
+    assert scale > 1e-4
+    assert np.max(np.abs(T - want)) < 1e-13 * scale
+
+
+def test_transfer_spectrum_conserves_and_matches_total(oracle_mod):
+    # the nonlinear term only moves energy between shells: sum_K T(K) = 0,
+    # while the individual shells are far from zero
+    n = 16
+    u = _random_uhat(oracle_mod, n, seed=6, k0=3.0)
+    N = oracle_mod.ns_rhs(u)
+    T = oracle_mod.transfer_spectrum(u, N)
+    assert np.max(np.abs(T)) > 1e-3
+    assert abs(T.sum()) < 1e-14 * np.sum(np.abs(T))
+    flux = -np.cumsum(T)
+    assert abs(flux[-1]) < 1e-14 * np.sum(np.abs(T))
+
+
+def test_transfer_spectrum_of_forcing_is_eps_in_forced_shell(oracle_mod):
+    # the constant-power forcing on 1 <= |k|^2 <= 2 (exactly shell K = 1) adds
+    # eps to T(1) and nothing elsewhere
+    n, eps = 16, 0.1
+    u = _random_uhat(oracle_mod, n, seed=7, k0=2.0)
+    T0 = oracle_mod.transfer_spectrum(u, oracle_mod.ns_rhs(u))
+    Tf = oracle_mod.transfer_spectrum(u, oracle_mod.ns_rhs(u, force_eps=eps, force_k2=(1, 2)))
+    d = Tf - T0
+    assert abs(d[1] - eps) < 1e-14
+    assert np.max(np.abs(np.delete(d, 1))) < 1e-15
+
+
+def test_transfer_spectrum_drops_shells_beyond_kmax(oracle_mod):
+    n = 16
+    u = _random_uhat(oracle_mod, n, seed=8, k0=3.0)
+    N = oracle_mod.ns_rhs(u)
+    T = oracle_mod.transfer_spectrum(u, N)
+    assert np.array_equal(oracle_mod.transfer_spectrum(u, N, kmax=5), T[:6])
