@@ -59,6 +59,7 @@ def lib():
             L.oracle_transfer.argtypes = [vp, vp, c.c_int]
             L.oracle_transfer.restype = c.c_double
             L.oracle_transfer_spectrum.argtypes = [vp, vp, c.c_int, vp, c.c_int]
+            L.oracle_shell_transfer.argtypes = [vp, c.c_int, c.c_int, vp, vp]
             L.oracle_ic_taylor_green.argtypes = [vp, c.c_int]
             L.oracle_ic_abc.argtypes = [vp, c.c_int]
             L.oracle_ic_random.argtypes = [vp, vp, c.c_int, c.c_double, c.c_double]
@@ -220,6 +221,16 @@ def transfer_spectrum(uhat, nhat, kmax=None) -> np.ndarray:
     kmax = kmax_shell(n) if kmax is None else kmax
     T = np.zeros(kmax + 1, dtype=np.float64)
     _check(lib().oracle_transfer_spectrum(_ptr(uhat), _ptr(nhat), n, _ptr(T), kmax), "transfer_spectrum")
+    return T
+
+
+def shell_transfer(uhat, bounds) -> np.ndarray:
+    """T[r, g]: energy rate from shell g to shell r, shells bounds[i] <= nint|k| < bounds[i+1]."""
+    uhat = np.ascontiguousarray(uhat, dtype=np.complex128)
+    b = np.ascontiguousarray(bounds, dtype=np.int32)
+    S = len(b) - 1
+    T = np.zeros((S, S), dtype=np.float64)
+    _check(lib().oracle_shell_transfer(_ptr(uhat), uhat.shape[1], S, _ptr(b), _ptr(T)), "shell_transfer")
     return T
 
 

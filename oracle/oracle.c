@@ -506,6 +506,81 @@ int oracle_transfer_spectrum(const cplx *u, const cplx *nh, int n, double *T, in
   return 0;
 }
 
+/* Shell-to-shell energy transfer (Tarang's scale-by-scale analysis, Sec. 1):
+ * shell i holds the modes with bounds[i] <= nint|k| < bounds[i+1], and
+ *   T[r * nshells + g] = -<u_r . (u . grad) u_g>
+ * is the rate at which shell r (receiver) gains energy from shell g (giver)
+ * through the advection by the whole field u.  Pseudo-spectral evaluation:
+ * for each giver, the gradient i k_j u_g,i of its modes and u itself go to
+ * real space, the product u_j d_j u_g,i comes back, and the receiver sums
+ * w Re(conj(u_r) . product) over its modes. */
+int oracle_shell_transfer(const cplx *u, int n, int nshells, const int *bounds, double *T) {
+  if (!is_pow2(n) || n < 2 || nshells < 1) return -1;
+  for (int i = 0; i < nshells; i++)
+    if (bounds[i] < 0 || bounds[i + 1] <= bounds[i]) return -1;
+  const long N = n, HZ = n / 2 + 1, M = N * N * HZ, R = N * N * N;
+  int *sh = (int *)malloc(sizeof(int) * (size_t)M); /* shell of each mode, -1 for none */
+  double *ur = (double *)malloc(sizeof(double) * 3 * (size_t)R);
+  double *gr = (double *)malloc(sizeof(double) * 9 * (size_t)R);
+  double *pr = (double *)malloc(sizeof(double) * (size_t)R);
+  cplx *gh = (cplx *)malloc(sizeof(cplx) * (size_t)M);
+  cplx *ph = (cplx *)malloc(sizeof(cplx) * 3 * (size_t)M);
+  if (!sh || !ur || !gr || !pr || !gh || !ph) return -2;
+  for (long a = 0; a < N; a++)
+    for (long b = 0; b < N; b++)
+      for (long c = 0; c < HZ; c++) {
+        long kx = kxy(a, N), ky = kxy(b, N), K = shell_of(kx * kx + ky * ky + c * c);
+        int s = -1;
+        for (int i = 0; i < nshells; i++)
+          if (K >= bounds[i] && K < bounds[i + 1]) s = i;
+        sh[(a * N + b) * HZ + c] = s;
+      }
+  for (int f = 0; f < 3; f++) oracle_irfft3(u + f * M, ur + f * R, n, n, n);
+  for (long i = 0; i < (long)nshells * nshells; i++) T[i] = 0.0;
+  for (int g = 0; g < nshells; g++) {
+    /* d_j u_g,i in real space, gr[(i * 3 + j) R + x] */
+    for (int i = 0; i < 3; i++)
+      for (int j = 0; j < 3; j++) {
+        for (long a = 0; a < N; a++)
+          for (long b = 0; b < N; b++)
+            for (long c = 0; c < HZ; c++) {
+              long idx = (a * N + b) * HZ + c;
+              double k[3] = {(double)kder(kxy(a, N), N), (double)kder(kxy(b, N), N),
+                             (double)kder(c, N)};
+              gh[idx] = (sh[idx] == g) ? I * k[j] * u[i * M + idx] : 0.0;
+            }
+        oracle_irfft3(gh, gr + (i * 3 + j) * R, n, n, n);
+      }
+    /* (u . grad) u_g back to Fourier space */
+    for (int i = 0; i < 3; i++) {
+      for (long x = 0; x < R; x++) {
+        double s = 0.0;
+        for (int j = 0; j < 3; j++) s += ur[j * R + x] * gr[(i * 3 + j) * R + x];
+        pr[x] = s;
+      }
+      oracle_rfft3(pr, ph + i * M, n, n, n);
+    }
+    /* every receiver's share */
+    for (long a = 0; a < N; a++)
+      for (long b = 0; b < N; b++)
+        for (long c = 0; c < HZ; c++) {
+          long idx = (a * N + b) * HZ + c;
+          int r = sh[idx];
+          if (r < 0) continue;
+          double t = 0.0;
+          for (int f = 0; f < 3; f++) t += creal(conj(u[f * M + idx]) * ph[f * M + idx]);
+          T[(long)r * nshells + g] -= mode_weight(c, N) * t;
+        }
+  }
+  free(sh);
+  free(ur);
+  free(gr);
+  free(pr);
+  free(gh);
+  free(ph);
+  return 0;
+}
+
 /* ----------------------------------------------------- initial fields ---- */
 
 static int ic_from_real(const double *ur, cplx *uhat, int n) {

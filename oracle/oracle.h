@@ -69,6 +69,9 @@ int oracle_diag(const ocplx *uhat, int n, double nu, double *E, double *eps,
 double oracle_transfer(const ocplx *uhat, const ocplx *nhat, int n);
 /* T(K), K = 0..kmax: per-shell sum of w Re(conj(u) . N) (shell nint|k|). */
 int oracle_transfer_spectrum(const ocplx *uhat, const ocplx *nhat, int n, double *T, int kmax);
+/* Shell-to-shell transfer T[r][g] = -<u_r . (u . grad) u_g>, shells
+ * bounds[i] <= nint|k| < bounds[i+1] (nshells + 1 increasing bounds). */
+int oracle_shell_transfer(const ocplx *uhat, int n, int nshells, const int *bounds, double *T);
 
 /* Initial conditions. */
 int oracle_ic_taylor_green(ocplx *uhat, int n);  /* u = (sin x cos y, -cos x sin y, 0) */

@@ -249,3 +249,72 @@ def test_transfer_spectrum_drops_shells_beyond_kmax(oracle_mod):
     N = oracle_mod.ns_rhs(u)
     T = oracle_mod.transfer_spectrum(u, N)
     assert np.array_equal(oracle_mod.transfer_spectrum(u, N, kmax=5), T[:6])
+
+
+def _full_spectrum(uhat, n):
+    # the full complex spectrum of the real field (numpy FFT)
+    ur = np.fft.irfftn(uhat * n**3, s=(n, n, n), axes=(-3, -2, -1))
+    return np.fft.fftn(ur, axes=(-3, -2, -1)) / n**3
+
+
+def test_shell_transfer_matches_triad_sum(oracle_mod):
+    # mode-to-mode form: T[r, g] = sum_{k in r} sum_{p in g} Im[(k . u(k - p)) (conj(u(k)) . u(p))],
+    # summed here over all triads of the full spectrum by brute force
+    n = 16
+    u = _random_uhat(oracle_mod, n, seed=9, k0=2.0)
+    bounds = [0, 1, 2, 3, 4, 6, 9]
+    T = oracle_mod.shell_transfer(u, bounds)
+    U = _full_spectrum(u, n)
+    a = np.arange(n)
+    k1 = np.where(2 * a < n, a, a - n)
+    KX, KY, KZ = np.meshgrid(k1, k1, k1, indexing="ij")
+    K = np.floor(np.sqrt(KX**2 + KY**2 + KZ**2) + 0.5).astype(int)
+    live = np.nonzero(np.max(np.abs(U), axis=0) > 0)
+    modes = np.stack(live, axis=1)
+    kvec = np.stack([KX[live], KY[live], KZ[live]], axis=1)
+    S = len(bounds) - 1
+    shell = np.full(len(modes), -1)
+    for i in range(S):
+        shell[(K[live] >= bounds[i]) & (K[live] < bounds[i + 1])] = i
+    want = np.zeros((S, S))
+    for ik in range(len(modes)):
+        r = shell[ik]
+        if r < 0:
+            continue
+        k = kvec[ik]
+        uk = U[:, modes[ik][0], modes[ik][1], modes[ik][2]]
+        q = (modes[ik][None, :] - modes) % n  # index of k - p for every p
+        uq = U[:, q[:, 0], q[:, 1], q[:, 2]]
+        up = U[:, modes[:, 0], modes[:, 1], modes[:, 2]]
+        s = np.imag((k @ uq) * (np.conj(uk) @ up))
+        for g in range(S):
+            want[r, g] += s[shell == g].sum()
+    scale = np.max(np.abs(want))
+    assert scale > 1e-3
+    assert np.max(np.abs(T - want)) < 1e-12 * scale
+
+
+def test_shell_transfer_antisymmetric_and_sums_to_transfer_spectrum(oracle_mod):
+    # T[r, g] = -T[g, r] (u solenoidal); the givers of a receiver add up to its
+    # transfer T(K) over the shell; the flux through a bound is the transfer
+    # from the shells inside to those outside
+    n = 16
+    u = _random_uhat(oracle_mod, n, seed=10, k0=3.0)
+    kmax = oracle_mod.kmax_shell(n)
+    bounds = [0, 2, 3, 4, 5, 6, 8, 10, 12, kmax + 1]
+    T = oracle_mod.shell_transfer(u, bounds)
+    scale = np.max(np.abs(T))
+    assert scale > 1e-3
+    assert np.max(np.abs(T + T.T)) < 1e-13 * scale
+    TK = oracle_mod.transfer_spectrum(u, oracle_mod.ns_rhs(u))
+    rows = np.array([TK[bounds[i]:bounds[i + 1]].sum() for i in range(len(bounds) - 1)])
+    assert np.max(np.abs(T.sum(axis=1) - rows)) < 1e-13 * scale
+    flux = -np.cumsum(TK)
+    for i in range(1, len(bounds) - 1):
+        assert abs(T[i:, :i].sum() - flux[bounds[i] - 1]) < 1e-13 * scale
+
+
+def test_shell_transfer_rejects_bad_bounds(oracle_mod):
+    u = _random_uhat(oracle_mod, 8, seed=0)
+    with pytest.raises(Exception):
+        oracle_mod.shell_transfer(u, [0, 2, 2, 4])
