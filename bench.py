@@ -524,7 +524,8 @@ def run_case(case: str):
     """One small invocation for profiler captures (no timing, no output line):
     'ns:<n>' = random-phase field + one NS step; 'fft:<nx>,<ny>,<nz>' = two pairs
     ('fft16:' in the split-FP16 mode); 'mlp:<batch>' = two training steps;
-    'sgs:<n>' = two unforced steps with the learned subgrid force."""
+    'sgs:<n>' = two unforced steps with the learned subgrid force;
+    'transfer:<n>' = random-phase field + one energy transfer spectrum."""
     import torch
 
     import paper_1805_07801_gb300 as fk
@@ -544,6 +545,16 @@ def run_case(case: str):
         fk.tarang_ic_random(plan, nr.data_ptr(), u.data_ptr(), K0, E0, st)
         del nr
         fk.tarang_ns_step(plan, u.data_ptr(), fk.make_params(NU, DT), 1, False, st)
+    elif kind == "transfer":
+        n = int(arg)
+        plan = fk.fftk_plan_create(n, n, n)
+        nr = torch.empty((3, n, n, n), dtype=torch.float32, device=dev)
+        for f in range(3):
+            fk.fftk_fill_normal(nr[f].data_ptr(), n**3, SEED, f, st)
+        u = torch.empty((3, n, n, n // 2 + 1, 2), dtype=torch.float32, device=dev)
+        fk.tarang_ic_random(plan, nr.data_ptr(), u.data_ptr(), K0, E0, st)
+        del nr
+        fk.tarang_transfer(plan, u.data_ptr(), None, st)
     elif kind in ("fft", "fft16"):
         nx, ny, nz = (int(v) for v in arg.split(","))
         plan = fk.fftk_plan_create(nx, ny, nz, fk.FFTK_R32_SPLIT16 if kind == "fft16" else fk.FFTK_R32)
@@ -653,6 +664,72 @@ def run_forced(n: int, steps: int):
                                           "max_shell_rel_diff": float(rel.max()),
                                           "shells_compared": int(res.sum()),
                                           "cutoff_shell": int(np.nonzero(res)[0].max())}}), flush=True)
+
+
+def run_transfer(n: int):
+    """Energy transfer spectrum and flux of the 512^3 decaying workload's field
+    after 50 steps: tarang_transfer (right-hand side + FP64 per-shell
+    reduction + host flux) against tarang_ns_rhs alone, CUDA events over 10
+    calls after 3, and the flux it reports; then the shell-to-shell matrix
+    over octave shells (tarang_shell_transfer, 3 calls after 3).  Prints one
+    JSON line."""
+    import numpy as np
+    import torch
+
+    import paper_1805_07801_gb300 as fk
+    from paper_1805_07801_gb300 import build as fkbuild
+
+    fkbuild.build()
+    dev = torch.device("cuda:0")
+    st = torch.cuda.current_stream(dev).cuda_stream
+    plan = fk.fftk_plan_create(n, n, n)
+    nr = torch.empty((3, n, n, n), dtype=torch.float32, device=dev)
+    for f in range(3):
+        fk.fftk_fill_normal(nr[f].data_ptr(), n**3, SEED, f, st)
+    u = torch.empty((3, n, n, n // 2 + 1, 2), dtype=torch.float32, device=dev)
+    fk.tarang_ic_random(plan, nr.data_ptr(), u.data_ptr(), K0, E0, st)
+    del nr
+    fk.tarang_ns_step(plan, u.data_ptr(), fk.make_params(NU, DT), 50, False, st)
+    nh = torch.empty_like(u)
+    prm = fk.make_params(NU, DT)
+
+    def timed(fn, k=10):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize(dev)
+        t = []
+        for _ in range(k):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            b.synchronize()
+            t.append(a.elapsed_time(b))
+        return float(np.median(t))
+
+    ms_transfer = timed(lambda: fk.tarang_transfer(plan, u.data_ptr(), None, st))
+    ms_rhs = timed(lambda: fk.tarang_ns_rhs(plan, u.data_ptr(), nh.data_ptr(), prm, st))
+    tot, T, Pi = fk.tarang_transfer(plan, u.data_ptr(), None, st)
+    kmax = fk.tarang_diag_kmax(plan)
+    bounds = [0] + [1 << i for i in range(int(np.log2(n)))] + [kmax + 1]
+    ms_shell = timed(lambda: fk.tarang_shell_transfer(plan, u.data_ptr(), bounds, st), k=3)
+    S = np.array(fk.tarang_shell_transfer(plan, u.data_ptr(), bounds, st))
+    fk.fftk_plan_destroy(plan)
+    T, Pi = np.array(T), np.array(Pi)
+    kd = (n - 1) // 3
+    kept = (2 * kd + 1) ** 2 * (kd + 1)
+    print(json.dumps({"workload": f"{n}^3 decaying field (k0={K0}, E={E0}, seed {SEED}) after 50 steps "
+                                  f"nu={NU}, dt={DT}",
+                      "ms_transfer": round(ms_transfer, 4), "ms_rhs": round(ms_rhs, 4),
+                      "ms_reduction_and_copy": round(ms_transfer - ms_rhs, 4),
+                      "reduction_bytes": 2 * 3 * 8 * kept,
+                      "sum_T_over_sum_absT": tot / float(np.sum(np.abs(T))),
+                      "flux_max": float(Pi.max()), "flux_argmax": int(Pi.argmax()),
+                      "flux_K_0_to_63": [float(v) for v in Pi[:64]],
+                      "shell_bounds": bounds, "ms_shell_transfer": round(ms_shell, 3),
+                      "shell_antisymmetry": float(np.max(np.abs(S + S.T)) / np.max(np.abs(S))),
+                      "shell_transfer": [[float(v) for v in row] for row in S]}), flush=True)
 
 
 def run_fft_sweep(args):
@@ -769,13 +846,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fft", action="store_true")
     ap.add_argument("--case", default=None,
-                    help="profiler case: ns:<n>, fft:<nx>,<ny>,<nz>, fft16:<nx>,<ny>,<nz>, mlp:<batch> or sgs:<n>")
+                    help="profiler case: ns:<n>, transfer:<n>, fft:<nx>,<ny>,<nz>, fft16:<nx>,<ny>,<nz>, mlp:<batch> "
+                         "or sgs:<n>")
     ap.add_argument("--closure", choices=["full", "small"], default=None,
                     help="run the learned-closure workflow instead of the benchmark")
     ap.add_argument("--closure-out", default="", help="JSON file for the closure workflow's results")
     ap.add_argument("--fft-sweep", action="store_true", help="batched pair sweep 256^3 x 64 ... 2048^3")
     ap.add_argument("--forced", type=int, default=0, metavar="N",
                     help="run N^3 forced turbulence for --steps steps and print its JSON line")
+    ap.add_argument("--transfer", type=int, default=0, metavar="N",
+                    help="time the energy transfer spectrum and flux of an N^3 field")
     args = ap.parse_args()
     if args.case:
         run_case(args.case)
@@ -788,6 +868,9 @@ def main():
         return
     if args.fft_sweep:
         run_fft_sweep(args)
+        return
+    if args.transfer:
+        run_transfer(args.transfer)
         return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

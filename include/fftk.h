@@ -172,6 +172,46 @@ int tarang_diag_kmax(fftk_plan p);
 fftk_status tarang_diag(fftk_plan p, const void *uhat, double nu, double *diag_host,
                         void *cuda_stream);
 
+/* Energy transfer spectrum and flux, the scale-by-scale analysis of the
+ * nonlinear term (Sec. 1 and Sec. 7 of the paper: energy flux Pi(k)).  With
+ * N the right-hand side of tarang_ns_rhs for the state uhat,
+ *   T(K) = sum_{nint|k| = K} w Re(conj(uhat) . N),  w as in tarang_diag,
+ *   Pi(K) = -sum_{K' <= K} T(K')   (energy leaving the sphere of radius K).
+ * prm: NULL for the nonlinear term alone (then sum_K T(K) vanishes up to
+ * rounding); otherwise the forcing and the subgrid model of prm are included
+ * as in tarang_ns_rhs (nu and dt are not used).  out_host: 1 + 2 (kmax + 1)
+ * doubles (kmax of tarang_diag_kmax): sum_K T(K), then T(0..kmax), then
+ * Pi(0..kmax).  The reduction is FP64 in a fixed order (bitwise
+ * reproducible); the right-hand side is the solver's FP32 one.  Uses the
+ * plan's solver workspace (do not overlap with tarang_ns_step on the same
+ * plan); synchronises cuda_stream.  FFTK_ERR_NONFINITE if the sum is not
+ * finite. */
+fftk_status tarang_transfer(fftk_plan p, const void *uhat, const tarang_params *prm, double *out_host,
+                            void *cuda_stream);
+
+/* Shell-to-shell energy transfer (the scale-by-scale analysis the paper
+ * names in Sec. 1 and Sec. 3): shell i holds the kept modes with
+ * bounds[i] <= nint|k| < bounds[i+1], and
+ *   out_host[r * nshells + g] = T(r <- g) = -<u_r . (u . grad) u_g>
+ * (average over the box) is the rate at which shell r receives energy from
+ * shell g through advection by the whole field.  T is antisymmetric, the
+ * givers of a receiver add up to its share of tarang_transfer's T(K), and
+ * the flux through a bound b is the sum of T(r <- g) over r >= b > g.
+ * Evaluated pseudo-spectrally with the plan's transforms: u to real space
+ * once, then per giver shell the gradient of its modes (nine c2r), the
+ * product u_j d_j u_g,i (real space), three r2c and an FP64 reduction over
+ * receivers in a fixed order (bitwise reproducible).  Givers beyond the
+ * dealiased radius are skipped (zero columns).
+ * nshells: 1 .. kmax + 1; bounds: host array of nshells + 1 strictly
+ * increasing integers in [0, kmax + 1] (kmax of tarang_diag_kmax); out_host:
+ * nshells * nshells doubles, row-major by receiver.  Device memory: nine more
+ * real fields (allocated on first use and kept by the plan).  Uses the plan's
+ * solver workspace (do not overlap with tarang_ns_step on the same plan);
+ * synchronises cuda_stream.  INVALID_ARG for bad bounds, NONFINITE if any
+ * entry is not finite. */
+fftk_status tarang_shell_transfer(fftk_plan p, const void *uhat, int nshells, const int *bounds,
+                                  double *out_host, void *cuda_stream);
+
 /* The diagnostics of tarang_diag for callers that cannot allocate device
  * memory.  The paper has no counterpart: this exists for host code that must
  * not call cudaMalloc (for instance a loop that cannot afford cudaMalloc's

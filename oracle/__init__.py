@@ -60,6 +60,9 @@ def lib():
             L.oracle_transfer.restype = c.c_double
             L.oracle_transfer_spectrum.argtypes = [vp, vp, c.c_int, vp, c.c_int]
             L.oracle_shell_transfer.argtypes = [vp, c.c_int, c.c_int, vp, vp]
+            L.oracle_sc1d.argtypes = [vp, vp, c.c_long, c.c_int, c.c_int]
+            L.oracle_transform3.argtypes = [vp, vp, c.c_int, c.c_int, c.c_int, vp]
+            L.oracle_itransform3.argtypes = [vp, vp, c.c_int, c.c_int, c.c_int, vp]
             L.oracle_ic_taylor_green.argtypes = [vp, c.c_int]
             L.oracle_ic_abc.argtypes = [vp, c.c_int]
             L.oracle_ic_random.argtypes = [vp, vp, c.c_int, c.c_double, c.c_double]
@@ -189,6 +192,44 @@ def ns_step(uhat, nu, dt, nsteps=1, force_eps=0.0, force_k2=(1, 4)) -> np.ndarra
     p = _params(nu, dt, force_eps, force_k2)
     _check(lib().oracle_ns_step(_ptr(u), u.shape[1], ctypes.byref(p), nsteps), "ns_step")
     return u
+
+
+FOURIER, SINE, COSINE = 0, 1, 2
+_BASIS = {"F": FOURIER, "S": SINE, "C": COSINE}
+
+
+def _kinds(basis) -> np.ndarray:
+    if isinstance(basis, str):
+        basis = [_BASIS[ch] for ch in basis]
+    return np.ascontiguousarray(basis, dtype=np.int32)
+
+
+def sc1d(x, kind, direction) -> np.ndarray:
+    """Sine (kind 'S') or cosine ('C') transform of a line; direction -1 forward, +1 inverse."""
+    x = np.ascontiguousarray(x, dtype=np.complex128)
+    out = np.empty_like(x)
+    _check(lib().oracle_sc1d(_ptr(x), _ptr(out), x.size, _BASIS[kind], direction), "sc1d")
+    return out
+
+
+def transform3(f, basis) -> np.ndarray:
+    """Forward 3D transform with a basis per axis, e.g. 'SFF' (x sine, y and z Fourier)."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    nx, ny, nz = f.shape
+    k = _kinds(basis)
+    hz = nz // 2 + 1 if k[2] == FOURIER else nz
+    out = np.empty((nx, ny, hz), dtype=np.complex128)
+    _check(lib().oracle_transform3(_ptr(f), _ptr(out), nx, ny, nz, _ptr(k)), "transform3")
+    return out
+
+
+def itransform3(F, nz: int, basis) -> np.ndarray:
+    F = np.ascontiguousarray(F, dtype=np.complex128)
+    nx, ny = F.shape[0], F.shape[1]
+    k = _kinds(basis)
+    out = np.empty((nx, ny, nz), dtype=np.float64)
+    _check(lib().oracle_itransform3(_ptr(F), _ptr(out), nx, ny, nz, _ptr(k)), "itransform3")
+    return out
 
 
 def kmax_shell(n: int) -> int:

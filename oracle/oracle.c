@@ -193,6 +193,172 @@ int oracle_irfft3(const cplx *in, double *out, int nx, int ny, int nz) {
   return 0;
 }
 
+/* ------------------------------------------------ sine / cosine bases ---- */
+/* Sec. 2.1, Eq. (2b, 2c): along a free-slip axis the inverse transform is
+ *   f(s_j) = sum_k fhat_k 2 sin(k s_j)   (sine, k = 1..n, fhat_k stored at k-1)
+ *   f(s_j) = sum_k fhat_k 2 cos(k s_j)   (cosine, k = 0..n-1, stored at k)
+ * on the n points s_j = (j + 1/2) pi / n of [0, pi], and the forward
+ * transform is its inverse:  fhat_k = (c_k / n) sum_j f(s_j) sin(k s_j)
+ * (cos(k s_j) for the cosine), c_k = 1/2 for the cosine k = 0 and the sine
+ * k = n, 1 otherwise.  Both by their definitions, O(n^2), complex-linear. */
+
+/* cos(pi m / (2n)) and sin(pi m / (2n)) for an integer m reduced mod 4n */
+static double cos_q(long m, long n) {
+  m %= 4 * n;
+  if (m < 0) m += 4 * n;
+  return cos(TWO_PI * (double)m / (double)(4 * n));
+}
+static double sin_q(long m, long n) {
+  m %= 4 * n;
+  if (m < 0) m += 4 * n;
+  return sin(TWO_PI * (double)m / (double)(4 * n));
+}
+
+/* table[k][j] = phi_k(s_j) / 2 for the n modes of the basis (k index of storage) */
+static double *sc_table(long n, int kind) {
+  double *t = (double *)malloc(sizeof(double) * (size_t)(n * n));
+  if (!t) return NULL;
+  for (long i = 0; i < n; i++) {
+    long k = (kind == ORACLE_SINE) ? i + 1 : i;
+    for (long j = 0; j < n; j++) {
+      long m = k * (2 * j + 1); /* k s_j = pi m / (2n) */
+      t[i * n + j] = (kind == ORACLE_SINE) ? sin_q(m, n) : cos_q(m, n);
+    }
+  }
+  return t;
+}
+
+static void sc_line(const cplx *in, cplx *out, long n, int kind, int dir, const double *t) {
+  if (dir < 0) {
+    for (long i = 0; i < n; i++) {
+      cplx acc = 0;
+      for (long j = 0; j < n; j++) acc += in[j] * t[i * n + j];
+      int edge = (kind == ORACLE_SINE) ? (i == n - 1) : (i == 0);
+      out[i] = acc * ((edge ? 0.5 : 1.0) / (double)n);
+    }
+  } else {
+    for (long j = 0; j < n; j++) {
+      cplx acc = 0;
+      for (long i = 0; i < n; i++) acc += in[i] * t[i * n + j];
+      out[j] = 2.0 * acc;
+    }
+  }
+}
+
+int oracle_sc1d(const cplx *in, cplx *out, long n, int kind, int dir) {
+  if (n < 1 || (kind != ORACLE_SINE && kind != ORACLE_COSINE) || (dir != 1 && dir != -1)) return -1;
+  double *t = sc_table(n, kind);
+  if (!t) return -2;
+  sc_line(in, out, n, kind, dir, t);
+  free(t);
+  return 0;
+}
+
+/* One axis of a 3D array a[n0][n1][n2] (complex): every line along `axis`
+ * goes through the Fourier transform (kind ORACLE_FOURIER, sign = dir, factor
+ * 1/n when forward) or the sine/cosine transform above. */
+static int axis_pass(cplx *a, const long dims[3], int axis, int kind, int dir) {
+  const long n = dims[axis];
+  long stride = 1;
+  for (int d = axis + 1; d < 3; d++) stride *= dims[d];
+  const long nlines = dims[0] * dims[1] * dims[2] / n;
+  double *t = NULL;
+  cplx *tw = NULL;
+  if (kind == ORACLE_FOURIER) {
+    if (!is_pow2(n)) return -1;
+    tw = make_twiddles(n, dir);
+  } else {
+    t = sc_table(n, kind);
+  }
+  if (!tw && !t) return -2;
+#pragma omp parallel
+  {
+    cplx *lin = (cplx *)malloc(sizeof(cplx) * (size_t)n);
+    cplx *lout = (cplx *)malloc(sizeof(cplx) * (size_t)n);
+#pragma omp for schedule(static)
+    for (long l = 0; l < nlines; l++) {
+      long outer = l / stride, inner = l % stride;
+      cplx *base = a + outer * n * stride + inner;
+      for (long i = 0; i < n; i++) lin[i] = base[i * stride];
+      if (kind == ORACLE_FOURIER) {
+        fft_rec(lin, 1, lout, n, tw, 1);
+        if (dir < 0)
+          for (long i = 0; i < n; i++) lout[i] /= (double)n;
+      } else {
+        sc_line(lin, lout, n, kind, dir, t);
+      }
+      for (long i = 0; i < n; i++) base[i * stride] = lout[i];
+    }
+    free(lin);
+    free(lout);
+  }
+  free(t);
+  free(tw);
+  return 0;
+}
+
+static int basis_ok(const int kind[3]) {
+  for (int d = 0; d < 3; d++)
+    if (kind[d] != ORACLE_FOURIER && kind[d] != ORACLE_SINE && kind[d] != ORACLE_COSINE) return 0;
+  /* Fourier axes are the trailing ones: FFF, SFF, SSF, SSS (Sec. 2.1) */
+  if (kind[0] == ORACLE_FOURIER && (kind[1] != ORACLE_FOURIER || kind[2] != ORACLE_FOURIER)) return 0;
+  if (kind[1] == ORACLE_FOURIER && kind[2] != ORACLE_FOURIER) return 0;
+  return 1;
+}
+
+/* Forward 3D transform in the paper's pass order (z, then y, then x) with a
+ * basis per axis.  in: real [nx][ny][nz].  out: complex [nx][ny][hz] with
+ * hz = nz/2 + 1 when z is Fourier (real-to-complex half spectrum), else
+ * hz = nz (the coefficients are real; imaginary parts 0). */
+int oracle_transform3(const double *in, cplx *out, int nx, int ny, int nz, const int kind[3]) {
+  if (!basis_ok(kind) || nx < 1 || ny < 1 || nz < 2) return -1;
+  const long NX = nx, NY = ny, NZ = nz;
+  const int zf = kind[2] == ORACLE_FOURIER;
+  const long HZ = zf ? NZ / 2 + 1 : NZ;
+  cplx *full = (cplx *)malloc(sizeof(cplx) * (size_t)(NX * NY * NZ));
+  if (!full) return -2;
+  for (long i = 0; i < NX * NY * NZ; i++) full[i] = in[i];
+  const long dfull[3] = {NX, NY, NZ};
+  int rc = axis_pass(full, dfull, 2, kind[2], -1);
+  const long dh[3] = {NX, NY, HZ};
+  for (long l = 0; l < NX * NY; l++)
+    for (long c = 0; c < HZ; c++) out[l * HZ + c] = full[l * NZ + c];
+  free(full);
+  if (!rc && NY > 1) rc = axis_pass(out, dh, 1, kind[1], -1);
+  if (!rc && NX > 1) rc = axis_pass(out, dh, 0, kind[0], -1);
+  return rc;
+}
+
+/* Inverse in the reverse order (x, y, then z).  A Fourier z axis is extended
+ * by conjugation per line and the real part kept (as oracle_irfft3). */
+int oracle_itransform3(const cplx *in, double *out, int nx, int ny, int nz, const int kind[3]) {
+  if (!basis_ok(kind) || nx < 1 || ny < 1 || nz < 2) return -1;
+  const long NX = nx, NY = ny, NZ = nz;
+  const int zf = kind[2] == ORACLE_FOURIER;
+  const long HZ = zf ? NZ / 2 + 1 : NZ;
+  cplx *w = (cplx *)malloc(sizeof(cplx) * (size_t)(NX * NY * HZ));
+  cplx *full = (cplx *)malloc(sizeof(cplx) * (size_t)(NX * NY * NZ));
+  if (!w || !full) return -2;
+  memcpy(w, in, sizeof(cplx) * (size_t)(NX * NY * HZ));
+  const long dh[3] = {NX, NY, HZ};
+  int rc = 0;
+  if (NX > 1) rc = axis_pass(w, dh, 0, kind[0], +1);
+  if (!rc && NY > 1) rc = axis_pass(w, dh, 1, kind[1], +1);
+  for (long l = 0; l < NX * NY; l++)
+    for (long c = 0; c < NZ; c++) {
+      if (zf)
+        full[l * NZ + c] = (c < HZ) ? w[l * HZ + c] : conj(w[l * HZ + (NZ - c)]);
+      else
+        full[l * NZ + c] = w[l * NZ + c];
+    }
+  const long dfull[3] = {NX, NY, NZ};
+  if (!rc) rc = axis_pass(full, dfull, 2, kind[2], +1);
+  for (long i = 0; i < NX * NY * NZ; i++) out[i] = creal(full[i]);
+  free(w);
+  free(full);
+  return rc;
+}
+
 /* exp(sign 2 pi i m / n) for m reduced mod n. */
 static cplx phase(long m, long n, int sign) {
   m %= n;
@@ -487,7 +653,7 @@ double oracle_transfer(const cplx *u, const cplx *nh, int n) {
 }
 
 /* Energy transfer spectrum of the nonlinear term (the scale-by-scale
- * analysis of Sec. 1 / Sec. 7): T(K) = sum over the shell K = nint|k| of
+ * analysis of Sec. 1 and Sec. 7): T(K) = sum over the shell K = nint|k| of
  * w Re(conj(u) . N), w = 1 on k_z = 0 and k_z = n/2, else 2.  The flux
  * through K is Pi(K) = -sum_{K' <= K} T(K'). */
 int oracle_transfer_spectrum(const cplx *u, const cplx *nh, int n, double *T, int kmax) {
@@ -506,7 +672,7 @@ int oracle_transfer_spectrum(const cplx *u, const cplx *nh, int n, double *T, in
   return 0;
 }
 
-/* Shell-to-shell energy transfer (Tarang's scale-by-scale analysis, Sec. 1):
+/* Shell-to-shell energy transfer (Tarang's scale-by-scale analysis, Sec. 1, Sec. 3):
  * shell i holds the modes with bounds[i] <= nint|k| < bounds[i+1], and
  *   T[r * nshells + g] = -<u_r . (u . grad) u_g>
  * is the rate at which shell r (receiver) gains energy from shell g (giver)

@@ -30,6 +30,25 @@ int oracle_threads(void);
 int oracle_fft1d(const ocplx *in, ocplx *out, long n, int sign);   /* recursive radix-2, n = 2^m */
 int oracle_dft1d(const ocplx *in, ocplx *out, long n, int sign);   /* O(n^2) definition, any n */
 
+/* Sine and cosine bases (Sec. 2.1, Eq. (2b, 2c)) on the n points
+ * s_j = (j + 1/2) pi / n of [0, pi]:
+ *   inverse (dir +1)  f(s_j) = sum_k fhat_k 2 sin(k s_j), k = 1..n (stored at k-1),
+ *                     or 2 cos(k s_j), k = 0..n-1 (stored at k);
+ *   forward (dir -1)  its inverse, fhat_k = (c_k/n) sum_j f(s_j) sin(k s_j) (cos),
+ *                     c_k = 1/2 for the cosine k = 0 and the sine k = n, else 1.
+ * By the definitions, O(n^2), complex-linear, any n >= 1. */
+#define ORACLE_FOURIER 0
+#define ORACLE_SINE 1
+#define ORACLE_COSINE 2
+int oracle_sc1d(const ocplx *in, ocplx *out, long n, int kind, int dir);
+/* 3D transforms with a basis per axis (kind[3] for x, y, z; Fourier axes
+ * trailing: FFF, SFF, SSF, SSS), passes in the paper's order (forward z, y,
+ * x; inverse x, y, z).  Fourier axes as in oracle_rfft3 (1/n per forward
+ * axis).  Spectrum: complex [nx][ny][hz], hz = nz/2+1 for a Fourier z axis
+ * (half spectrum) else nz (real coefficients, imaginary parts 0). */
+int oracle_transform3(const double *in, ocplx *out, int nx, int ny, int nz, const int kind[3]);
+int oracle_itransform3(const ocplx *in, double *out, int nx, int ny, int nz, const int kind[3]);
+
 /* 3D transforms in the paper's pass order (Sec. 3): forward z r2c, y c2c, x c2c
  * then the 1/N^3 factor; inverse x c2c, y c2c, z c2r. */
 int oracle_rfft3(const double *in, ocplx *out, int nx, int ny, int nz);

@@ -85,6 +85,8 @@ def lib() -> ctypes.CDLL:
             "tarang_diag_kmax": ([vp], i),
             "tarang_diag": ([vp, vp, d, vp, vp], i),
             "tarang_diag_noalloc": ([i, vp, d, vp, vp], i),
+            "tarang_transfer": ([vp, vp, c.POINTER(tarang_params), vp, vp], i),
+            "tarang_shell_transfer": ([vp, vp, i, vp, vp, vp], i),
             "tarang_ic_random": ([vp, vp, vp, d, d, vp], i),
             "tarang_dealias_project": ([vp, vp, vp], i),
             "fftk_fill_normal": ([vp, ll, i, i, vp], i),
@@ -193,6 +195,28 @@ def tarang_ns_step(plan: int, uhat_ptr, params: tarang_params, nsteps: int = 1, 
         return None
     vals = list(buf)
     return vals[0], vals[1], vals[2:]
+
+
+def tarang_transfer(plan: int, uhat_ptr, params: tarang_params = None, stream=0):
+    """(sum_K T(K), T(K) list, Pi(K) list) of a velocity state; synchronises."""
+    nb = tarang_diag_kmax(plan) + 1
+    buf = (ctypes.c_double * (1 + 2 * nb))()
+    _check(lib().tarang_transfer(_vp(plan), _vp(uhat_ptr), ctypes.byref(params) if params is not None else None,
+                                 ctypes.cast(buf, ctypes.c_void_p), _vp(stream)), "tarang_transfer")
+    vals = list(buf)
+    return vals[0], vals[1:1 + nb], vals[1 + nb:]
+
+
+def tarang_shell_transfer(plan: int, uhat_ptr, bounds, stream=0):
+    """Shell-to-shell transfer matrix T[r][g] (list of rows) for the shells
+    bounds[i] <= nint|k| < bounds[i+1]; synchronises."""
+    S = len(bounds) - 1
+    b = (ctypes.c_int * len(bounds))(*[int(v) for v in bounds])
+    buf = (ctypes.c_double * max(S * S, 1))()
+    _check(lib().tarang_shell_transfer(_vp(plan), _vp(uhat_ptr), S, ctypes.cast(b, ctypes.c_void_p),
+                                       ctypes.cast(buf, ctypes.c_void_p), _vp(stream)), "tarang_shell_transfer")
+    vals = list(buf)
+    return [vals[r * S:(r + 1) * S] for r in range(S)]
 
 
 def tarang_diag(plan: int, uhat_ptr, nu: float, stream=0):
