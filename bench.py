@@ -525,7 +525,8 @@ def run_case(case: str):
     'ns:<n>' = random-phase field + one NS step; 'fft:<nx>,<ny>,<nz>' = two pairs
     ('fft16:' in the split-FP16 mode); 'mlp:<batch>' = two training steps;
     'sgs:<n>' = two unforced steps with the learned subgrid force;
-    'transfer:<n>' = random-phase field + one energy transfer spectrum."""
+    'transfer:<n>' = random-phase field + one energy transfer spectrum;
+    'bases:<nx>,<ny>,<nz>' = one SFF and one CCS forward + inverse pair."""
     import torch
 
     import paper_1805_07801_gb300 as fk
@@ -545,6 +546,16 @@ def run_case(case: str):
         fk.tarang_ic_random(plan, nr.data_ptr(), u.data_ptr(), K0, E0, st)
         del nr
         fk.tarang_ns_step(plan, u.data_ptr(), fk.make_params(NU, DT), 1, False, st)
+    elif kind == "bases":
+        nx, ny, nz = (int(v) for v in arg.split(","))
+        plan = fk.fftk_plan_create(nx, ny, nz)
+        x = torch.empty((nx, ny, nz), dtype=torch.float32, device=dev)
+        fk.fftk_fill_normal(x.data_ptr(), x.numel(), SEED, 0, st)
+        F = torch.empty((nx, ny, nz // 2 + 1, 2), dtype=torch.float32, device=dev)
+        y = torch.empty_like(x)
+        for basis in ("SFF", "CCS"):
+            fk.fftk_forward(plan, basis, x.data_ptr(), F.data_ptr(), 1, st)
+            fk.fftk_inverse(plan, basis, F.data_ptr(), y.data_ptr(), 1, st)
     elif kind == "transfer":
         n = int(arg)
         plan = fk.fftk_plan_create(n, n, n)
@@ -732,6 +743,104 @@ def run_transfer(n: int):
                       "shell_transfer": [[float(v) for v in row] for row in S]}), flush=True)
 
 
+def run_schemes(n: int, steps: int):
+    """The n^3 decaying workload (random-phase field, k0 = 4, E = 0.5, seed 0,
+    nu = 1e-3, dt = 5e-4) stepped with RK2 and with the paper's RK4 (four
+    fused right-hand sides per step), CUDA events over `steps` steps after 3.
+    Prints one JSON line with steps/s, the per-step bytes of each scheme and
+    the energies reached."""
+    import torch
+
+    import paper_1805_07801_gb300 as fk
+    from paper_1805_07801_gb300 import build as fkbuild
+
+    fkbuild.build()
+    dev = torch.device("cuda:0")
+    st = torch.cuda.current_stream(dev).cuda_stream
+    hbm, peak_kind = peaks()
+    plan = fk.fftk_plan_create(n, n, n)
+    nr = torch.empty((3, n, n, n), dtype=torch.float32, device=dev)
+    for f in range(3):
+        fk.fftk_fill_normal(nr[f].data_ptr(), n**3, SEED, f, st)
+    u0 = torch.empty((3, n, n, n // 2 + 1, 2), dtype=torch.float32, device=dev)
+    fk.tarang_ic_random(plan, nr.data_ptr(), u0.data_ptr(), K0, E0, st)
+    del nr
+    pruned, _ = ns_step_bytes(n)
+    out = {}
+    for name, scheme in (("rk2", fk.TARANG_RK2), ("rk4", fk.TARANG_RK4)):
+        u = u0.clone()
+        prm = fk.make_params(NU, DT, scheme=scheme)
+        fk.tarang_ns_step(plan, u.data_ptr(), prm, 3, False, st)
+        torch.cuda.synchronize(dev)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        fk.tarang_ns_step(plan, u.data_ptr(), prm, steps, False, st)
+        b.record()
+        b.synchronize()
+        ms = a.elapsed_time(b) / steps
+        E, eps, _ = fk.tarang_diag(plan, u.data_ptr(), NU, st)
+        # RK4: four right-hand sides of about half an RK2 step's bytes each, plus the accumulator
+        step_bytes = pruned if scheme == fk.TARANG_RK2 else 2 * pruned
+        out[name] = {"steps_per_s": round(1e3 / ms, 3), "ms_per_step": round(ms, 4),
+                     "approx_step_bytes": step_bytes, "frac": round(step_bytes / (ms * 1e-3) / 1e9 / hbm, 4),
+                     "E": E, "eps": eps, "steps": steps + 3}
+    fk.fftk_sync(plan, st)
+    fk.fftk_plan_destroy(plan)
+    print(json.dumps({"workload": f"{n}^3 decaying turbulence, nu={NU}, dt={DT}, seed {SEED}",
+                      "peak_GBps": hbm, "peak_kind": peak_kind, **out}), flush=True)
+
+
+def run_bases(n: int):
+    """Forward + inverse pairs of an n^3 normal(0,1) field (seed 0) in the
+    paper's bases FFF, SFF, SSF and SSS (sine on x, y and z in turn; cosine
+    on the other S axes: {S,F,F}, {S,C,F}, {C,C,S}), CUDA events over 20
+    pairs after 3, against the pair roofline: every pass reads and writes its
+    field once (8R + 80M bytes with a Fourier z axis, 48R for SSS).  Prints
+    one JSON line."""
+    import torch
+
+    import paper_1805_07801_gb300 as fk
+    from paper_1805_07801_gb300 import build as fkbuild
+
+    fkbuild.build()
+    dev = torch.device("cuda:0")
+    st_obj = torch.cuda.Stream(dev)
+    st = st_obj.cuda_stream
+    hbm, peak_kind = peaks()
+    R, M = n**3, n * n * (n // 2 + 1)
+    plan = fk.fftk_plan_create(n, n, n)
+    x = torch.empty((n, n, n), dtype=torch.float32, device=dev)
+    with torch.cuda.stream(st_obj):
+        fk.fftk_fill_normal(x.data_ptr(), R, SEED, 0, st)
+        spec = torch.empty((n, n, n // 2 + 1, 2), dtype=torch.float32, device=dev)
+        y = torch.empty_like(x)
+    rows = []
+    for name, basis in (("FFF", "FFF"), ("SFF", "SFF"), ("SSF", "SCF"), ("SSS", "CCS")):
+        pair = 48 * R if basis[2] != "F" else 8 * R + 80 * M
+        for _ in range(3):
+            fk.fftk_forward(plan, basis, x.data_ptr(), spec.data_ptr(), 1, st)
+            fk.fftk_inverse(plan, basis, spec.data_ptr(), y.data_ptr(), 1, st)
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        kp = 20
+        e0.record(st_obj)
+        for _ in range(kp):
+            fk.fftk_forward(plan, basis, x.data_ptr(), spec.data_ptr(), 1, st)
+            fk.fftk_inverse(plan, basis, spec.data_ptr(), y.data_ptr(), 1, st)
+        e1.record(st_obj)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / kp
+        err = float(torch.linalg.vector_norm((y - x).double()) / torch.linalg.vector_norm(x.double()))
+        rows.append({"basis": name, "axes": basis, "pairs_s": round(1e3 / ms, 3), "ms_per_pair": round(ms, 4),
+                     "pair_bytes": pair, "frac_pair": round(pair / (ms * 1e-3) / 1e9 / hbm, 4),
+                     "round_trip_rel_l2": err})
+    fk.fftk_plan_destroy(plan)
+    print(json.dumps({"workload": f"{n}^3 forward + inverse pairs of normal(0,1), seed {SEED}, mixed bases",
+                      "peak_GBps": hbm, "peak_kind": peak_kind, "bases": rows}), flush=True)
+
+
 def run_fft_sweep(args):
     """Batched R2C + C2R pairs with B * N^3 = 2^30 reals: 256^3 x 64, 512^3 x 8,
     1024^3 and 2048^3, each in FP32 and in split-FP16.  Pairs/s (CUDA events,
@@ -846,7 +955,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fft", action="store_true")
     ap.add_argument("--case", default=None,
-                    help="profiler case: ns:<n>, transfer:<n>, fft:<nx>,<ny>,<nz>, fft16:<nx>,<ny>,<nz>, mlp:<batch> "
+                    help="profiler case: ns:<n>, transfer:<n>, bases:<nx>,<ny>,<nz>, fft:<nx>,<ny>,<nz>, "
+                         "fft16:<nx>,<ny>,<nz>, mlp:<batch> "
                          "or sgs:<n>")
     ap.add_argument("--closure", choices=["full", "small"], default=None,
                     help="run the learned-closure workflow instead of the benchmark")
@@ -856,6 +966,10 @@ def main():
                     help="run N^3 forced turbulence for --steps steps and print its JSON line")
     ap.add_argument("--transfer", type=int, default=0, metavar="N",
                     help="time the energy transfer spectrum and flux of an N^3 field")
+    ap.add_argument("--schemes", type=int, default=0, metavar="N",
+                    help="time N^3 NS steps with RK2 and with RK4 for --steps steps")
+    ap.add_argument("--bases", type=int, default=0, metavar="N",
+                    help="time N^3 transform pairs in the FFF, SFF, SSF and SSS bases")
     args = ap.parse_args()
     if args.case:
         run_case(args.case)
@@ -871,6 +985,12 @@ def main():
         return
     if args.transfer:
         run_transfer(args.transfer)
+        return
+    if args.bases:
+        run_bases(args.bases)
+        return
+    if args.schemes:
+        run_schemes(args.schemes, args.steps)
         return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

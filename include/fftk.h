@@ -102,6 +102,35 @@ fftk_status fftk_r2c(fftk_plan p, const float *in, void *out, int batch, void *c
  * Hermitian-consistent spectra (those produced by fftk_r2c).  Out-of-place. */
 fftk_status fftk_c2r(fftk_plan p, const void *in, float *out, int batch, void *cuda_stream);
 
+/* Bases per axis (paper Sec. 2.1, Eq. (2a-2c)): FOURIER exp(i k s) on a
+ * 2 pi-periodic axis; SINE 2 sin(k s) (k = 1..n, coefficient k stored at
+ * k - 1) and COSINE 2 cos(k s) (k = 0..n-1, stored at k) on the n points
+ * s_j = (j + 1/2) pi / n of [0, pi] (free-slip walls at 0 and pi).  The
+ * inverse is the sum over the basis with no factor; the forward is its exact
+ * inverse (1/n per axis; the sine k = n and cosine k = 0 coefficients take
+ * 1/(2n)). */
+typedef enum { FFTK_FOURIER = 0, FFTK_SINE = 1, FFTK_COSINE = 2 } fftk_basis;
+
+/* Forward 3D transform with a basis per axis, basis[3] = {x, y, z}, Fourier
+ * axes trailing: FFF, SFF, SSF or SSS in the paper's naming, where each S
+ * axis is FFTK_SINE or FFTK_COSINE (e.g. the all-free-slip u_z is
+ * {COSINE, COSINE, SINE}).  Passes in the paper's order: z, then y, then x.
+ * in: float [batch][nx][ny][nz].  out: float2 [batch][nx][ny][nz/2+1] when z
+ * is Fourier (half spectrum), else float [batch][nx][ny][nz] (all-real
+ * coefficients).  Sine/cosine passes are FP32 in both plan dtypes (one
+ * complex FFT of the line's length with pre- and post-twiddles, Makhoul's
+ * method); Fourier passes follow the plan dtype.  An S axis needs n >= 2.
+ * Out-of-place; overlap, a Fourier axis before an S axis or an unknown
+ * basis is INVALID_ARG.  fftk_forward(p, {F,F,F}, ...) equals fftk_r2c. */
+fftk_status fftk_forward(fftk_plan p, const int *basis, const float *in, void *out, int batch,
+                         void *cuda_stream);
+
+/* Inverse of fftk_forward: x, then y, then z; `in` is not modified (with a
+ * Fourier z axis the x and y passes run in the plan's c2r workspace, else in
+ * `out`).  A Fourier z axis is inverted line-wise as in fftk_c2r. */
+fftk_status fftk_inverse(fftk_plan p, const int *basis, const void *in, float *out, int batch,
+                         void *cuda_stream);
+
 /* ---------------------------------------------------------------- Tarang --
  * Pseudo-spectral incompressible Navier-Stokes on a 2 pi-periodic cubic grid
  * (plan with nx = ny = nz = n, n >= 8), paper Sec. 2.2, Eqs. (7)-(8).
@@ -140,7 +169,11 @@ typedef struct {
    * subgrid force P[-i k_j tau_hat_ij] of the model's stress, evaluated per
    * grid point from the current state's gradient (fused inference). */
   const tarang_sgs_model *sgs_model;
+  /* tarang_ns_step's time stepper: TARANG_RK2 (0) or TARANG_RK4 (1). */
+  int scheme;
 } tarang_params;
+
+enum { TARANG_RK2 = 0, TARANG_RK4 = 1 };
 
 /* Nonlinear right-hand side without the viscous term:
  *   nhat = P[ F(u x omega) ] on the 2/3 set, 0 elsewhere, + forcing,
@@ -153,8 +186,15 @@ fftk_status tarang_ns_rhs(fftk_plan p, const void *uhat, void *nhat, const taran
                           void *cuda_stream);
 
 /* nsteps steps of RK2 (Heun) with the viscous integrating factor
- * E = exp(-nu |k|^2 dt):
- *   u1 = E (u + dt N(u)),   u <- 1/2 E u + 1/2 (u1 + dt N(u1)).
+ * E = exp(-nu |k|^2 dt) (scheme TARANG_RK2):
+ *   u1 = E (u + dt N(u)),   u <- 1/2 E u + 1/2 (u1 + dt N(u1)),
+ * or of the paper's fourth-order Runge-Kutta scheme (Sec. 2.2, 36
+ * transforms per step as counted in Sec. 6) with the same factor in
+ * Lawson's form (scheme TARANG_RK4), H = exp(-nu |k|^2 dt/2):
+ *   N1 = N(u), ua = H (u + dt/2 N1), N2 = N(ua), ub = H u + dt/2 N2,
+ *   N3 = N(ub), uc = E u + dt H N3, N4 = N(uc),
+ *   u <- E u + dt/6 (E N1 + 2 H N2 + 2 H N3 + N4);
+ * RK4 keeps three more fields of device memory (the accumulator).
  * uhat is updated in place.  diag_host: NULL, or room for 2 + kmax + 1
  * doubles, kmax = nint(sqrt(3) n / 2) + 1 (see tarang_diag_kmax); when given,
  * the call synchronises and writes E, eps and E(K) of the final state, and

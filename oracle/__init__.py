@@ -55,6 +55,7 @@ def lib():
             L.oracle_ns_rhs.argtypes = [vp, vp, c.c_int, vp]
             L.oracle_ns_rhs_divergence.argtypes = [vp, vp, c.c_int]
             L.oracle_ns_step.argtypes = [vp, c.c_int, vp, c.c_int]
+            L.oracle_ns_step_rk4.argtypes = [vp, c.c_int, vp, c.c_int]
             L.oracle_diag.argtypes = [vp, c.c_int, c.c_double, dp, dp, vp, c.c_int]
             L.oracle_transfer.argtypes = [vp, vp, c.c_int]
             L.oracle_transfer.restype = c.c_double
@@ -63,6 +64,8 @@ def lib():
             L.oracle_sc1d.argtypes = [vp, vp, c.c_long, c.c_int, c.c_int]
             L.oracle_transform3.argtypes = [vp, vp, c.c_int, c.c_int, c.c_int, vp]
             L.oracle_itransform3.argtypes = [vp, vp, c.c_int, c.c_int, c.c_int, vp]
+            L.oracle_transform3_coeff_f32.argtypes = [vp, c.c_int, c.c_int, c.c_int, vp, c.c_int, c.c_int,
+                                                      c.c_int, vp]
             L.oracle_ic_taylor_green.argtypes = [vp, c.c_int]
             L.oracle_ic_abc.argtypes = [vp, c.c_int]
             L.oracle_ic_random.argtypes = [vp, vp, c.c_int, c.c_double, c.c_double]
@@ -230,6 +233,24 @@ def itransform3(F, nz: int, basis) -> np.ndarray:
     out = np.empty((nx, ny, nz), dtype=np.float64)
     _check(lib().oracle_itransform3(_ptr(F), _ptr(out), nx, ny, nz, _ptr(k)), "itransform3")
     return out
+
+
+def transform3_coeff(f32: np.ndarray, basis, a: int, b: int, c: int) -> complex:
+    """Coefficient (a, b, c) of transform3 of an FP32 field, by its definition."""
+    f32 = np.ascontiguousarray(f32, dtype=np.float32)
+    nx, ny, nz = f32.shape
+    k = _kinds(basis)
+    out = np.zeros(2, dtype=np.float64)
+    _check(lib().oracle_transform3_coeff_f32(_ptr(f32), nx, ny, nz, _ptr(k), a, b, c, _ptr(out)),
+           "transform3_coeff")
+    return complex(out[0], out[1])
+
+
+def ns_step_rk4(uhat, nu, dt, nsteps=1, force_eps=0.0, force_k2=(1, 4)) -> np.ndarray:
+    u = np.array(uhat, dtype=np.complex128, order="C", copy=True)
+    p = _params(nu, dt, force_eps, force_k2)
+    _check(lib().oracle_ns_step_rk4(_ptr(u), u.shape[1], ctypes.byref(p), nsteps), "ns_step_rk4")
+    return u
 
 
 def kmax_shell(n: int) -> int:

@@ -359,6 +359,53 @@ int oracle_itransform3(const cplx *in, double *out, int nx, int ny, int nz, cons
   return rc;
 }
 
+/* One coefficient of oracle_transform3 straight from its definition, for
+ * FP32 input too large for the full transform: the sum over all points of
+ * f times the product of the three axis factors (exp(-i k s)/n on a Fourier
+ * axis, c_k sin(k s_j)/n or c_k cos(k s_j)/n on a sine/cosine axis). */
+static cplx axis_factor(int kind, long idx, long j, long n) {
+  if (kind == ORACLE_FOURIER) {
+    long m = (idx * j) % n;
+    double ang = TWO_PI * (double)m / (double)n;
+    return (cos(ang) - sin(ang) * I) / (double)n;
+  }
+  long k = (kind == ORACLE_SINE) ? idx + 1 : idx;
+  int edge = (kind == ORACLE_SINE) ? (k == n) : (k == 0);
+  double c = (edge ? 0.5 : 1.0) / (double)n;
+  long m = k * (2 * j + 1);
+  return c * ((kind == ORACLE_SINE) ? sin_q(m, n) : cos_q(m, n));
+}
+
+int oracle_transform3_coeff_f32(const float *in, int nx, int ny, int nz, const int kind[3], int a, int b,
+                                int c, double *out) {
+  if (!basis_ok(kind)) return -1;
+  const long NX = nx, NY = ny, NZ = nz;
+  cplx *fy = (cplx *)malloc(sizeof(cplx) * (size_t)NY);
+  cplx *fz = (cplx *)malloc(sizeof(cplx) * (size_t)NZ);
+  if (!fy || !fz) return -2;
+  for (long j = 0; j < NY; j++) fy[j] = axis_factor(kind[1], b, j, NY);
+  for (long l = 0; l < NZ; l++) fz[l] = axis_factor(kind[2], c, l, NZ);
+  double re = 0.0, im = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : re, im)
+  for (long i = 0; i < NX; i++) {
+    cplx row = 0;
+    for (long j = 0; j < NY; j++) {
+      cplx acc = 0;
+      const float *line = in + (i * NY + j) * NZ;
+      for (long l = 0; l < NZ; l++) acc += (double)line[l] * fz[l];
+      row += acc * fy[j];
+    }
+    cplx t = row * axis_factor(kind[0], a, i, NX);
+    re += creal(t);
+    im += cimag(t);
+  }
+  free(fy);
+  free(fz);
+  out[0] = re;
+  out[1] = im;
+  return 0;
+}
+
 /* exp(sign 2 pi i m / n) for m reduced mod n. */
 static cplx phase(long m, long n, int sign) {
   m %= n;
@@ -610,6 +657,73 @@ int oracle_ns_step(cplx *uhat, int n, const oracle_ns_params *p, int nsteps) {
   free(u1);
   free(nh);
   free(E);
+  return 0;
+}
+
+/* The paper's Runge-Kutta scheme of fourth order (Sec. 2.2; RK4, 36
+ * transforms per step in Sec. 6) with the viscous integrating factor
+ * (Lawson's form): with E = exp(-nu k^2 dt), H = exp(-nu k^2 dt/2),
+ *   N1 = N(u),                 ua = H (u + dt/2 N1),
+ *   N2 = N(ua),                ub = H u + dt/2 N2,
+ *   N3 = N(ub),                uc = E u + dt H N3,
+ *   N4 = N(uc),
+ *   u <- E u + dt/6 (E N1 + 2 H N2 + 2 H N3 + N4). */
+int oracle_ns_step_rk4(cplx *uhat, int n, const oracle_ns_params *p, int nsteps) {
+  if (!is_pow2(n) || n < 2 || !p) return -1;
+  const long N = n, HZ = n / 2 + 1, M = N * N * HZ;
+  cplx *us = (cplx *)malloc(sizeof(cplx) * 3 * (size_t)M);
+  cplx *nh = (cplx *)malloc(sizeof(cplx) * 3 * (size_t)M);
+  cplx *acc = (cplx *)malloc(sizeof(cplx) * 3 * (size_t)M);
+  double *E = (double *)malloc(sizeof(double) * (size_t)M);
+  double *H = (double *)malloc(sizeof(double) * (size_t)M);
+  if (!us || !nh || !acc || !E || !H) return -2;
+  for (long a = 0; a < N; a++)
+    for (long b = 0; b < N; b++)
+      for (long c = 0; c < HZ; c++) {
+        double kx = (double)kxy(a, N), ky = (double)kxy(b, N), kz = (double)c;
+        double k2 = kx * kx + ky * ky + kz * kz;
+        E[(a * N + b) * HZ + c] = exp(-p->nu * k2 * p->dt);
+        H[(a * N + b) * HZ + c] = exp(-p->nu * k2 * p->dt * 0.5);
+      }
+  const double dt = p->dt;
+  for (int s = 0; s < nsteps; s++) {
+    int rc = oracle_ns_rhs(uhat, nh, n, p); /* N1 */
+    if (rc) return rc;
+    for (int f = 0; f < 3; f++)
+      for (long m = 0; m < M; m++) {
+        long i = f * M + m;
+        acc[i] = E[m] * uhat[i] + dt / 6.0 * E[m] * nh[i];
+        us[i] = H[m] * (uhat[i] + 0.5 * dt * nh[i]);
+      }
+    oracle_dealias(us, 3, n);
+    rc = oracle_ns_rhs(us, nh, n, p); /* N2 */
+    if (rc) return rc;
+    for (int f = 0; f < 3; f++)
+      for (long m = 0; m < M; m++) {
+        long i = f * M + m;
+        acc[i] += dt / 3.0 * H[m] * nh[i];
+        us[i] = H[m] * uhat[i] + 0.5 * dt * nh[i];
+      }
+    oracle_dealias(us, 3, n);
+    rc = oracle_ns_rhs(us, nh, n, p); /* N3 */
+    if (rc) return rc;
+    for (int f = 0; f < 3; f++)
+      for (long m = 0; m < M; m++) {
+        long i = f * M + m;
+        acc[i] += dt / 3.0 * H[m] * nh[i];
+        us[i] = E[m] * uhat[i] + dt * H[m] * nh[i];
+      }
+    oracle_dealias(us, 3, n);
+    rc = oracle_ns_rhs(us, nh, n, p); /* N4 */
+    if (rc) return rc;
+    for (long i = 0; i < 3 * M; i++) uhat[i] = acc[i] + dt / 6.0 * nh[i];
+    oracle_dealias(uhat, 3, n);
+  }
+  free(us);
+  free(nh);
+  free(acc);
+  free(E);
+  free(H);
   return 0;
 }
 

@@ -48,6 +48,10 @@ int oracle_sc1d(const ocplx *in, ocplx *out, long n, int kind, int dir);
  * (half spectrum) else nz (real coefficients, imaginary parts 0). */
 int oracle_transform3(const double *in, ocplx *out, int nx, int ny, int nz, const int kind[3]);
 int oracle_itransform3(const ocplx *in, double *out, int nx, int ny, int nz, const int kind[3]);
+/* One coefficient (a, b, c) of oracle_transform3 of FP32 input by its
+ * definition, O(nx ny nz); out = (re, im). */
+int oracle_transform3_coeff_f32(const float *in, int nx, int ny, int nz, const int kind[3], int a, int b, int c,
+                                double *out);
 
 /* 3D transforms in the paper's pass order (Sec. 3): forward z r2c, y c2c, x c2c
  * then the 1/N^3 factor; inverse x c2c, y c2c, z c2r. */
@@ -79,6 +83,8 @@ int oracle_ns_rhs(const ocplx *uhat, ocplx *nhat, int n, const oracle_ns_params 
 int oracle_ns_rhs_divergence(const ocplx *uhat, ocplx *nhat, int n);
 /* nsteps of RK2 (Heun) with the viscous integrating factor exp(-nu k^2 dt). */
 int oracle_ns_step(ocplx *uhat, int n, const oracle_ns_params *p, int nsteps);
+/* nsteps of the paper's RK4 with the same integrating factor (Lawson form). */
+int oracle_ns_step_rk4(ocplx *uhat, int n, const oracle_ns_params *p, int nsteps);
 
 /* Diagnostics: E = 1/2 sum w |u|^2, eps = nu sum w k^2 |u|^2,
  * EK[K] = 1/2 sum_{nint|k| = K} w |u|^2 for K = 0..kmax (modes beyond kmax dropped). */

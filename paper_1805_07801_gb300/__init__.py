@@ -56,7 +56,11 @@ class tarang_params(ctypes.Structure):
         ("force_k2min", ctypes.c_int),
         ("force_k2max", ctypes.c_int),
         ("sgs_model", ctypes.POINTER(tarang_sgs_model)),
+        ("scheme", ctypes.c_int),
     ]
+
+
+TARANG_RK2, TARANG_RK4 = 0, 1
 
 
 _lib = None
@@ -85,6 +89,8 @@ def lib() -> ctypes.CDLL:
             "tarang_diag_kmax": ([vp], i),
             "tarang_diag": ([vp, vp, d, vp, vp], i),
             "tarang_diag_noalloc": ([i, vp, d, vp, vp], i),
+            "fftk_forward": ([vp, vp, vp, vp, i, vp], i),
+            "fftk_inverse": ([vp, vp, vp, vp, i, vp], i),
             "tarang_transfer": ([vp, vp, c.POINTER(tarang_params), vp, vp], i),
             "tarang_shell_transfer": ([vp, vp, i, vp, vp, vp], i),
             "tarang_ic_random": ([vp, vp, vp, d, d, vp], i),
@@ -155,8 +161,10 @@ def fftk_c2r(plan: int, in_ptr, out_ptr, batch: int = 1, stream=0) -> None:
     _check(lib().fftk_c2r(_vp(plan), _vp(in_ptr), _vp(out_ptr), batch, _vp(stream)), "fftk_c2r")
 
 
-def make_params(nu: float, dt: float = 0.0, force_eps: float = 0.0, force_k2=(1, 4), sgs_model=None) -> tarang_params:
+def make_params(nu: float, dt: float = 0.0, force_eps: float = 0.0, force_k2=(1, 4), sgs_model=None,
+                scheme: int = TARANG_RK2) -> tarang_params:
     p = tarang_params(float(nu), float(dt), float(force_eps), int(force_k2[0]), int(force_k2[1]))
+    p.scheme = int(scheme)
     if sgs_model is not None:
         p.sgs_model = ctypes.pointer(sgs_model)
         p._model_ref = sgs_model  # keep alive with the params
@@ -195,6 +203,29 @@ def tarang_ns_step(plan: int, uhat_ptr, params: tarang_params, nsteps: int = 1, 
         return None
     vals = list(buf)
     return vals[0], vals[1], vals[2:]
+
+
+FFTK_FOURIER, FFTK_SINE, FFTK_COSINE = 0, 1, 2
+_BASIS_CHARS = {"F": FFTK_FOURIER, "S": FFTK_SINE, "C": FFTK_COSINE}
+
+
+def _basis(basis):
+    if isinstance(basis, str):
+        basis = [_BASIS_CHARS[ch] for ch in basis]
+    return (ctypes.c_int * 3)(*[int(b) for b in basis])
+
+
+def fftk_forward(plan: int, basis, in_ptr, out_ptr, batch: int = 1, stream=0) -> None:
+    """Forward transform with a basis per axis ('SFF', 'CCS', ... or three fftk_basis codes)."""
+    b = _basis(basis)
+    _check(lib().fftk_forward(_vp(plan), ctypes.cast(b, ctypes.c_void_p), _vp(in_ptr), _vp(out_ptr), batch,
+                              _vp(stream)), "fftk_forward")
+
+
+def fftk_inverse(plan: int, basis, in_ptr, out_ptr, batch: int = 1, stream=0) -> None:
+    b = _basis(basis)
+    _check(lib().fftk_inverse(_vp(plan), ctypes.cast(b, ctypes.c_void_p), _vp(in_ptr), _vp(out_ptr), batch,
+                              _vp(stream)), "fftk_inverse")
 
 
 def tarang_transfer(plan: int, uhat_ptr, params: tarang_params = None, stream=0):

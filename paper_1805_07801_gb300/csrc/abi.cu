@@ -12,7 +12,7 @@ namespace fftk {
 const char* const kKernelNames[KK_COUNT] = {
     "z_r2c", "y_fwd", "x_fwd", "x_inv", "y_inv", "z_c2r",
     "ns_invx_curl", "ns_invy", "ns_z_product", "ns_fwdy", "ns_fwdx_update",
-    "ns_reduce", "aux"};
+    "ns_reduce", "aux", "sc_fwd", "sc_inv"};
 
 bool is_pow2(long long v) { return v >= 1 && (v & (v - 1)) == 0; }
 int ilog2(long long v) {
@@ -146,10 +146,12 @@ extern "C" fftk_status fftk_plan_create(int nx, int ny, int nz, fftk_dtype dtype
   if (nz > lt) lt = nz;
   p->twlog = ilog2(lt);
   // Twiddle tables in FP64 (host libm), rounded once to FP32: for every
-  // power of two L <= LT, exp(-2 pi i m / L), m < L, at offset L (2 LT values).
-  std::vector<float2> h(2 * (size_t)lt, make_float2(1.f, 0.f));
+  // power of two L <= 4 LT, exp(-2 pi i m / L), m < L, at offset L (8 LT
+  // values; the sizes above LT are the sine/cosine passes' quarter waves).
+  const int ltab = 4 * lt;
+  std::vector<float2> h(2 * (size_t)ltab, make_float2(1.f, 0.f));
   const double two_pi = 6.283185307179586476925286766559;
-  for (int L = 1; L <= lt; L *= 2)
+  for (int L = 1; L <= ltab; L *= 2)
     for (int m = 0; m < L; ++m) {
       const double ang = two_pi * (double)m / (double)L;
       h[(size_t)L + m] = make_float2((float)std::cos(ang), (float)(-std::sin(ang)));
@@ -262,6 +264,98 @@ extern "C" fftk_status fftk_c2r(fftk_plan p, const void* in, float* out, int bat
     }
   }
   if (e == cudaSuccess) e = launch_z_c2r(p, src, out, B * p->nx * p->ny, st);
+  return from_cuda(e);
+}
+
+// ------------------------------------------------------ mixed bases ----
+// Fourier axes trailing (FFF, SFF, SSF, SSS; Sec. 2.1); every axis of a
+// sine/cosine basis longer than 1 point, z even.
+static bool basis_ok(fftk_plan p, const int* b) {
+  for (int d = 0; d < 3; ++d)
+    if (b[d] != FFTK_FOURIER && b[d] != FFTK_SINE && b[d] != FFTK_COSINE) return false;
+  if (b[0] == FFTK_FOURIER && (b[1] != FFTK_FOURIER || b[2] != FFTK_FOURIER)) return false;
+  if (b[1] == FFTK_FOURIER && b[2] != FFTK_FOURIER) return false;
+  if (b[0] != FFTK_FOURIER && p->nx < 2) return false;
+  if (b[1] != FFTK_FOURIER && p->ny < 2) return false;
+  return true;
+}
+
+static size_t basis_spectrum_bytes(fftk_plan p, const int* b, int batch) {
+  const size_t cells = (size_t)batch * p->nx * p->ny;
+  return b[2] == FFTK_FOURIER ? cells * p->hz * sizeof(float2) : cells * p->nz * sizeof(float);
+}
+
+// One x or y pass over float2 columns: Fourier (plan dtype) or sine/cosine.
+static cudaError_t axis_pass(fftk_plan p, int basis, int L, int dir, const float2* in, float2* out, long long P,
+                             long long Q, float scale, int fkind, cudaStream_t st) {
+  if (basis == FFTK_FOURIER) return strided_pass(p, L, dir, in, out, P, Q, scale, fkind, st);
+  return launch_scpass(p, L, basis == FFTK_SINE, dir, in, out, P, Q, scale, dir < 0 ? KK_SC_FWD : KK_SC_INV, st);
+}
+
+extern "C" fftk_status fftk_forward(fftk_plan p, const int* basis, const float* in, void* out, int batch,
+                                    void* cuda_stream) {
+  if (!p || !basis || !in || !out || batch < 1) return FFTK_ERR_INVALID_ARG;
+  if (misaligned(in) || misaligned(out) || !basis_ok(p, basis)) return FFTK_ERR_INVALID_ARG;
+  const long long B = batch;
+  const size_t in_bytes = (size_t)B * p->nx * p->ny * p->nz * sizeof(float);
+  if (overlap(in, in_bytes, out, basis_spectrum_bytes(p, basis, batch))) return FFTK_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  const float sx = (float)(1.0 / p->nx), sy = (float)(1.0 / p->ny), sz = (float)(1.0 / p->nz);
+  cudaError_t e;
+  long long qy, qx;  // float2 columns of the y and x passes
+  float2* o = static_cast<float2*>(out);
+  if (basis[2] == FFTK_FOURIER) {
+    e = launch_z_r2c(p, in, o, B * p->nx * p->ny, sz, st);
+    qy = p->hz;
+  } else {
+    e = launch_scz(p, basis[2] == FFTK_SINE, -1, in, static_cast<float*>(out), B * p->nx * p->ny, sz, KK_SC_FWD,
+                   st);
+    qy = p->nz / 2;  // a real field read as pairs of adjacent z values
+  }
+  qx = (long long)p->ny * qy;
+  if (e == cudaSuccess && p->ny > 1) e = axis_pass(p, basis[1], p->ny, -1, o, o, B * p->nx, qy, sy, KK_Y_FWD, st);
+  if (e == cudaSuccess && p->nx > 1) e = axis_pass(p, basis[0], p->nx, -1, o, o, B, qx, sx, KK_X_FWD, st);
+  return from_cuda(e);
+}
+
+extern "C" fftk_status fftk_inverse(fftk_plan p, const int* basis, const void* in, float* out, int batch,
+                                    void* cuda_stream) {
+  if (!p || !basis || !in || !out || batch < 1) return FFTK_ERR_INVALID_ARG;
+  if (misaligned(in) || misaligned(out) || !basis_ok(p, basis)) return FFTK_ERR_INVALID_ARG;
+  const long long B = batch;
+  const size_t in_bytes = basis_spectrum_bytes(p, basis, batch);
+  const size_t out_bytes = (size_t)B * p->nx * p->ny * p->nz * sizeof(float);
+  if (overlap(in, in_bytes, out, out_bytes)) return FFTK_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  const bool zf = basis[2] == FFTK_FOURIER;
+  const long long qy = zf ? p->hz : p->nz / 2, qx = (long long)p->ny * qy;
+  const float2* src = static_cast<const float2*>(in);
+  cudaError_t e = cudaSuccess;
+  // the x and y passes run in the plan's workspace (Fourier z) or in `out`
+  // (all-real spectra have the size of the field); `in` is not modified
+  float2* w = reinterpret_cast<float2*>(out);
+  if (zf && (p->nx > 1 || p->ny > 1)) {
+    void* wv = nullptr;
+    fftk_status s = ensure_ws(p, in_bytes, &wv);
+    if (s != FFTK_OK) return s;
+    if (overlap(wv, in_bytes, in, in_bytes) || overlap(wv, in_bytes, out, out_bytes)) return FFTK_ERR_INVALID_ARG;
+    w = static_cast<float2*>(wv);
+  }
+  if (p->nx > 1) {
+    e = axis_pass(p, basis[0], p->nx, +1, src, w, B, qx, 1.f, KK_X_INV, st);
+    src = w;
+  }
+  if (e == cudaSuccess && p->ny > 1) {
+    e = axis_pass(p, basis[1], p->ny, +1, src, w, B * p->nx, qy, 1.f, KK_Y_INV, st);
+    src = w;
+  }
+  if (e == cudaSuccess) {
+    if (zf)
+      e = launch_z_c2r(p, src, out, B * p->nx * p->ny, st);
+    else
+      e = launch_scz(p, basis[2] == FFTK_SINE, +1, reinterpret_cast<const float*>(src), out, B * p->nx * p->ny,
+                     1.f, KK_SC_INV, st);
+  }
   return from_cuda(e);
 }
 

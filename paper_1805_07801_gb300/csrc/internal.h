@@ -29,6 +29,8 @@ enum KernelKind : int {
   KK_NS_FWDX,
   KK_NS_REDUCE,
   KK_AUX,
+  KK_SC_FWD,
+  KK_SC_INV,
   KK_COUNT
 };
 extern const char* const kKernelNames[KK_COUNT];
@@ -56,7 +58,7 @@ struct fftk_plan_s {
   fftk_dtype dtype;
   int device;
   int twlog;                 // LT = 2^twlog = max(nx, ny, nz)
-  float2* d_tw = nullptr;    // twiddle tables: at offset L (L = 1, 2, 4, ..., LT), exp(-2 pi i m / L), m < L
+  float2* d_tw = nullptr;    // twiddle tables: at offset L (L = 1, 2, 4, ..., 4 LT), exp(-2 pi i m / L), m < L
   __half* d_dft16 = nullptr; // split-FP16 DFT-16 operands (FFTK_R32_SPLIT16): forward, inverse
   int* d_err = nullptr;      // device error word (bounded waits that expired)
   // c2r workspace (one complex field per batch element)
@@ -73,7 +75,8 @@ struct fftk_plan_s {
 
 namespace fftk {
 
-// The plan's twiddle table of size L (a power of two <= LT): exp(-2 pi i m / L), m < L.
+// The plan's twiddle table of size L (a power of two <= 4 LT): exp(-2 pi i m / L), m < L.
+// Tables beyond LT serve the quarter-wave factors of the sine/cosine passes.
 inline const float2* twiddles(const fftk_plan_s* p, int L) { return p->d_tw + L; }
 
 // Launch bracketing: counts the launch and records profiling events.
@@ -95,6 +98,10 @@ cudaError_t launch_z_c2r(fftk_plan p, const float2* in, float* out, long long nl
                          cudaStream_t st);
 // strided c2c pass: array [P][L][Q], transform along L (element stride Q),
 // in may equal out.  sign = -1 forward, +1 inverse; output multiplied by scale.
+cudaError_t launch_scpass(fftk_plan p, int L, bool sine, int dir, const float2* in, float2* out, long long P,
+                          long long Q, float scale, int kind, cudaStream_t st);
+cudaError_t launch_scz(fftk_plan p, bool sine, int dir, const float* in, float* out, long long nlines,
+                       float scale, int kind, cudaStream_t st);
 cudaError_t launch_cpass(fftk_plan p, int L, int sign, const float2* in, float2* out, long long P,
                          long long Q, float scale, int kind, cudaStream_t st);
 

@@ -322,10 +322,21 @@ __global__ void __launch_bounds__(NZCfg<N>::THREADS, 3)
 }
 
 // ----------------------------------------------------- x pass + update -----
-enum NSMode : int { NS_RHS = 0, NS_STAGE1 = 1, NS_STAGE2 = 2 };
+enum NSMode : int {
+  NS_RHS = 0,
+  NS_STAGE1 = 1,
+  NS_STAGE2 = 2,
+  NS_RK4_1 = 3,
+  NS_RK4_2 = 4,
+  NS_RK4_3 = 5,
+  NS_RK4_4 = 6
+};
 
 struct NSUpdate {
-  const float2* etab;  // exp(-nu k^2 dt) = hi + lo (two FP32 parts), indexed by integer k^2
+  const float2* etab;  // exp(-nu k^2 dt) = hi + lo (two FP32 parts), indexed by integer k^2;
+                       // exp(-nu k^2 dt/2) follows at offset etab_len (the RK4 half steps)
+  int etab_len;
+  float2* acc;         // RK4 accumulator (3 fields)
   const double* ef;    // forced-mode energy (device scalar)
   double feps;         // injected power (0 = off)
   int k2min, k2max;
@@ -338,6 +349,12 @@ struct NSUpdate {
 //   RHS:    out = N
 //   STAGE1: out = E (u0 + dt N)                      (out = u1)
 //   STAGE2: out = 1/2 E u0 + 1/2 (u1 + dt N)         (out = u0, in place)
+// or one stage of RK4 with H = exp(-nu k^2 dt/2), state u0, stage state u1,
+// accumulator A (N from the stage's input: u0 in RK4_1, u1 after):
+//   RK4_1:  A = E u0 + dt/6 E N,   out = H (u0 + dt/2 N)   (out = u1)
+//   RK4_2:  A += dt/3 H N,         out = H u0 + dt/2 N     (out = u1)
+//   RK4_3:  A += dt/3 H N,         out = E u0 + dt H N     (out = u1)
+//   RK4_4:  out = A + dt/6 N                                (out = u0)
 __device__ __forceinline__ void ns_mode_update(float2 nx, float2 ny, float2 nz, int kx, int ky, int kz,
                                                long long idx, long long M, const NSUpdate& upd, int mode,
                                                float gforce, const float2* u0, const float2* u1,
@@ -360,7 +377,7 @@ __device__ __forceinline__ void ns_mode_update(float2 nx, float2 ny, float2 nz, 
     nz = cadd(nz, extra[idx + 2 * M]);
   }
   const bool forced = gforce != 0.f && k2 >= upd.k2min && k2 <= upd.k2max;
-  const float2* ucur = (mode == NS_STAGE2) ? u1 : u0;
+  const float2* ucur = (mode == NS_STAGE2 || mode >= NS_RK4_2) ? u1 : u0;
   if (forced) {
     nx = cadd(nx, cscale(ucur[idx], gforce));
     ny = cadd(ny, cscale(ucur[idx + M], gforce));
@@ -377,6 +394,35 @@ __device__ __forceinline__ void ns_mode_update(float2 nx, float2 ny, float2 nz, 
   const float2 E = __ldg(&upd.etab[k2]);
   const float dt = upd.dt;
   const float2 n3[3] = {nx, ny, nz};
+  if (mode >= NS_RK4_1) {
+    const float2 H = __ldg(&upd.etab[upd.etab_len + k2]);
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+      const long long i = idx + f * M;
+      const float2 nv = n3[f];
+      if (mode == NS_RK4_4) {
+        const float2 a = upd.acc[i];
+        out[i] = make_float2(fmaf(dt / 6.f, nv.x, a.x), fmaf(dt / 6.f, nv.y, a.y));
+        continue;
+      }
+      const float2 a = u0[i];
+      const float2 ea = make_float2(fmaf(a.x, E.x, a.x * E.y), fmaf(a.y, E.x, a.y * E.y));  // E u0
+      const float2 ha = make_float2(fmaf(a.x, H.x, a.x * H.y), fmaf(a.y, H.x, a.y * H.y));  // H u0
+      const float2 hn = make_float2(fmaf(nv.x, H.x, nv.x * H.y), fmaf(nv.y, H.x, nv.y * H.y));  // H N
+      if (mode == NS_RK4_1) {
+        const float2 en = make_float2(fmaf(nv.x, E.x, nv.x * E.y), fmaf(nv.y, E.x, nv.y * E.y));
+        upd.acc[i] = make_float2(fmaf(dt / 6.f, en.x, ea.x), fmaf(dt / 6.f, en.y, ea.y));
+        const float sx = a.x + 0.5f * dt * nv.x, sy = a.y + 0.5f * dt * nv.y;
+        out[i] = make_float2(fmaf(sx, H.x, sx * H.y), fmaf(sy, H.x, sy * H.y));
+      } else {
+        const float2 ac = upd.acc[i];
+        upd.acc[i] = make_float2(fmaf(dt / 3.f, hn.x, ac.x), fmaf(dt / 3.f, hn.y, ac.y));
+        out[i] = (mode == NS_RK4_2) ? make_float2(fmaf(0.5f * dt, nv.x, ha.x), fmaf(0.5f * dt, nv.y, ha.y))
+                                    : make_float2(fmaf(dt, hn.x, ea.x), fmaf(dt, hn.y, ea.y));
+      }
+    }
+    return;
+  }
 #pragma unroll
   for (int f = 0; f < 3; ++f) {
     const float2 a = u0[idx + f * M];
@@ -700,6 +746,7 @@ struct NSWork {
   fftk_sgs_work* sgs = nullptr;  // learned-closure scratch
   float* r6 = nullptr;     // 6 real fields (unfused split-precision right-hand side)
   float* r3 = nullptr;     // 3 real fields (shell-to-shell transfer: the advection term)
+  float2* acc = nullptr;   // 3 fields (RK4 accumulator)
   double* sout = nullptr;  // per-giver shell sums of the shell-to-shell transfer
   int sout_rows = 0;
   int kmax = 0;
@@ -750,7 +797,7 @@ static fftk_status ns_ensure(fftk_plan p) {
   cudaError_t e = cudaMalloc(&s->w, 6 * fb);
   if (e == cudaSuccess) e = cudaMalloc(&s->u1, 3 * fb);
   if (e == cudaSuccess) e = cudaMemset(s->u1, 0, 3 * fb);
-  if (e == cudaSuccess) e = cudaMalloc(&s->etab, sizeof(float2) * (size_t)s->etab_len);
+  if (e == cudaSuccess) e = cudaMalloc(&s->etab, sizeof(float2) * 2 * (size_t)s->etab_len);
   if (e == cudaSuccess) e = cudaMalloc(&s->ef, sizeof(double));
   if (e == cudaSuccess) e = cudaMemset(s->ef, 0, sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&s->part, sizeof(double) * (size_t)diag_blocks(width) * width);
@@ -779,12 +826,13 @@ static fftk_status ns_ensure(fftk_plan p) {
 static fftk_status ns_etab(fftk_plan p, double nu, double dt) {
   NSWork* s = p->ns;
   if (s->etab_nu == nu && s->etab_dt == dt) return FFTK_OK;
-  std::vector<float2> h((size_t)s->etab_len);
-  for (int k2 = 0; k2 < s->etab_len; ++k2) {
-    const double E = std::exp(-nu * (double)k2 * dt);
-    const float hi = (float)E;
-    h[(size_t)k2] = make_float2(hi, (float)(E - (double)hi));
-  }
+  std::vector<float2> h(2 * (size_t)s->etab_len);
+  for (int half = 0; half < 2; ++half)
+    for (int k2 = 0; k2 < s->etab_len; ++k2) {
+      const double E = std::exp(-nu * (double)k2 * (half ? 0.5 * dt : dt));
+      const float hi = (float)E;
+      h[(size_t)half * s->etab_len + k2] = make_float2(hi, (float)(E - (double)hi));
+    }
   cudaError_t e = cudaMemcpy(s->etab, h.data(), sizeof(float2) * h.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return from_cuda(e);
   s->etab_nu = nu;
@@ -1028,6 +1076,7 @@ static fftk_status ns_check(fftk_plan p, const tarang_params* prm, bool need_dt)
   if (!(prm->nu >= 0.0) || !std::isfinite(prm->nu)) return FFTK_ERR_INVALID_ARG;
   if (need_dt && (!(prm->dt > 0.0) || !std::isfinite(prm->dt))) return FFTK_ERR_INVALID_ARG;
   if (prm->sgs_model && !prm->sgs_model->params) return FFTK_ERR_INVALID_ARG;
+  if (prm->scheme != TARANG_RK2 && prm->scheme != TARANG_RK4) return FFTK_ERR_INVALID_ARG;
   if (prm->force_eps != 0.0) {
     const int kd = (p->nx - 1) / 3;
     if (!(prm->force_eps > 0.0) || prm->force_k2min < 1 || prm->force_k2max < prm->force_k2min ||
@@ -1053,6 +1102,7 @@ void ns_free(fftk_plan p) {
   if (s->hout) cudaFreeHost(s->hout);
   cudaFree(s->r6);
   cudaFree(s->r3);
+  cudaFree(s->acc);
   cudaFree(s->sout);
   sgs_free(s->sgs);
   delete s;
@@ -1074,7 +1124,8 @@ extern "C" fftk_status tarang_ns_rhs(fftk_plan p, const void* uhat, void* nhat,
   const float2* u = static_cast<const float2*>(uhat);
   float2* out = static_cast<float2*>(nhat);
   cudaError_t e = cudaMemsetAsync(out, 0, sizeof(float2) * 3 * (size_t)g.M, st);
-  NSUpdate upd{p->ns->etab, p->ns->ef, prm->force_eps, prm->force_k2min, prm->force_k2max, 0.f,
+  NSUpdate upd{p->ns->etab, p->ns->etab_len, nullptr, p->ns->ef, prm->force_eps, prm->force_k2min,
+               prm->force_k2max, 0.f,
                (float)(1.0 / ((double)g.n * g.n * g.n))};
   if (e == cudaSuccess && prm->force_eps > 0.0) e = forced_energy(p, u, prm, st);
   const float2* extra = nullptr;
@@ -1231,9 +1282,31 @@ extern "C" fftk_status tarang_ns_step(fftk_plan p, void* uhat, const tarang_para
   NSWork* w = p->ns;
   const NSGeom g = w->g;
   float2* u = static_cast<float2*>(uhat);
-  NSUpdate upd{w->etab, w->ef, prm->force_eps, prm->force_k2min, prm->force_k2max, (float)prm->dt,
-               (float)(1.0 / ((double)g.n * g.n * g.n))};
+  if (prm->scheme == TARANG_RK4 && !w->acc) {
+    cudaError_t ea = cudaMalloc(&w->acc, sizeof(float2) * 3 * (size_t)g.M);
+    if (ea != cudaSuccess) {
+      cudaGetLastError();
+      return from_cuda(ea);
+    }
+  }
+  NSUpdate upd{w->etab, w->etab_len, w->acc, w->ef, prm->force_eps, prm->force_k2min, prm->force_k2max,
+               (float)prm->dt, (float)(1.0 / ((double)g.n * g.n * g.n))};
   cudaError_t e = cudaSuccess;
+  if (prm->scheme == TARANG_RK4) {
+    // four evaluations of N: from u, then from the stage state u1
+    for (int it = 0; it < nsteps && e == cudaSuccess; ++it)
+      for (int stage = 0; stage < 4 && e == cudaSuccess; ++stage) {
+        const float2* in = stage == 0 ? u : w->u1;
+        const float2* extra = nullptr;
+        if (prm->force_eps > 0.0) e = forced_energy(p, in, prm, st);
+        if (e == cudaSuccess && prm->sgs_model) e = sgs_term(p, &w->sgs, in, prm->sgs_model, st, &extra);
+        if (e == cudaSuccess)
+          e = ns_rhs_dispatch(p, in, u, w->u1, stage == 3 ? u : w->u1, upd, NS_RK4_1 + stage, extra, st);
+      }
+    if (e != cudaSuccess) return from_cuda(e);
+    if (diag_host) return tarang_diag(p, u, prm->nu, diag_host, cuda_stream);
+    return FFTK_OK;
+  }
   for (int it = 0; it < nsteps && e == cudaSuccess; ++it) {
     const float2* extra = nullptr;
     if (prm->force_eps > 0.0) e = forced_energy(p, u, prm, st);

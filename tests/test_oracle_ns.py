@@ -318,3 +318,43 @@ def test_shell_transfer_rejects_bad_bounds(oracle_mod):
     u = _random_uhat(oracle_mod, 8, seed=0)
     with pytest.raises(Exception):
         oracle_mod.shell_transfer(u, [0, 2, 2, 4])
+
+
+def test_rk4_taylor_green_exact_decay(oracle_mod):
+    # N = 0 for Taylor-Green: the integrating factor makes every stage exact
+    n, nu, dt, steps = 16, 0.01, 1e-2, 20
+    u0 = oracle_mod.ic_taylor_green(n)
+    u = oracle_mod.ns_step_rk4(u0, nu, dt, steps)
+    assert np.max(np.abs(u - u0 * np.exp(-2 * nu * steps * dt))) < 1e-15
+
+
+def test_rk4_is_fourth_order(oracle_mod):
+    # global error against a fine-step solution falls by 2^4 when dt halves
+    # (and by 2^2 for the second-order scheme on the same problem)
+    n, nu, T = 16, 0.02, 0.2
+    u0 = _random_uhat(oracle_mod, n, seed=11, k0=2.0)
+    ref = oracle_mod.ns_step_rk4(u0, nu, T / 64, 64)
+    e4 = [np.linalg.norm(oracle_mod.ns_step_rk4(u0, nu, T / s, s) - ref) for s in (4, 8)]
+    e2 = [np.linalg.norm(oracle_mod.ns_step(u0, nu, T / s, s) - ref) for s in (8, 16)]
+    assert 13.0 < e4[0] / e4[1] < 19.0, e4
+    assert 3.3 < e2[0] / e2[1] < 4.7, e2
+
+
+def test_rk4_matches_rk2_at_small_dt(oracle_mod):
+    n, nu, T = 16, 0.01, 0.05
+    u0 = _random_uhat(oracle_mod, n, seed=12, k0=2.0)
+    a = oracle_mod.ns_step_rk4(u0, nu, T / 10, 10)
+    b = oracle_mod.ns_step(u0, nu, T / 200, 200)
+    assert np.linalg.norm(a - b) < 1e-6 * np.linalg.norm(a)
+
+
+def test_rk4_forced_energy_budget(oracle_mod):
+    # dE/dt = eps_injected - dissipation: over a short interval with the
+    # constant-power forcing, E(T) - E(0) = eps T - int 2 nu Z dt (trapezoid)
+    n, nu, dt, steps, eps = 16, 0.02, 2e-3, 10, 0.1
+    u0 = _random_uhat(oracle_mod, n, seed=13, k0=2.0)
+    E0, d0, _ = oracle_mod.diag(u0, nu)
+    u = oracle_mod.ns_step_rk4(u0, nu, dt, steps, force_eps=eps, force_k2=(1, 4))
+    E1, d1, _ = oracle_mod.diag(u, nu)
+    T = dt * steps
+    assert abs((E1 - E0) - (eps * T - 0.5 * (d0 + d1) * T)) < 2e-3 * abs(E1 - E0) + 1e-6

@@ -131,3 +131,12 @@ def test_bad_bases_rejected(oracle_mod):
     for bad in ("FSF", "FFS", "SFS", [0, 0, 3]):
         with pytest.raises(Exception):
             oracle_mod.transform3(f, bad)
+
+
+@pytest.mark.parametrize("basis", ["SFF", "SSF", "CCS", "FFF"])
+def test_single_coefficient_matches_full_transform(oracle_mod, basis):
+    f = synth.uniform_pm1(5, 0, (8, 16, 8))
+    full = oracle_mod.transform3(f.astype(np.float64), basis)
+    for a, b, c in ((0, 0, 0), (3, 5, 2), (7, 15, full.shape[2] - 1), (1, 9, 4)):
+        got = oracle_mod.transform3_coeff(f, basis, a, b, c)
+        assert abs(got - full[a, b, c]) < 1e-15
