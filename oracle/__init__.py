@@ -56,6 +56,8 @@ def lib():
             L.oracle_ns_rhs_divergence.argtypes = [vp, vp, c.c_int]
             L.oracle_ns_step.argtypes = [vp, c.c_int, vp, c.c_int]
             L.oracle_ns_step_rk4.argtypes = [vp, c.c_int, vp, c.c_int]
+            L.oracle_rbc_rhs.argtypes = [vp, vp, c.c_int]
+            L.oracle_rbc_step.argtypes = [vp, c.c_int, c.c_double, c.c_double, c.c_double, c.c_int, c.c_int]
             L.oracle_diag.argtypes = [vp, c.c_int, c.c_double, dp, dp, vp, c.c_int]
             L.oracle_transfer.argtypes = [vp, vp, c.c_int]
             L.oracle_transfer.restype = c.c_double
@@ -251,6 +253,21 @@ def ns_step_rk4(uhat, nu, dt, nsteps=1, force_eps=0.0, force_k2=(1, 4)) -> np.nd
     p = _params(nu, dt, force_eps, force_k2)
     _check(lib().oracle_ns_step_rk4(_ptr(u), u.shape[1], ctypes.byref(p), nsteps), "ns_step_rk4")
     return u
+
+
+def rbc_rhs(state) -> np.ndarray:
+    """(N_u, N_theta) of a Rayleigh-Benard state [4][n][n][n/2+1]."""
+    st = np.ascontiguousarray(state, dtype=np.complex128)
+    out = np.empty_like(st)
+    _check(lib().oracle_rbc_rhs(_ptr(st), _ptr(out), st.shape[1]), "rbc_rhs")
+    return out
+
+
+def rbc_step(state, Ra, Pr, dt, nsteps=1, scheme=1) -> np.ndarray:
+    st = np.array(state, dtype=np.complex128, order="C", copy=True)
+    _check(lib().oracle_rbc_step(_ptr(st), st.shape[1], float(Ra), float(Pr), float(dt), nsteps, scheme),
+           "rbc_step")
+    return st
 
 
 def kmax_shell(n: int) -> int:

@@ -727,6 +727,142 @@ int oracle_ns_step_rk4(cplx *uhat, int n, const oracle_ns_params *p, int nsteps)
   return 0;
 }
 
+/* ------------------------------------------------ Rayleigh-Benard (FFF) -- */
+/* Sec. 2.2, Eqs. (12)-(13) in the non-dimensional form, on the 2 pi-periodic
+ * cube with gravity along z: state s[4][n][n][n/2+1] = (u_x, u_y, u_z, theta),
+ *   d_t u + (u.grad) u = -grad sigma + theta z + nu lap u,      nu = sqrt(Pr/Ra),
+ *   d_t theta + (u.grad) theta = u_z + kappa lap theta,        kappa = 1/sqrt(Ra Pr).
+ * Right-hand side without the diffusive terms (u solenoidal):
+ *   N_u = P[F(u x omega) + theta z],  N_theta = -i k . F(u theta) + u_z,
+ * both 2/3-truncated. */
+int oracle_rbc_rhs(const cplx *st, cplx *out, int n) {
+  if (!is_pow2(n) || n < 2) return -1;
+  const long N = n, HZ = n / 2 + 1, M = N * N * HZ, R = N * N * N;
+  int rc = oracle_ns_rhs(st, out, n, NULL); /* P[F(u x omega)] */
+  if (rc) return rc;
+  /* + P[theta z]: theta z - k k_z theta / |k|^2 */
+  for (long a = 0; a < N; a++)
+    for (long b = 0; b < N; b++)
+      for (long c = 0; c < HZ; c++) {
+        long idx = (a * N + b) * HZ + c;
+        double kx = (double)kxy(a, N), ky = (double)kxy(b, N), kz = (double)c;
+        double k2 = kx * kx + ky * ky + kz * kz;
+        if (k2 == 0.0 || !kept(kxy(a, N), kxy(b, N), c, N)) continue;
+        cplx th = st[3 * M + idx];
+        out[idx] += -kx * kz * th / k2;
+        out[M + idx] += -ky * kz * th / k2;
+        out[2 * M + idx] += th - kz * kz * th / k2;
+      }
+  /* N_theta = -i k . F(u theta) + u_z */
+  double *ur = (double *)malloc(sizeof(double) * 3 * (size_t)R);
+  double *tr = (double *)malloc(sizeof(double) * (size_t)R);
+  double *pr = (double *)malloc(sizeof(double) * (size_t)R);
+  cplx *ph = (cplx *)malloc(sizeof(cplx) * 3 * (size_t)M);
+  if (!ur || !tr || !pr || !ph) return -2;
+  for (int f = 0; f < 3; f++) oracle_irfft3(st + f * M, ur + f * R, n, n, n);
+  oracle_irfft3(st + 3 * M, tr, n, n, n);
+  for (int f = 0; f < 3; f++) {
+    for (long x = 0; x < R; x++) pr[x] = ur[f * R + x] * tr[x];
+    oracle_rfft3(pr, ph + f * M, n, n, n);
+  }
+  for (long a = 0; a < N; a++)
+    for (long b = 0; b < N; b++)
+      for (long c = 0; c < HZ; c++) {
+        long idx = (a * N + b) * HZ + c;
+        double kx = (double)kder(kxy(a, N), N), ky = (double)kder(kxy(b, N), N), kz = (double)kder(c, N);
+        cplx div = kx * ph[idx] + ky * ph[M + idx] + kz * ph[2 * M + idx];
+        out[3 * M + idx] = -I * div + st[2 * M + idx];
+      }
+  oracle_dealias(out + 3 * M, 1, n);
+  free(ur);
+  free(tr);
+  free(pr);
+  free(ph);
+  return 0;
+}
+
+/* nsteps of RK2 (Heun, scheme 0) or RK4 (Lawson, scheme 1) with the
+ * integrating factors exp(-nu k^2 dt) for u and exp(-kappa k^2 dt) for theta,
+ * in the forms of oracle_ns_step and oracle_ns_step_rk4. */
+int oracle_rbc_step(cplx *st, int n, double Ra, double Pr, double dt, int nsteps, int scheme) {
+  if (!is_pow2(n) || n < 2 || Ra <= 0.0 || Pr <= 0.0 || (scheme != 0 && scheme != 1)) return -1;
+  const long N = n, HZ = n / 2 + 1, M = N * N * HZ;
+  const double nu = sqrt(Pr / Ra), kappa = 1.0 / sqrt(Ra * Pr);
+  cplx *us = (cplx *)malloc(sizeof(cplx) * 4 * (size_t)M);
+  cplx *nh = (cplx *)malloc(sizeof(cplx) * 4 * (size_t)M);
+  cplx *acc = (cplx *)malloc(sizeof(cplx) * 4 * (size_t)M);
+  double *E = (double *)malloc(sizeof(double) * 2 * (size_t)M); /* [u or theta][mode] */
+  double *H = (double *)malloc(sizeof(double) * 2 * (size_t)M);
+  if (!us || !nh || !acc || !E || !H) return -2;
+  for (long a = 0; a < N; a++)
+    for (long b = 0; b < N; b++)
+      for (long c = 0; c < HZ; c++) {
+        long m = (a * N + b) * HZ + c;
+        double kx = (double)kxy(a, N), ky = (double)kxy(b, N), kz = (double)c;
+        double k2 = kx * kx + ky * ky + kz * kz;
+        E[m] = exp(-nu * k2 * dt);
+        E[M + m] = exp(-kappa * k2 * dt);
+        H[m] = exp(-nu * k2 * dt * 0.5);
+        H[M + m] = exp(-kappa * k2 * dt * 0.5);
+      }
+  for (int s = 0; s < nsteps; s++) {
+    int rc = oracle_rbc_rhs(st, nh, n);
+    if (rc) return rc;
+    if (scheme == 0) {
+      for (int f = 0; f < 4; f++)
+        for (long m = 0; m < M; m++) {
+          long i = f * M + m, e = (f == 3 ? M : 0) + m;
+          us[i] = E[e] * (st[i] + dt * nh[i]);
+        }
+      oracle_dealias(us, 4, n);
+      rc = oracle_rbc_rhs(us, nh, n);
+      if (rc) return rc;
+      for (int f = 0; f < 4; f++)
+        for (long m = 0; m < M; m++) {
+          long i = f * M + m, e = (f == 3 ? M : 0) + m;
+          st[i] = 0.5 * E[e] * st[i] + 0.5 * (us[i] + dt * nh[i]);
+        }
+      oracle_dealias(st, 4, n);
+      continue;
+    }
+    for (int f = 0; f < 4; f++)
+      for (long m = 0; m < M; m++) {
+        long i = f * M + m, e = (f == 3 ? M : 0) + m;
+        acc[i] = E[e] * st[i] + dt / 6.0 * E[e] * nh[i];
+        us[i] = H[e] * (st[i] + 0.5 * dt * nh[i]);
+      }
+    oracle_dealias(us, 4, n);
+    rc = oracle_rbc_rhs(us, nh, n);
+    if (rc) return rc;
+    for (int f = 0; f < 4; f++)
+      for (long m = 0; m < M; m++) {
+        long i = f * M + m, e = (f == 3 ? M : 0) + m;
+        acc[i] += dt / 3.0 * H[e] * nh[i];
+        us[i] = H[e] * st[i] + 0.5 * dt * nh[i];
+      }
+    oracle_dealias(us, 4, n);
+    rc = oracle_rbc_rhs(us, nh, n);
+    if (rc) return rc;
+    for (int f = 0; f < 4; f++)
+      for (long m = 0; m < M; m++) {
+        long i = f * M + m, e = (f == 3 ? M : 0) + m;
+        acc[i] += dt / 3.0 * H[e] * nh[i];
+        us[i] = E[e] * st[i] + dt * H[e] * nh[i];
+      }
+    oracle_dealias(us, 4, n);
+    rc = oracle_rbc_rhs(us, nh, n);
+    if (rc) return rc;
+    for (long i = 0; i < 4 * M; i++) st[i] = acc[i] + dt / 6.0 * nh[i];
+    oracle_dealias(st, 4, n);
+  }
+  free(us);
+  free(nh);
+  free(acc);
+  free(E);
+  free(H);
+  return 0;
+}
+
 /* Shell index K = nint(|k|); |k| is never a half-integer for integer k. */
 static long shell_of(long k2) { return (long)floor(sqrt((double)k2) + 0.5); }
 

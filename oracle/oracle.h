@@ -86,6 +86,15 @@ int oracle_ns_step(ocplx *uhat, int n, const oracle_ns_params *p, int nsteps);
 /* nsteps of the paper's RK4 with the same integrating factor (Lawson form). */
 int oracle_ns_step_rk4(ocplx *uhat, int n, const oracle_ns_params *p, int nsteps);
 
+/* Rayleigh-Benard convection (Sec. 2.2, Eqs. (12)-(13), non-dimensional, FFF
+ * basis on the 2 pi-periodic cube, gravity along z), state
+ * s[4][n][n][n/2+1] = (u_x, u_y, u_z, theta):
+ *   N_u = P[F(u x omega) + theta z],  N_theta = -i k . F(u theta) + u_z
+ * (2/3-truncated; diffusion nu = sqrt(Pr/Ra), kappa = 1/sqrt(Ra Pr) is left
+ * to the integrating factors of the stepper; scheme 0 RK2, 1 RK4). */
+int oracle_rbc_rhs(const ocplx *s, ocplx *out, int n);
+int oracle_rbc_step(ocplx *s, int n, double Ra, double Pr, double dt, int nsteps, int scheme);
+
 /* Diagnostics: E = 1/2 sum w |u|^2, eps = nu sum w k^2 |u|^2,
  * EK[K] = 1/2 sum_{nint|k| = K} w |u|^2 for K = 0..kmax (modes beyond kmax dropped). */
 int oracle_diag(const ocplx *uhat, int n, double nu, double *E, double *eps,
