@@ -87,7 +87,7 @@ def fft_pass_bytes(n):
 
 # --------------------------------------------------- measured DRAM traffic ---
 KERNEL_SOURCES = {
-    "ns": ["ns.cu", "fft_engine.cuh", "internal.h"],
+    "ns": ["ns.cu", "ns_common.cuh", "fft_engine.cuh", "internal.h"],
     "fft": ["fft_passes.cu", "fft_engine.cuh", "internal.h"],
     "fft16": ["fft_tc.cu", "tcgen05.cuh", "fft_passes.cu", "fft_engine.cuh", "internal.h"],
 }
@@ -791,6 +791,49 @@ def run_schemes(n: int, steps: int):
                       "peak_GBps": hbm, "peak_kind": peak_kind, **out}), flush=True)
 
 
+def run_rbc(n: int, steps: int):
+    """Rayleigh-Benard convection at n^3 (FFF, Ra = 1e8, Pr = 1, dt = 1e-3):
+    the random-phase velocity of the decaying workload with theta = u_z,
+    stepped with RK4 (the paper's scheme: 52 transforms per step) and with
+    RK2, CUDA events over `steps` steps after 3.  Prints one JSON line with
+    steps/s and the time per transform."""
+    import torch
+
+    import paper_1805_07801_gb300 as fk
+    from paper_1805_07801_gb300 import build as fkbuild
+
+    fkbuild.build()
+    dev = torch.device("cuda:0")
+    st = torch.cuda.current_stream(dev).cuda_stream
+    plan = fk.fftk_plan_create(n, n, n)
+    nr = torch.empty((3, n, n, n), dtype=torch.float32, device=dev)
+    for f in range(3):
+        fk.fftk_fill_normal(nr[f].data_ptr(), n**3, SEED, f, st)
+    s0 = torch.empty((4, n, n, n // 2 + 1, 2), dtype=torch.float32, device=dev)
+    fk.tarang_ic_random(plan, nr.data_ptr(), s0.data_ptr(), K0, E0, st)
+    s0[3].copy_(s0[2])
+    del nr
+    out = {}
+    for name, scheme, ntr in (("rk4", fk.TARANG_RK4, 52), ("rk2", fk.TARANG_RK2, 26)):
+        s = s0.clone()
+        fk.tarang_rbc_step(plan, s.data_ptr(), 1e8, 1.0, 1e-3, 3, scheme, st)
+        torch.cuda.synchronize(dev)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        fk.tarang_rbc_step(plan, s.data_ptr(), 1e8, 1.0, 1e-3, steps, scheme, st)
+        b.record()
+        b.synchronize()
+        ms = a.elapsed_time(b) / steps
+        fin = bool(torch.isfinite(s).all())
+        out[name] = {"steps_per_s": round(1e3 / ms, 3), "ms_per_step": round(ms, 4), "transforms_per_step": ntr,
+                     "ms_per_transform_incl_pointwise": round(ms / ntr, 4), "finite": fin}
+    fk.fftk_sync(plan, st)
+    fk.fftk_plan_destroy(plan)
+    print(json.dumps({"workload": f"{n}^3 Rayleigh-Benard (FFF), Ra=1e8, Pr=1, dt=1e-3, random-phase u (k0={K0}), "
+                                  f"theta = u_z, seed {SEED}", **out}), flush=True)
+
+
 def run_bases(n: int):
     """Forward + inverse pairs of an n^3 normal(0,1) field (seed 0) in the
     paper's bases FFF, SFF, SSF and SSS (sine on x, y and z in turn; cosine
@@ -968,6 +1011,8 @@ def main():
                     help="time the energy transfer spectrum and flux of an N^3 field")
     ap.add_argument("--schemes", type=int, default=0, metavar="N",
                     help="time N^3 NS steps with RK2 and with RK4 for --steps steps")
+    ap.add_argument("--rbc", type=int, default=0, metavar="N",
+                    help="time N^3 Rayleigh-Benard steps (RK4 and RK2) for --steps steps")
     ap.add_argument("--bases", type=int, default=0, metavar="N",
                     help="time N^3 transform pairs in the FFF, SFF, SSF and SSS bases")
     args = ap.parse_args()
@@ -991,6 +1036,9 @@ def main():
         return
     if args.schemes:
         run_schemes(args.schemes, args.steps)
+        return
+    if args.rbc:
+        run_rbc(args.rbc, args.steps)
         return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

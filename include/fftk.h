@@ -202,6 +202,33 @@ fftk_status tarang_ns_rhs(fftk_plan p, const void *uhat, void *nhat, const taran
 fftk_status tarang_ns_step(fftk_plan p, void *uhat, const tarang_params *prm, int nsteps,
                            double *diag_host, void *cuda_stream);
 
+/* Rayleigh-Benard convection (Sec. 2.2, Eqs. (12)-(13) in their
+ * non-dimensional form; FFF basis: the 2 pi-periodic cube, gravity along z):
+ *   d_t u + (u.grad) u = -grad sigma + theta z + sqrt(Pr/Ra) lap u,
+ *   d_t theta + (u.grad) theta = u_z + lap theta / sqrt(Ra Pr).
+ * State: float2 [4][n][n][n/2+1] = (u_x, u_y, u_z, theta) on the 2/3 set
+ * (zero elsewhere, as for the velocity of tarang_ns_step).  The right-hand
+ * side without diffusion, N_u = P[F(u x omega) + theta z] and
+ * N_theta = -i k . F(u theta) + u_z, is evaluated through the plan's own
+ * transforms: seven inverse (u, omega, theta) and six forward (u x omega,
+ * u theta) per stage, the paper's 52 transforms per RK4 step (Sec. 7).
+ * Device memory: 18 more fields (allocated on first use, kept by the plan). */
+typedef struct {
+  double Ra;  /* Rayleigh number */
+  double Pr;  /* Prandtl number */
+  double dt;  /* time step */
+  int scheme; /* TARANG_RK2 or TARANG_RK4, integrating factors exp(-nu k^2 dt), exp(-kappa k^2 dt) */
+} tarang_rbc_params;
+
+/* out = (N_u, N_theta), float2 [4][n][n][n/2+1], distinct from state. */
+fftk_status tarang_rbc_rhs(fftk_plan p, const void *state, void *out, void *cuda_stream);
+
+/* nsteps steps in place, in the forms of tarang_ns_step (u and theta each
+ * with its own factor).  Asynchronous.  INVALID_ARG for non-positive or
+ * non-finite Ra, Pr, dt or an unknown scheme. */
+fftk_status tarang_rbc_step(fftk_plan p, void *state, const tarang_rbc_params *prm, int nsteps,
+                            void *cuda_stream);
+
 /* Largest shell index reported by the diagnostics for this plan. */
 int tarang_diag_kmax(fftk_plan p);
 

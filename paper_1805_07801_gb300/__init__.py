@@ -63,6 +63,15 @@ class tarang_params(ctypes.Structure):
 TARANG_RK2, TARANG_RK4 = 0, 1
 
 
+class tarang_rbc_params(ctypes.Structure):
+    _fields_ = [
+        ("Ra", ctypes.c_double),
+        ("Pr", ctypes.c_double),
+        ("dt", ctypes.c_double),
+        ("scheme", ctypes.c_int),
+    ]
+
+
 _lib = None
 
 
@@ -89,6 +98,8 @@ def lib() -> ctypes.CDLL:
             "tarang_diag_kmax": ([vp], i),
             "tarang_diag": ([vp, vp, d, vp, vp], i),
             "tarang_diag_noalloc": ([i, vp, d, vp, vp], i),
+            "tarang_rbc_rhs": ([vp, vp, vp, vp], i),
+            "tarang_rbc_step": ([vp, vp, c.POINTER(tarang_rbc_params), i, vp], i),
             "fftk_forward": ([vp, vp, vp, vp, i, vp], i),
             "fftk_inverse": ([vp, vp, vp, vp, i, vp], i),
             "tarang_transfer": ([vp, vp, c.POINTER(tarang_params), vp, vp], i),
@@ -203,6 +214,17 @@ def tarang_ns_step(plan: int, uhat_ptr, params: tarang_params, nsteps: int = 1, 
         return None
     vals = list(buf)
     return vals[0], vals[1], vals[2:]
+
+
+def tarang_rbc_rhs(plan: int, state_ptr, out_ptr, stream=0) -> None:
+    _check(lib().tarang_rbc_rhs(_vp(plan), _vp(state_ptr), _vp(out_ptr), _vp(stream)), "tarang_rbc_rhs")
+
+
+def tarang_rbc_step(plan: int, state_ptr, Ra: float, Pr: float, dt: float, nsteps: int = 1,
+                    scheme: int = TARANG_RK4, stream=0) -> None:
+    prm = tarang_rbc_params(float(Ra), float(Pr), float(dt), int(scheme))
+    _check(lib().tarang_rbc_step(_vp(plan), _vp(state_ptr), ctypes.byref(prm), int(nsteps), _vp(stream)),
+           "tarang_rbc_step")
 
 
 FFTK_FOURIER, FFTK_SINE, FFTK_COSINE = 0, 1, 2
