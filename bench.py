@@ -566,6 +566,16 @@ def run_case(case: str):
         fk.tarang_ic_random(plan, nr.data_ptr(), u.data_ptr(), K0, E0, st)
         del nr
         fk.tarang_transfer(plan, u.data_ptr(), None, st)
+    elif kind == "fft3":  # a grid with 3 * 2^m axes, same as fft
+        nx, ny, nz = (int(v) for v in arg.split(","))
+        plan = fk.fftk_plan_create(nx, ny, nz)
+        x = torch.empty((nx, ny, nz), dtype=torch.float32, device=dev)
+        fk.fftk_fill_normal(x.data_ptr(), x.numel(), SEED, 0, st)
+        F = torch.empty((nx, ny, nz // 2 + 1, 2), dtype=torch.float32, device=dev)
+        y = torch.empty_like(x)
+        for _ in range(2):
+            fk.fftk_r2c(plan, x.data_ptr(), F.data_ptr(), 1, st)
+            fk.fftk_c2r(plan, F.data_ptr(), y.data_ptr(), 1, st)
     elif kind in ("fft", "fft16"):
         nx, ny, nz = (int(v) for v in arg.split(","))
         plan = fk.fftk_plan_create(nx, ny, nz, fk.FFTK_R32_SPLIT16 if kind == "fft16" else fk.FFTK_R32)
@@ -834,6 +844,57 @@ def run_rbc(n: int, steps: int):
                                   f"theta = u_z, seed {SEED}", **out}), flush=True)
 
 
+def run_radix3():
+    """R2C + C2R pairs on the paper's 3 * 2^m grids (768^3 and 1536^3; 3072^3
+    needs 348 GB for input, spectrum and inverse workspace and is left out)
+    beside 512^3 and 1024^3, normal(0,1), seed 0, CUDA events over 10 pairs
+    after 3, against the pair roofline 8R + 80M.  Prints one JSON line."""
+    import numpy as np
+    import torch
+
+    import paper_1805_07801_gb300 as fk
+    from paper_1805_07801_gb300 import build as fkbuild
+
+    fkbuild.build()
+    dev = torch.device("cuda:0")
+    st_obj = torch.cuda.Stream(dev)
+    st = st_obj.cuda_stream
+    hbm, peak_kind = peaks()
+    rows = []
+    for n in (512, 768, 1024, 1536):
+        R, M = n**3, n * n * (n // 2 + 1)
+        pair = 8 * R + 80 * M
+        plan = fk.fftk_plan_create(n, n, n)
+        with torch.cuda.stream(st_obj):
+            x = torch.empty((n, n, n), dtype=torch.float32, device=dev)
+            fk.fftk_fill_normal(x.data_ptr(), R, SEED, 0, st)
+            F = torch.empty((n, n, n // 2 + 1, 2), dtype=torch.float32, device=dev)
+            y = torch.empty_like(x)
+        for _ in range(3):
+            fk.fftk_r2c(plan, x.data_ptr(), F.data_ptr(), 1, st)
+            fk.fftk_c2r(plan, F.data_ptr(), y.data_ptr(), 1, st)
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        kp = 10
+        e0.record(st_obj)
+        for _ in range(kp):
+            fk.fftk_r2c(plan, x.data_ptr(), F.data_ptr(), 1, st)
+            fk.fftk_c2r(plan, F.data_ptr(), y.data_ptr(), 1, st)
+        e1.record(st_obj)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / kp
+        err = float(torch.linalg.vector_norm((y - x).double()) / torch.linalg.vector_norm(x.double()))
+        rows.append({"n": n, "pairs_s": round(1e3 / ms, 3), "ms_per_pair": round(ms, 4), "pair_bytes": pair,
+                     "frac_pair": round(pair / (ms * 1e-3) / 1e9 / hbm, 4), "round_trip_rel_l2": err,
+                     "gflops_paper_model": round(2 * 5 * R * np.log2(R) / (ms * 1e-3) / 1e9, 1)})
+        fk.fftk_plan_destroy(plan)
+        del x, F, y
+        torch.cuda.empty_cache()
+    print(json.dumps({"workload": "R2C+C2R pairs of normal(0,1), seed 0, 2^m and 3*2^m cubes", "peak_GBps": hbm,
+                      "peak_kind": peak_kind, "sizes": rows}), flush=True)
+
+
 def run_bases(n: int):
     """Forward + inverse pairs of an n^3 normal(0,1) field (seed 0) in the
     paper's bases FFF, SFF, SSF and SSS (sine on x, y and z in turn; cosine
@@ -1013,6 +1074,7 @@ def main():
                     help="time N^3 NS steps with RK2 and with RK4 for --steps steps")
     ap.add_argument("--rbc", type=int, default=0, metavar="N",
                     help="time N^3 Rayleigh-Benard steps (RK4 and RK2) for --steps steps")
+    ap.add_argument("--radix3", action="store_true", help="time pairs at 512^3, 768^3, 1024^3 and 1536^3")
     ap.add_argument("--bases", type=int, default=0, metavar="N",
                     help="time N^3 transform pairs in the FFF, SFF, SSF and SSS bases")
     args = ap.parse_args()
@@ -1033,6 +1095,9 @@ def main():
         return
     if args.bases:
         run_bases(args.bases)
+        return
+    if args.radix3:
+        run_radix3()
         return
     if args.schemes:
         run_schemes(args.schemes, args.steps)

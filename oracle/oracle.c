@@ -92,6 +92,34 @@ int oracle_dft1d(const cplx *in, cplx *out, long n, int sign) {
   return 0;
 }
 
+/* Lines of a 3D transform: n = 2^m by the recursive radix-2 FFT above, or
+ * n = 3 * 2^m (the paper's 768, 1536, 3072 grids) by the DFT's definition,
+ * O(n^2), with the phase j k reduced mod n. */
+static int ok_len(long n) { return is_pow2(n) || (n % 3 == 0 && is_pow2(n / 3)); }
+
+static cplx *make_line_table(long n, int sign) {
+  if (is_pow2(n)) return make_twiddles(n, sign);
+  cplx *t = (cplx *)malloc(sizeof(cplx) * (size_t)n);
+  if (!t) return NULL;
+  for (long m = 0; m < n; m++) {
+    double ang = TWO_PI * (double)m / (double)n;
+    t[m] = cos(ang) + (double)sign * sin(ang) * I;
+  }
+  return t;
+}
+
+static void line_transform(const cplx *in, cplx *out, long n, const cplx *tab) {
+  if (is_pow2(n)) {
+    fft_rec(in, 1, out, n, tab, 1);
+    return;
+  }
+  for (long k = 0; k < n; k++) {
+    cplx acc = 0;
+    for (long j = 0; j < n; j++) acc += in[j] * tab[(j * k) % n];
+    out[k] = acc;
+  }
+}
+
 /* ---------------------------------------------------------------- 3D ---- */
 
 static long maxl3(long a, long b, long c) {
@@ -102,10 +130,10 @@ static long maxl3(long a, long b, long c) {
 /* Forward: Sec. 3 steps 1 (r2c along z), 3 (c2c along y), 5 (c2c along x);
  * the 1/(Nx Ny Nz) factor makes Eq. (1) its inverse. */
 int oracle_rfft3(const double *in, cplx *out, int nx, int ny, int nz) {
-  if (!is_pow2(nx) || !is_pow2(ny) || !is_pow2(nz) || nz < 2) return -1;
+  if (!ok_len(nx) || !ok_len(ny) || !ok_len(nz) || nz < 2) return -1;
   const long NX = nx, NY = ny, NZ = nz, HZ = nz / 2 + 1;
-  cplx *twz = make_twiddles(NZ, -1), *twy = make_twiddles(NY, -1),
-       *twx = make_twiddles(NX, -1);
+  cplx *twz = make_line_table(NZ, -1), *twy = make_line_table(NY, -1),
+       *twx = make_line_table(NX, -1);
   const long LMAX = maxl3(NX, NY, NZ);
   int rc = 0;
 #pragma omp parallel
@@ -116,7 +144,7 @@ int oracle_rfft3(const double *in, cplx *out, int nx, int ny, int nz) {
 #pragma omp for schedule(static)
     for (long ij = 0; ij < NX * NY; ij++) {
       for (long l = 0; l < NZ; l++) lin[l] = in[ij * NZ + l];
-      fft_rec(lin, 1, lout, NZ, twz, 1);
+      line_transform(lin, lout, NZ, twz);
       for (long c = 0; c < HZ; c++) out[ij * HZ + c] = lout[c];
     }
     /* step 3: complex-to-complex along y for every (i, k_z) */
@@ -124,14 +152,14 @@ int oracle_rfft3(const double *in, cplx *out, int nx, int ny, int nz) {
     for (long ic = 0; ic < NX * HZ; ic++) {
       long i = ic / HZ, c = ic % HZ;
       for (long j = 0; j < NY; j++) lin[j] = out[(i * NY + j) * HZ + c];
-      fft_rec(lin, 1, lout, NY, twy, 1);
+      line_transform(lin, lout, NY, twy);
       for (long j = 0; j < NY; j++) out[(i * NY + j) * HZ + c] = lout[j];
     }
     /* step 5: complex-to-complex along x for every (k_y, k_z) */
 #pragma omp for schedule(static)
     for (long jc = 0; jc < NY * HZ; jc++) {
       for (long i = 0; i < NX; i++) lin[i] = out[i * NY * HZ + jc];
-      fft_rec(lin, 1, lout, NX, twx, 1);
+      line_transform(lin, lout, NX, twx);
       for (long i = 0; i < NX; i++) out[i * NY * HZ + jc] = lout[i];
     }
     free(lin);
@@ -150,14 +178,14 @@ int oracle_rfft3(const double *in, cplx *out, int nx, int ny, int nz) {
 /* Inverse: the reverse of the forward passes (Sec. 3): x, y, then z c2r.  The
  * z line is extended by f(N-c) = conj(f(c)) and the real part is kept. */
 int oracle_irfft3(const cplx *in, double *out, int nx, int ny, int nz) {
-  if (!is_pow2(nx) || !is_pow2(ny) || !is_pow2(nz) || nz < 2) return -1;
+  if (!ok_len(nx) || !ok_len(ny) || !ok_len(nz) || nz < 2) return -1;
   const long NX = nx, NY = ny, NZ = nz, HZ = nz / 2 + 1;
   const long M = NX * NY * HZ;
   cplx *work = (cplx *)malloc(sizeof(cplx) * (size_t)M);
   if (!work) return -2;
   memcpy(work, in, sizeof(cplx) * (size_t)M);
-  cplx *twz = make_twiddles(NZ, +1), *twy = make_twiddles(NY, +1),
-       *twx = make_twiddles(NX, +1);
+  cplx *twz = make_line_table(NZ, +1), *twy = make_line_table(NY, +1),
+       *twx = make_line_table(NX, +1);
   const long LMAX = maxl3(NX, NY, NZ);
 #pragma omp parallel
   {
@@ -166,21 +194,21 @@ int oracle_irfft3(const cplx *in, double *out, int nx, int ny, int nz) {
 #pragma omp for schedule(static)
     for (long jc = 0; jc < NY * HZ; jc++) {
       for (long i = 0; i < NX; i++) lin[i] = work[i * NY * HZ + jc];
-      fft_rec(lin, 1, lout, NX, twx, 1);
+      line_transform(lin, lout, NX, twx);
       for (long i = 0; i < NX; i++) work[i * NY * HZ + jc] = lout[i];
     }
 #pragma omp for schedule(static)
     for (long ic = 0; ic < NX * HZ; ic++) {
       long i = ic / HZ, c = ic % HZ;
       for (long j = 0; j < NY; j++) lin[j] = work[(i * NY + j) * HZ + c];
-      fft_rec(lin, 1, lout, NY, twy, 1);
+      line_transform(lin, lout, NY, twy);
       for (long j = 0; j < NY; j++) work[(i * NY + j) * HZ + c] = lout[j];
     }
 #pragma omp for schedule(static)
     for (long ij = 0; ij < NX * NY; ij++) {
       for (long c = 0; c < NZ; c++)
         lin[c] = (c < HZ) ? work[ij * HZ + c] : conj(work[ij * HZ + (NZ - c)]);
-      fft_rec(lin, 1, lout, NZ, twz, 1);
+      line_transform(lin, lout, NZ, twz);
       for (long l = 0; l < NZ; l++) out[ij * NZ + l] = creal(lout[l]);
     }
     free(lin);

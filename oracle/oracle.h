@@ -54,7 +54,8 @@ int oracle_transform3_coeff_f32(const float *in, int nx, int ny, int nz, const i
                                 double *out);
 
 /* 3D transforms in the paper's pass order (Sec. 3): forward z r2c, y c2c, x c2c
- * then the 1/N^3 factor; inverse x c2c, y c2c, z c2r. */
+ * then the 1/N^3 factor; inverse x c2c, y c2c, z c2r.  Every dimension 2^m
+ * (lines by the radix-2 FFT) or 3 * 2^m (lines by the DFT's definition). */
 int oracle_rfft3(const double *in, ocplx *out, int nx, int ny, int nz);
 int oracle_irfft3(const ocplx *in, double *out, int nx, int ny, int nz);
 

@@ -15,6 +15,16 @@ const char* const kKernelNames[KK_COUNT] = {
     "ns_reduce", "aux", "sc_fwd", "sc_inv"};
 
 bool is_pow2(long long v) { return v >= 1 && (v & (v - 1)) == 0; }
+bool is_pow2_or_3x(long long v) { return is_pow2(v) || (v % 3 == 0 && is_pow2(v / 3)); }
+
+// A transform length the passes support: a power of two up to 4096, or
+// 3 * 2^m (a radix-3 step over power-of-two sub-lines of at least 2 points)
+// up to 3072; along z (halved by the real packing) at least 12.
+static bool dim_ok(int n, bool z) {
+  if (is_pow2(n)) return n <= 4096 && (!z || n >= 2);
+  if (n % 3 != 0 || !is_pow2(n / 3)) return false;
+  return n <= 3072 && n >= (z ? 12 : 6);
+}
 int ilog2(long long v) {
   int l = 0;
   while ((1LL << l) < v) ++l;
@@ -124,9 +134,7 @@ extern "C" fftk_status fftk_plan_create(int nx, int ny, int nz, fftk_dtype dtype
   if (!out) return FFTK_ERR_INVALID_ARG;
   *out = nullptr;
   if (dtype != FFTK_R32 && dtype != FFTK_R32_SPLIT16) return FFTK_ERR_INVALID_ARG;
-  if (!is_pow2(nx) || !is_pow2(ny) || !is_pow2(nz) || nx > 4096 || ny > 4096 || nz > 4096 ||
-      nz < 2)
-    return FFTK_ERR_UNSUPPORTED_SIZE;
+  if (!dim_ok(nx, false) || !dim_ok(ny, false) || !dim_ok(nz, true)) return FFTK_ERR_UNSUPPORTED_SIZE;
   int ndev = 0;
   cudaError_t e = cudaGetDeviceCount(&ndev);
   if (e != cudaSuccess || ndev <= 0) {
@@ -159,6 +167,21 @@ extern "C" fftk_status fftk_plan_create(int nx, int ny, int nz, fftk_dtype dtype
   e = cudaMalloc(&p->d_tw, sizeof(float2) * h.size());
   if (e == cudaSuccess)
     e = cudaMemcpy(p->d_tw, h.data(), sizeof(float2) * h.size(), cudaMemcpyHostToDevice);
+  // tables of size 3 * 2^j for the radix-3 lines, at offset L (2 L3 values)
+  int lt3 = 0;
+  for (int d : {nx, ny, nz})
+    if (!is_pow2(d) && d > lt3) lt3 = d;
+  if (e == cudaSuccess && lt3 > 0) {
+    std::vector<float2> h3(2 * (size_t)lt3, make_float2(1.f, 0.f));
+    for (int L = 3; L <= lt3; L *= 2)
+      for (int m = 0; m < L; ++m) {
+        const double ang = two_pi * (double)m / (double)L;
+        h3[(size_t)L + m] = make_float2((float)std::cos(ang), (float)(-std::sin(ang)));
+      }
+    e = cudaMalloc(&p->d_tw3, sizeof(float2) * h3.size());
+    if (e == cudaSuccess)
+      e = cudaMemcpy(p->d_tw3, h3.data(), sizeof(float2) * h3.size(), cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess) e = cudaMalloc(&p->d_err, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, sizeof(int));
   if (e == cudaSuccess && dtype == FFTK_R32_SPLIT16) e = upload_dft16_operands(p);
@@ -166,6 +189,7 @@ extern "C" fftk_status fftk_plan_create(int nx, int ny, int nz, fftk_dtype dtype
     fftk_status s = from_cuda(e);
     cudaGetLastError();
     if (p->d_tw) cudaFree(p->d_tw);
+    if (p->d_tw3) cudaFree(p->d_tw3);
     if (p->d_err) cudaFree(p->d_err);
     if (p->d_dft16) cudaFree(p->d_dft16);
     delete p;
@@ -182,6 +206,7 @@ extern "C" fftk_status fftk_plan_destroy(fftk_plan p) {
   cudaDeviceSynchronize();
   ns_free(p);
   if (p->d_tw) cudaFree(p->d_tw);
+  if (p->d_tw3) cudaFree(p->d_tw3);
   if (p->d_err) cudaFree(p->d_err);
   if (p->d_dft16) cudaFree(p->d_dft16);
   if (p->ws && p->ws_owned) cudaFree(p->ws);
@@ -210,6 +235,7 @@ extern "C" fftk_status fftk_set_workspace(fftk_plan p, void* dev_ptr, size_t byt
 // and the line length has two radix-16 stages, the FP32 kernel otherwise.
 static cudaError_t strided_pass(fftk_plan p, int L, int sign, const float2* in, float2* out,
                                 long long P, long long Q, float scale, int kind, cudaStream_t st) {
+  if (!is_pow2(L)) return launch_cpass3(p, L, sign, in, out, P, Q, scale, kind, st);
   if (p->dtype == FFTK_R32_SPLIT16 && cpass_tc_supported(L))
     return launch_cpass_tc(p, L, sign, in, out, P, Q, scale, kind, st);
   return launch_cpass(p, L, sign, in, out, P, Q, scale, kind, st);
@@ -275,8 +301,9 @@ static bool basis_ok(fftk_plan p, const int* b) {
     if (b[d] != FFTK_FOURIER && b[d] != FFTK_SINE && b[d] != FFTK_COSINE) return false;
   if (b[0] == FFTK_FOURIER && (b[1] != FFTK_FOURIER || b[2] != FFTK_FOURIER)) return false;
   if (b[1] == FFTK_FOURIER && b[2] != FFTK_FOURIER) return false;
-  if (b[0] != FFTK_FOURIER && p->nx < 2) return false;
-  if (b[1] != FFTK_FOURIER && p->ny < 2) return false;
+  if (b[0] != FFTK_FOURIER && (p->nx < 2 || !is_pow2(p->nx))) return false;
+  if (b[1] != FFTK_FOURIER && (p->ny < 2 || !is_pow2(p->ny))) return false;
+  if (b[2] != FFTK_FOURIER && !is_pow2(p->nz)) return false;
   return true;
 }
 

@@ -787,7 +787,7 @@ extern "C" fftk_status tarang_closure_features(fftk_plan p, const float* ubar, c
                                                float* frame, float* tau_frame, void* cuda_stream) {
   if (!p || !ubar || !inv || !frame || mis16(ubar) || ((tau == nullptr) != (tau_frame == nullptr)))
     return FFTK_ERR_INVALID_ARG;
-  if (p->nx != p->ny || p->nx != p->nz || p->nx < 8) return FFTK_ERR_UNSUPPORTED_SIZE;
+  if (p->nx != p->ny || p->nx != p->nz || p->nx < 8 || !is_pow2(p->nx)) return FFTK_ERR_UNSUPPORTED_SIZE;
   const int n = p->nx;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   const long long R = (long long)n * n * n, M = (long long)n * n * (n / 2 + 1);

@@ -191,6 +191,7 @@ static cudaError_t cpass_l(fftk_plan p, const float2* in, float2* out, long long
 cudaError_t launch_z_r2c(fftk_plan p, const float* in, float2* out, long long nlines, float scale,
                          cudaStream_t st) {
   if (nlines <= 0) return cudaSuccess;
+  if (!is_pow2(p->nz)) return launch_z3(p, true, in, out, nlines, scale, st);
   switch (p->nz) {
 #define CASE(n) \
   case n:       \
@@ -204,6 +205,7 @@ cudaError_t launch_z_r2c(fftk_plan p, const float* in, float2* out, long long nl
 cudaError_t launch_z_c2r(fftk_plan p, const float2* in, float* out, long long nlines,
                          cudaStream_t st) {
   if (nlines <= 0) return cudaSuccess;
+  if (!is_pow2(p->nz)) return launch_z3(p, false, in, out, nlines, 1.f, st);
   switch (p->nz) {
 #define CASE(n) \
   case n:       \

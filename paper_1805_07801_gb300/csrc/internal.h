@@ -59,6 +59,7 @@ struct fftk_plan_s {
   int device;
   int twlog;                 // LT = 2^twlog = max(nx, ny, nz)
   float2* d_tw = nullptr;    // twiddle tables: at offset L (L = 1, 2, 4, ..., 4 LT), exp(-2 pi i m / L), m < L
+  float2* d_tw3 = nullptr;   // the same for L = 3, 6, 12, ... up to the largest 3 * 2^m dimension
   __half* d_dft16 = nullptr; // split-FP16 DFT-16 operands (FFTK_R32_SPLIT16): forward, inverse
   int* d_err = nullptr;      // device error word (bounded waits that expired)
   // c2r workspace (one complex field per batch element)
@@ -74,6 +75,9 @@ struct fftk_plan_s {
 };
 
 namespace fftk {
+
+// The table of size L = 3 * 2^m (a dimension of the plan or a divisor of one).
+inline const float2* twiddles3(const fftk_plan_s* p, int L) { return p->d_tw3 + L; }
 
 // The plan's twiddle table of size L (a power of two <= 4 LT): exp(-2 pi i m / L), m < L.
 // Tables beyond LT serve the quarter-wave factors of the sine/cosine passes.
@@ -102,6 +106,12 @@ cudaError_t launch_scpass(fftk_plan p, int L, bool sine, int dir, const float2* 
                           long long Q, float scale, int kind, cudaStream_t st);
 cudaError_t launch_scz(fftk_plan p, bool sine, int dir, const float* in, float* out, long long nlines,
                        float scale, int kind, cudaStream_t st);
+// lines of length 3 * 2^m (fft_radix3.cu)
+cudaError_t launch_cpass3(fftk_plan p, int L, int sign, const float2* in, float2* out, long long B, long long Q,
+                          float scale, int kind, cudaStream_t st);
+cudaError_t launch_z3(fftk_plan p, bool fwd, const void* in, void* out, long long nlines, float scale,
+                      cudaStream_t st);
+bool is_pow2_or_3x(long long v);
 cudaError_t launch_cpass(fftk_plan p, int L, int sign, const float2* in, float2* out, long long P,
                          long long Q, float scale, int kind, cudaStream_t st);
 

@@ -774,7 +774,7 @@ static cudaError_t forced_energy(fftk_plan p, const float2* u, const tarang_para
 fftk_status ns_check(fftk_plan p, const tarang_params* prm, bool need_dt) {
   if (!p || !prm) return FFTK_ERR_INVALID_ARG;
   if (p->nx != p->ny || p->nx != p->nz) return FFTK_ERR_UNSUPPORTED_SIZE;
-  if (p->nx < 8 || p->nx > 1024) return FFTK_ERR_UNSUPPORTED_SIZE;
+  if (p->nx < 8 || p->nx > 1024 || !is_pow2(p->nx)) return FFTK_ERR_UNSUPPORTED_SIZE;
   if (!(prm->nu >= 0.0) || !std::isfinite(prm->nu)) return FFTK_ERR_INVALID_ARG;
   if (need_dt && (!(prm->dt > 0.0) || !std::isfinite(prm->dt))) return FFTK_ERR_INVALID_ARG;
   if (prm->sgs_model && !prm->sgs_model->params) return FFTK_ERR_INVALID_ARG;
@@ -968,7 +968,7 @@ extern "C" fftk_status tarang_ic_random(fftk_plan p, const float* normals, void*
   if (!p || !normals || !uhat || !(k0 > 0.0) || !(E0 > 0.0) || !std::isfinite(k0) ||
       !std::isfinite(E0))
     return FFTK_ERR_INVALID_ARG;
-  if (p->nx != p->ny || p->nx != p->nz || p->nx < 8 || p->nx > 1024)
+  if (p->nx != p->ny || p->nx != p->nz || p->nx < 8 || p->nx > 1024 || !is_pow2(p->nx))
     return FFTK_ERR_UNSUPPORTED_SIZE;
   fftk_status s = ns_ensure(p);
   if (s != FFTK_OK) return s;
@@ -1024,7 +1024,7 @@ extern "C" fftk_status tarang_ic_random(fftk_plan p, const float* normals, void*
 // a coarse grid, into a valid solver state.
 extern "C" fftk_status tarang_dealias_project(fftk_plan p, void* uhat, void* cuda_stream) {
   if (!p || !uhat || misaligned16(uhat)) return FFTK_ERR_INVALID_ARG;
-  if (p->nx != p->ny || p->nx != p->nz || p->nx < 8 || p->nx > 1024)
+  if (p->nx != p->ny || p->nx != p->nz || p->nx < 8 || p->nx > 1024 || !is_pow2(p->nx))
     return FFTK_ERR_UNSUPPORTED_SIZE;
   fftk_status s = ns_ensure(p);
   if (s != FFTK_OK) return s;

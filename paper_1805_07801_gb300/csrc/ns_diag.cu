@@ -290,7 +290,7 @@ extern "C" int tarang_diag_kmax(fftk_plan p) { return p ? ns_kmax(p->nx) : -1; }
 extern "C" fftk_status tarang_diag(fftk_plan p, const void* uhat, double nu, double* diag_host,
                                    void* cuda_stream) {
   if (!p || !uhat || !diag_host || misaligned16(uhat)) return FFTK_ERR_INVALID_ARG;
-  if (p->nx != p->ny || p->nx != p->nz || p->nx < 8 || p->nx > 1024)
+  if (p->nx != p->ny || p->nx != p->nz || p->nx < 8 || p->nx > 1024 || !is_pow2(p->nx))
     return FFTK_ERR_UNSUPPORTED_SIZE;
   fftk_status s = ns_ensure(p);
   if (s != FFTK_OK) return s;
@@ -338,7 +338,7 @@ extern "C" fftk_status tarang_transfer(fftk_plan p, const void* uhat, const tara
 extern "C" fftk_status tarang_shell_transfer(fftk_plan p, const void* uhat, int nshells, const int* bounds,
                                              double* out_host, void* cuda_stream) {
   if (!p || !uhat || !bounds || !out_host || misaligned16(uhat)) return FFTK_ERR_INVALID_ARG;
-  if (p->nx != p->ny || p->nx != p->nz || p->nx < 8 || p->nx > 1024) return FFTK_ERR_UNSUPPORTED_SIZE;
+  if (p->nx != p->ny || p->nx != p->nz || p->nx < 8 || p->nx > 1024 || !is_pow2(p->nx)) return FFTK_ERR_UNSUPPORTED_SIZE;
   const int kmax = ns_kmax(p->nx);
   if (nshells < 1 || nshells > kmax + 1 || bounds[0] < 0 || bounds[nshells] > kmax + 1)
     return FFTK_ERR_INVALID_ARG;

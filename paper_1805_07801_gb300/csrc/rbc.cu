@@ -230,7 +230,7 @@ static cudaError_t rbc_stage(fftk_plan p, const float2* x, const float2* u0, flo
 static fftk_status rbc_check(fftk_plan p, const void* state) {
   if (!p || !state || misaligned16(state)) return FFTK_ERR_INVALID_ARG;
   if (p->nx != p->ny || p->nx != p->nz) return FFTK_ERR_UNSUPPORTED_SIZE;
-  if (p->nx < 8 || p->nx > 1024) return FFTK_ERR_UNSUPPORTED_SIZE;
+  if (p->nx < 8 || p->nx > 1024 || !is_pow2(p->nx)) return FFTK_ERR_UNSUPPORTED_SIZE;
   return FFTK_OK;
 }
 

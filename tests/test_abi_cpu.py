@@ -57,7 +57,10 @@ def test_status_strings(fk):
 @pytest.mark.parametrize(
     "shape,dtype,want",
     [
-        ((6, 8, 8), 0, 2),
+        ((5, 8, 8), 0, 2),
+        ((10, 8, 8), 0, 2),
+        ((8, 8, 6), 0, 2),
+        ((6144, 8, 12), 0, 2),
         ((8, 8, 1), 0, 2),
         ((8, 8192, 8), 0, 2),
         ((0, 8, 8), 0, 2),

@@ -172,6 +172,21 @@ def test_direct_coefficient_and_point_sums(oracle_mod):
 
 def test_rejects_bad_shapes(oracle_mod):
     with pytest.raises(RuntimeError):
-        oracle_mod.rfft3(np.zeros((6, 8, 8)))
+        oracle_mod.rfft3(np.zeros((5, 8, 8)))
+    with pytest.raises(RuntimeError):
+        oracle_mod.rfft3(np.zeros((8, 9, 8)))
     with pytest.raises(RuntimeError):
         oracle_mod.rfft3(np.zeros((8, 8, 1)))
+
+
+@pytest.mark.parametrize("shape", [(6, 12, 24), (3, 8, 6), (12, 6, 48), (24, 3, 12)])
+def test_radix3_lengths_match_numpy_and_brute_force(oracle_mod, shape):
+    # dimensions 3 * 2^m (the paper's 768, 1536, 3072 grids): numpy's FFT and
+    # the three explicit DFT matrices
+    f = synth.uniform_pm1(9, 0, shape).astype(np.float64)
+    F = oracle_mod.rfft3(f)
+    assert np.max(np.abs(F - np.fft.rfftn(f) / f.size)) < 1e-15
+    assert np.max(np.abs(F - _direct_rfft3(f))) < 1e-15
+    assert np.max(np.abs(oracle_mod.irfft3(F, shape[2]) - f)) < 1e-14
+    for (a, b, c) in [(0, 0, 0), (1, 2, 3), (shape[0] - 1, shape[1] - 1, shape[2] // 2)]:
+        assert abs(oracle_mod.rfft3_coeff(f.astype(np.float32), a, b, c) - F[a, b, c]) < 1e-14
