@@ -58,6 +58,8 @@ def lib():
             L.oracle_ns_step_rk4.argtypes = [vp, c.c_int, vp, c.c_int]
             L.oracle_rbc_rhs.argtypes = [vp, vp, c.c_int]
             L.oracle_rbc_step.argtypes = [vp, c.c_int, c.c_double, c.c_double, c.c_double, c.c_int, c.c_int]
+            L.oracle_rbc_sff_rhs.argtypes = [vp, vp, c.c_int]
+            L.oracle_rbc_sff_step.argtypes = [vp, c.c_int, c.c_double, c.c_double, c.c_double, c.c_int, c.c_int]
             L.oracle_diag.argtypes = [vp, c.c_int, c.c_double, dp, dp, vp, c.c_int]
             L.oracle_transfer.argtypes = [vp, vp, c.c_int]
             L.oracle_transfer.restype = c.c_double
@@ -267,6 +269,21 @@ def rbc_step(state, Ra, Pr, dt, nsteps=1, scheme=1) -> np.ndarray:
     st = np.array(state, dtype=np.complex128, order="C", copy=True)
     _check(lib().oracle_rbc_step(_ptr(st), st.shape[1], float(Ra), float(Pr), float(dt), nsteps, scheme),
            "rbc_step")
+    return st
+
+
+def rbc_sff_rhs(state) -> np.ndarray:
+    """(N_u, N_theta) between free-slip plates: u_x, theta sine along x, u_y, u_z cosine."""
+    st = np.ascontiguousarray(state, dtype=np.complex128)
+    out = np.empty_like(st)
+    _check(lib().oracle_rbc_sff_rhs(_ptr(st), _ptr(out), st.shape[1]), "rbc_sff_rhs")
+    return out
+
+
+def rbc_sff_step(state, Ra, Pr, dt, nsteps=1, scheme=1) -> np.ndarray:
+    st = np.array(state, dtype=np.complex128, order="C", copy=True)
+    _check(lib().oracle_rbc_sff_step(_ptr(st), st.shape[1], float(Ra), float(Pr), float(dt), nsteps, scheme),
+           "rbc_sff_step")
     return st
 
 

@@ -891,6 +891,189 @@ int oracle_rbc_step(cplx *st, int n, double Ra, double Pr, double dt, int nsteps
   return 0;
 }
 
+/* ------------------------------------------ Rayleigh-Benard (SFF plates) -- */
+/* Eqs. (12)-(14) between free-slip, isothermal plates (the SFF basis,
+ * Sec. 2.2): the wall-normal axis is x on [0, pi] (the n points of the sine
+ * and cosine bases), y and z are 2 pi-periodic, gravity along x.  State
+ * s[4][n][n][n/2+1]: u_x and theta in the sine basis along x (index a is
+ * k_x = a + 1: u_x = theta = 0 on the plates), u_y, u_z in the cosine basis
+ * (index a is k_x = a: d_x u_y = d_x u_z = 0 on the plates); Fourier along
+ * y and z as everywhere.  Right-hand side without diffusion:
+ *   N_u = P[u x omega + theta x],  N_theta = -div(u theta) + u_x,
+ * 2/3-truncated (3 k_x < 2n on the wall-normal axis, 3|k| < n on the
+ * periodic ones); P subtracts the gradient of a cosine-basis pressure. */
+static const int kSFF_S[3] = {ORACLE_SINE, ORACLE_FOURIER, ORACLE_FOURIER};
+static const int kSFF_C[3] = {ORACLE_COSINE, ORACLE_FOURIER, ORACLE_FOURIER};
+
+static int sff_kept(long kx, long ky, long kz, long n) { return 3 * kx < 2 * n && 3 * labs(ky) < n && 3 * kz < n; }
+
+/* zero the modes outside the truncated set; sine fields index a is k_x = a + 1 */
+static void sff_dealias(cplx *f, int sine, int n) {
+  const long N = n, HZ = n / 2 + 1;
+  for (long a = 0; a < N; a++)
+    for (long b = 0; b < N; b++)
+      for (long c = 0; c < HZ; c++)
+        if (!sff_kept(sine ? a + 1 : a, kxy(b, N), c, N)) f[(a * N + b) * HZ + c] = 0;
+}
+
+int oracle_rbc_sff_rhs(const cplx *st, cplx *out, int n) {
+  if (!is_pow2(n) || n < 2) return -1;
+  const long N = n, HZ = n / 2 + 1, M = N * N * HZ, R = N * N * N;
+  const cplx *ux = st, *uy = st + M, *uz = st + 2 * M, *th = st + 3 * M;
+  cplx *w = (cplx *)malloc(sizeof(cplx) * 3 * (size_t)M); /* omega_x (cos), omega_y, omega_z (sin) */
+  double *r = (double *)malloc(sizeof(double) * 7 * (size_t)R);
+  double *pr = (double *)malloc(sizeof(double) * (size_t)R);
+  cplx *ph = (cplx *)malloc(sizeof(cplx) * 6 * (size_t)M);
+  if (!w || !r || !pr || !ph) return -2;
+  /* omega = curl u in the mixed basis: d_x of a sine coefficient s_k is the
+   * cosine coefficient k s_k, d_x of a cosine coefficient c_k the sine
+   * coefficient -k c_k */
+  for (long a = 0; a < N; a++)
+    for (long b = 0; b < N; b++)
+      for (long c = 0; c < HZ; c++) {
+        long idx = (a * N + b) * HZ + c, up = ((a + 1) * N + b) * HZ + c;
+        double ky = (double)kder(kxy(b, N), N), kz = (double)kder(c, N), kxs = (double)(a + 1);
+        w[idx] = I * ky * uz[idx] - I * kz * uy[idx];                       /* cos: d_y u_z - d_z u_y */
+        cplx uzc = (a + 1 < N) ? uz[up] : 0, uyc = (a + 1 < N) ? uy[up] : 0; /* cosine mode k_x = a + 1 */
+        w[M + idx] = I * kz * ux[idx] + kxs * uzc;                          /* sin: d_z u_x - d_x u_z */
+        w[2 * M + idx] = -kxs * uyc - I * ky * ux[idx];                     /* sin: d_x u_y - d_y u_x */
+      }
+  /* real space: r = u_x, u_y, u_z, omega_x, omega_y, omega_z, theta */
+  oracle_itransform3(ux, r, n, n, n, kSFF_S);
+  oracle_itransform3(uy, r + R, n, n, n, kSFF_C);
+  oracle_itransform3(uz, r + 2 * R, n, n, n, kSFF_C);
+  oracle_itransform3(w, r + 3 * R, n, n, n, kSFF_C);
+  oracle_itransform3(w + M, r + 4 * R, n, n, n, kSFF_S);
+  oracle_itransform3(w + 2 * M, r + 5 * R, n, n, n, kSFF_S);
+  oracle_itransform3(th, r + 6 * R, n, n, n, kSFF_S);
+  /* products back to the mixed basis: (u x omega)_x, u_y theta, u_z theta in
+   * sine; (u x omega)_y, (u x omega)_z, u_x theta in cosine */
+  const double *rx = r, *ry = r + R, *rz = r + 2 * R, *wx = r + 3 * R, *wy = r + 4 * R, *wz = r + 5 * R,
+               *tt = r + 6 * R;
+  for (int q = 0; q < 6; q++) {
+    for (long x = 0; x < R; x++) {
+      double v = 0.0;
+      switch (q) {
+        case 0: v = ry[x] * wz[x] - rz[x] * wy[x]; break;
+        case 1: v = rz[x] * wx[x] - rx[x] * wz[x]; break;
+        case 2: v = rx[x] * wy[x] - ry[x] * wx[x]; break;
+        case 3: v = rx[x] * tt[x]; break;
+        case 4: v = ry[x] * tt[x]; break;
+        default: v = rz[x] * tt[x]; break;
+      }
+      pr[x] = v;
+    }
+    const int sine = (q == 0 || q == 4 || q == 5);
+    oracle_transform3(pr, ph + q * M, n, n, n, sine ? kSFF_S : kSFF_C);
+  }
+  /* v = u x omega + theta x, then v - grad p with the cosine pressure
+   * p = -div v / k^2 (div v in the cosine basis: k_x v_x + i k_y v_y + i k_z v_z) */
+  cplx *vx = out, *vy = out + M, *vz = out + 2 * M;
+  for (long i = 0; i < M; i++) {
+    vx[i] = ph[i] + th[i];
+    vy[i] = ph[M + i];
+    vz[i] = ph[2 * M + i];
+  }
+  for (long a = 0; a < N; a++)
+    for (long b = 0; b < N; b++)
+      for (long c = 0; c < HZ; c++) {
+        long idx = (a * N + b) * HZ + c;
+        double kx = (double)a, ky = (double)kxy(b, N), kz = (double)c;
+        double k2 = kx * kx + ky * ky + kz * kz;
+        if (k2 == 0.0) continue;
+        long sidx = ((a - 1) * N + b) * HZ + c; /* sine index of k_x = a */
+        cplx vxs = (a >= 1) ? vx[sidx] : 0;
+        cplx div = kx * vxs + I * ky * vy[idx] + I * kz * vz[idx];
+        cplx pc = -div / k2;
+        vy[idx] -= I * ky * pc;
+        vz[idx] -= I * kz * pc;
+        if (a >= 1) vx[sidx] += kx * pc; /* d_x p has the sine coefficient -k_x p */
+      }
+  /* the sine mode k_x = n has no cosine partner: it is outside the kept set */
+  /* N_theta = -(d_x(u_x theta) + d_y(u_y theta) + d_z(u_z theta)) + u_x */
+  for (long a = 0; a < N; a++)
+    for (long b = 0; b < N; b++)
+      for (long c = 0; c < HZ; c++) {
+        long idx = (a * N + b) * HZ + c, up = ((a + 1) * N + b) * HZ + c;
+        double ky = (double)kder(kxy(b, N), N), kz = (double)kder(c, N), kxs = (double)(a + 1);
+        cplx cxt = (a + 1 < N) ? ph[3 * M + up] : 0;
+        cplx div = -kxs * cxt + I * ky * ph[4 * M + idx] + I * kz * ph[5 * M + idx];
+        out[3 * M + idx] = -div + ux[idx];
+      }
+  sff_dealias(vx, 1, n);
+  sff_dealias(vy, 0, n);
+  sff_dealias(vz, 0, n);
+  sff_dealias(out + 3 * M, 1, n);
+  free(w);
+  free(r);
+  free(pr);
+  free(ph);
+  return 0;
+}
+
+/* nsteps of RK2 (scheme 0) or RK4 (scheme 1) for the SFF state, as
+ * oracle_rbc_step, with k^2 = k_x^2 + k_y^2 + k_z^2 and k_x per field's basis. */
+int oracle_rbc_sff_step(cplx *st, int n, double Ra, double Pr, double dt, int nsteps, int scheme) {
+  if (!is_pow2(n) || n < 2 || Ra <= 0.0 || Pr <= 0.0 || (scheme != 0 && scheme != 1)) return -1;
+  const long N = n, HZ = n / 2 + 1, M = N * N * HZ;
+  const double nu = sqrt(Pr / Ra), kappa = 1.0 / sqrt(Ra * Pr);
+  cplx *us = (cplx *)malloc(sizeof(cplx) * 4 * (size_t)M);
+  cplx *nh = (cplx *)malloc(sizeof(cplx) * 4 * (size_t)M);
+  cplx *acc = (cplx *)malloc(sizeof(cplx) * 4 * (size_t)M);
+  double *E = (double *)malloc(sizeof(double) * 4 * (size_t)M);
+  double *H = (double *)malloc(sizeof(double) * 4 * (size_t)M);
+  if (!us || !nh || !acc || !E || !H) return -2;
+  for (int f = 0; f < 4; f++) {
+    const int sine = (f == 0 || f == 3);
+    const double d = (f == 3) ? kappa : nu;
+    for (long a = 0; a < N; a++)
+      for (long b = 0; b < N; b++)
+        for (long c = 0; c < HZ; c++) {
+          double kx = (double)(sine ? a + 1 : a), ky = (double)kxy(b, N), kz = (double)c;
+          double k2 = kx * kx + ky * ky + kz * kz;
+          long i = f * M + (a * N + b) * HZ + c;
+          E[i] = exp(-d * k2 * dt);
+          H[i] = exp(-d * k2 * dt * 0.5);
+        }
+  }
+  for (int s = 0; s < nsteps; s++) {
+    int rc = oracle_rbc_sff_rhs(st, nh, n);
+    if (rc) return rc;
+    if (scheme == 0) {
+      for (long i = 0; i < 4 * M; i++) us[i] = E[i] * (st[i] + dt * nh[i]);
+      rc = oracle_rbc_sff_rhs(us, nh, n);
+      if (rc) return rc;
+      for (long i = 0; i < 4 * M; i++) st[i] = 0.5 * E[i] * st[i] + 0.5 * (us[i] + dt * nh[i]);
+      continue;
+    }
+    for (long i = 0; i < 4 * M; i++) {
+      acc[i] = E[i] * st[i] + dt / 6.0 * E[i] * nh[i];
+      us[i] = H[i] * (st[i] + 0.5 * dt * nh[i]);
+    }
+    rc = oracle_rbc_sff_rhs(us, nh, n);
+    if (rc) return rc;
+    for (long i = 0; i < 4 * M; i++) {
+      acc[i] += dt / 3.0 * H[i] * nh[i];
+      us[i] = H[i] * st[i] + 0.5 * dt * nh[i];
+    }
+    rc = oracle_rbc_sff_rhs(us, nh, n);
+    if (rc) return rc;
+    for (long i = 0; i < 4 * M; i++) {
+      acc[i] += dt / 3.0 * H[i] * nh[i];
+      us[i] = E[i] * st[i] + dt * H[i] * nh[i];
+    }
+    rc = oracle_rbc_sff_rhs(us, nh, n);
+    if (rc) return rc;
+    for (long i = 0; i < 4 * M; i++) st[i] = acc[i] + dt / 6.0 * nh[i];
+  }
+  free(us);
+  free(nh);
+  free(acc);
+  free(E);
+  free(H);
+  return 0;
+}
+
 /* Shell index K = nint(|k|); |k| is never a half-integer for integer k. */
 static long shell_of(long k2) { return (long)floor(sqrt((double)k2) + 0.5); }
 

@@ -95,6 +95,13 @@ int oracle_ns_step_rk4(ocplx *uhat, int n, const oracle_ns_params *p, int nsteps
  * to the integrating factors of the stepper; scheme 0 RK2, 1 RK4). */
 int oracle_rbc_rhs(const ocplx *s, ocplx *out, int n);
 int oracle_rbc_step(ocplx *s, int n, double Ra, double Pr, double dt, int nsteps, int scheme);
+/* The same between free-slip, isothermal plates (SFF, Eq. (14)): wall-normal
+ * axis x on [0, pi] with gravity along it; u_x, theta in the sine basis
+ * along x (index a: k_x = a + 1), u_y, u_z in the cosine basis (k_x = a);
+ *   N_u = P[u x omega + theta x],  N_theta = -div(u theta) + u_x,
+ * truncated to 3 k_x < 2n, 3|k_y| < n, 3|k_z| < n. */
+int oracle_rbc_sff_rhs(const ocplx *s, ocplx *out, int n);
+int oracle_rbc_sff_step(ocplx *s, int n, double Ra, double Pr, double dt, int nsteps, int scheme);
 
 /* Diagnostics: E = 1/2 sum w |u|^2, eps = nu sum w k^2 |u|^2,
  * EK[K] = 1/2 sum_{nint|k| = K} w |u|^2 for K = 0..kmax (modes beyond kmax dropped). */
