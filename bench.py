@@ -802,11 +802,12 @@ def run_schemes(n: int, steps: int):
 
 
 def run_rbc(n: int, steps: int):
-    """Rayleigh-Benard convection at n^3 (FFF, Ra = 1e8, Pr = 1, dt = 1e-3):
-    the random-phase velocity of the decaying workload with theta = u_z,
-    stepped with RK4 (the paper's scheme: 52 transforms per step) and with
-    RK2, CUDA events over `steps` steps after 3.  Prints one JSON line with
-    steps/s and the time per transform."""
+    """Rayleigh-Benard convection at n^3 (Ra = 1e8, Pr = 1, dt = 1e-3): the
+    random-phase velocity of the decaying workload with theta = u_z, stepped
+    on the periodic cube with RK4 (the paper's scheme: 52 transforms per step)
+    and RK2, and between free-slip plates (the same coefficients read in the
+    plates' bases) with RK4; CUDA events over `steps` steps after 3.  Prints
+    one JSON line with steps/s and the time per transform."""
     import torch
 
     import paper_1805_07801_gb300 as fk
@@ -824,14 +825,18 @@ def run_rbc(n: int, steps: int):
     s0[3].copy_(s0[2])
     del nr
     out = {}
-    for name, scheme, ntr in (("rk4", fk.TARANG_RK4, 52), ("rk2", fk.TARANG_RK2, 26)):
+    for name, scheme, ntr, basis in (("rk4", fk.TARANG_RK4, 52, fk.TARANG_RBC_FFF),
+                                     ("rk2", fk.TARANG_RK2, 26, fk.TARANG_RBC_FFF),
+                                     ("sff_rk4", fk.TARANG_RK4, 52, fk.TARANG_RBC_SFF)):
         s = s0.clone()
-        fk.tarang_rbc_step(plan, s.data_ptr(), 1e8, 1.0, 1e-3, 3, scheme, st)
+        if basis == fk.TARANG_RBC_SFF:  # the same coefficients read in the plates' bases, truncated to them
+            s[:, (2 * n - 1) // 3:] = 0
+        fk.tarang_rbc_step(plan, s.data_ptr(), 1e8, 1.0, 1e-3, 3, scheme, st, basis=basis)
         torch.cuda.synchronize(dev)
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record()
-        fk.tarang_rbc_step(plan, s.data_ptr(), 1e8, 1.0, 1e-3, steps, scheme, st)
+        fk.tarang_rbc_step(plan, s.data_ptr(), 1e8, 1.0, 1e-3, steps, scheme, st, basis=basis)
         b.record()
         b.synchronize()
         ms = a.elapsed_time(b) / steps

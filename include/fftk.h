@@ -203,25 +203,37 @@ fftk_status tarang_ns_step(fftk_plan p, void *uhat, const tarang_params *prm, in
                            double *diag_host, void *cuda_stream);
 
 /* Rayleigh-Benard convection (Sec. 2.2, Eqs. (12)-(13) in their
- * non-dimensional form; FFF basis: the 2 pi-periodic cube, gravity along z):
- *   d_t u + (u.grad) u = -grad sigma + theta z + sqrt(Pr/Ra) lap u,
- *   d_t theta + (u.grad) theta = u_z + lap theta / sqrt(Ra Pr).
- * State: float2 [4][n][n][n/2+1] = (u_x, u_y, u_z, theta) on the 2/3 set
- * (zero elsewhere, as for the velocity of tarang_ns_step).  The right-hand
- * side without diffusion, N_u = P[F(u x omega) + theta z] and
- * N_theta = -i k . F(u theta) + u_z, is evaluated through the plan's own
- * transforms: seven inverse (u, omega, theta) and six forward (u x omega,
- * u theta) per stage, the paper's 52 transforms per RK4 step (Sec. 7).
+ * non-dimensional form):
+ *   d_t u + (u.grad) u = -grad sigma + theta g + sqrt(Pr/Ra) lap u,
+ *   d_t theta + (u.grad) theta = u.g + lap theta / sqrt(Ra Pr),
+ * g the unit vector against gravity, on one of two bases:
+ *   TARANG_RBC_FFF  the 2 pi-periodic cube, g = z;
+ *   TARANG_RBC_SFF  free-slip, isothermal plates (Eq. (14)) at x = 0 and pi,
+ *                   g = x, y and z 2 pi-periodic: u_x and theta in the sine
+ *                   basis along x (storage index a is k_x = a + 1), u_y and
+ *                   u_z in the cosine basis (index a is k_x = a), on the
+ *                   sine/cosine grid of fftk_forward (n points of [0, pi]).
+ * State: float2 [4][n][n][n/2+1] = (u_x, u_y, u_z, theta), truncated (FFF:
+ * the 2/3 set of tarang_ns_step; SFF: 3 k_x < 2n, 3|k_y| < n, 3 k_z < n),
+ * zero elsewhere.  The right-hand side without diffusion,
+ * N_u = P[u x omega + theta g] and N_theta = -div(u theta) + u.g, goes
+ * through the plan's own transforms: seven inverse (u, omega, theta) and six
+ * forward (u x omega, u theta) per stage, the paper's 52 transforms per RK4
+ * step (Sec. 7); between plates the x passes are sine/cosine passes.
  * Device memory: 18 more fields (allocated on first use, kept by the plan). */
+enum { TARANG_RBC_FFF = 0, TARANG_RBC_SFF = 1 };
+
 typedef struct {
   double Ra;  /* Rayleigh number */
   double Pr;  /* Prandtl number */
   double dt;  /* time step */
   int scheme; /* TARANG_RK2 or TARANG_RK4, integrating factors exp(-nu k^2 dt), exp(-kappa k^2 dt) */
+  int basis;  /* TARANG_RBC_FFF or TARANG_RBC_SFF */
 } tarang_rbc_params;
 
-/* out = (N_u, N_theta), float2 [4][n][n][n/2+1], distinct from state. */
-fftk_status tarang_rbc_rhs(fftk_plan p, const void *state, void *out, void *cuda_stream);
+/* out = (N_u, N_theta), float2 [4][n][n][n/2+1], distinct from state;
+ * basis TARANG_RBC_FFF or TARANG_RBC_SFF. */
+fftk_status tarang_rbc_rhs(fftk_plan p, int basis, const void *state, void *out, void *cuda_stream);
 
 /* nsteps steps in place, in the forms of tarang_ns_step (u and theta each
  * with its own factor).  Asynchronous.  INVALID_ARG for non-positive or

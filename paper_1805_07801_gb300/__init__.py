@@ -61,6 +61,7 @@ class tarang_params(ctypes.Structure):
 
 
 TARANG_RK2, TARANG_RK4 = 0, 1
+TARANG_RBC_FFF, TARANG_RBC_SFF = 0, 1
 
 
 class tarang_rbc_params(ctypes.Structure):
@@ -69,6 +70,7 @@ class tarang_rbc_params(ctypes.Structure):
         ("Pr", ctypes.c_double),
         ("dt", ctypes.c_double),
         ("scheme", ctypes.c_int),
+        ("basis", ctypes.c_int),
     ]
 
 
@@ -98,7 +100,7 @@ def lib() -> ctypes.CDLL:
             "tarang_diag_kmax": ([vp], i),
             "tarang_diag": ([vp, vp, d, vp, vp], i),
             "tarang_diag_noalloc": ([i, vp, d, vp, vp], i),
-            "tarang_rbc_rhs": ([vp, vp, vp, vp], i),
+            "tarang_rbc_rhs": ([vp, i, vp, vp, vp], i),
             "tarang_rbc_step": ([vp, vp, c.POINTER(tarang_rbc_params), i, vp], i),
             "fftk_forward": ([vp, vp, vp, vp, i, vp], i),
             "fftk_inverse": ([vp, vp, vp, vp, i, vp], i),
@@ -216,13 +218,14 @@ def tarang_ns_step(plan: int, uhat_ptr, params: tarang_params, nsteps: int = 1, 
     return vals[0], vals[1], vals[2:]
 
 
-def tarang_rbc_rhs(plan: int, state_ptr, out_ptr, stream=0) -> None:
-    _check(lib().tarang_rbc_rhs(_vp(plan), _vp(state_ptr), _vp(out_ptr), _vp(stream)), "tarang_rbc_rhs")
+def tarang_rbc_rhs(plan: int, state_ptr, out_ptr, stream=0, basis: int = TARANG_RBC_FFF) -> None:
+    _check(lib().tarang_rbc_rhs(_vp(plan), int(basis), _vp(state_ptr), _vp(out_ptr), _vp(stream)),
+           "tarang_rbc_rhs")
 
 
 def tarang_rbc_step(plan: int, state_ptr, Ra: float, Pr: float, dt: float, nsteps: int = 1,
-                    scheme: int = TARANG_RK4, stream=0) -> None:
-    prm = tarang_rbc_params(float(Ra), float(Pr), float(dt), int(scheme))
+                    scheme: int = TARANG_RK4, stream=0, basis: int = TARANG_RBC_FFF) -> None:
+    prm = tarang_rbc_params(float(Ra), float(Pr), float(dt), int(scheme), int(basis))
     _check(lib().tarang_rbc_step(_vp(plan), _vp(state_ptr), ctypes.byref(prm), int(nsteps), _vp(stream)),
            "tarang_rbc_step")
 

@@ -1,4 +1,5 @@
-// Rayleigh-Benard convection on the FFF basis through the plan's transforms.
+// Rayleigh-Benard convection through the plan's transforms: the periodic
+// cube (FFF basis) and free-slip, isothermal plates (SFF basis).
 #include <cmath>
 #include <mutex>
 #include <new>
@@ -46,7 +47,9 @@ static fftk_status rbc_ensure(fftk_plan p) {
   if (!r) return FFTK_ERR_OOM;
   const NSGeom g = s->g;
   const size_t fb = sizeof(float2) * (size_t)g.M, rb = sizeof(float) * (size_t)g.n * g.n * g.n;
-  r->tab_len = 3 * g.kd * g.kd + 1;
+  // |k|^2 up to 3 kd^2 on the cube, (2n-1)/3 squared + 2 kd^2 between plates
+  const int kxs = (2 * g.n - 1) / 3;
+  r->tab_len = kxs * kxs + 2 * g.kd * g.kd + 1;
   cudaError_t e = cudaMalloc(&r->w7, 7 * fb);
   if (e == cudaSuccess) e = cudaMalloc(&r->r7, 7 * rb);
   if (e == cudaSuccess) e = cudaMalloc(&r->s1, 4 * fb);
@@ -202,14 +205,174 @@ __global__ void k_rbc_update(const float2* __restrict__ w7, const float2* x, con
   }
 }
 
+// ---- free-slip plates (SFF): wall-normal axis x on [0, pi], gravity along x.
+// u_x and theta are sine series along x (storage index a is k_x = a + 1),
+// u_y and u_z cosine series (index a is k_x = a); y and z Fourier.  d_x of a
+// sine coefficient s_k is the cosine coefficient k s_k, d_x of a cosine
+// coefficient c_k the sine coefficient -k c_k.  Kept: 3 k_x < 2n, 3|k_y| < n,
+// 3 k_z < n.  A thread owns the wavenumber triple (k_x = a, k_y, k_z): the
+// cosine entry at index a and the sine entry at index a - 1.
+
+__device__ __forceinline__ bool sff_kept(int kx, int b, int c, const NSGeom& g) {
+  return 3 * kx < 2 * g.n && kept_xy(b, g.n, g.kd) && c < g.kc;
+}
+
+// w7 = [u_x, omega_y, omega_z, theta | u_y, u_z, omega_x]: sine group, then
+// cosine group (each contiguous, for one batched transform per group)
+__global__ void k_rbc_sff_prep(const float2* __restrict__ x, float2* __restrict__ w7, NSGeom g) {
+  const long long M = g.M, rowa = (long long)g.n * g.h1;  // one step of the x index
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < M;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(idx % g.h1);
+    const long long ab = idx / g.h1;
+    const int b = (int)(ab % g.n), a = (int)(ab / g.n);
+    const int kb = kwav(b, g.n);
+    const float ky = (2 * abs(kb) == g.n) ? 0.f : (float)kb, kz = (2 * c == g.n) ? 0.f : (float)c;
+    const float2 uy = x[idx + M], uz = x[idx + 2 * M];
+    // cosine entries at index a
+    w7[idx + 4 * M] = uy;
+    w7[idx + 5 * M] = uz;
+    w7[idx + 6 * M] = csub(mul_i(uz, ky), mul_i(uy, kz));  // omega_x = d_y u_z - d_z u_y
+    // sine entries of k_x = a at index a - 1; index n - 1 (k_x = n, no cosine partner) by a = 0
+    const long long sidx = a >= 1 ? idx - rowa : idx + (long long)(g.n - 1) * rowa;
+    const float kx = a >= 1 ? (float)a : 0.f;
+    const float2 ux = x[sidx], th = x[sidx + 3 * M];
+    const float2 uyc = a >= 1 ? uy : make_float2(0.f, 0.f), uzc = a >= 1 ? uz : make_float2(0.f, 0.f);
+    w7[sidx] = ux;
+    w7[sidx + M] = cadd(mul_i(ux, kz), cscale(uzc, kx));      // omega_y = d_z u_x - d_x u_z
+    w7[sidx + 2 * M] = csub(cscale(uyc, -kx), mul_i(ux, ky));  // omega_z = d_x u_y - d_y u_x
+    w7[sidx + 3 * M] = th;
+  }
+}
+
+// r7 = [u_x, omega_y, omega_z, theta, u_y, u_z, omega_x] -> in place
+// [(u x omega)_x, u_y theta, u_z theta | (u x omega)_y, (u x omega)_z, u_x theta]:
+// the sine-parity products first, then the cosine-parity ones
+__global__ void k_rbc_sff_products(float* __restrict__ r7, long long R) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < R;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float ux = r7[i], wy = r7[R + i], wz = r7[2 * R + i], th = r7[3 * R + i];
+    const float uy = r7[4 * R + i], uz = r7[5 * R + i], wx = r7[6 * R + i];
+    r7[i] = uy * wz - uz * wy;
+    r7[R + i] = uy * th;
+    r7[2 * R + i] = uz * th;
+    r7[3 * R + i] = uz * wx - ux * wz;
+    r7[4 * R + i] = ux * wy - uy * wx;
+    r7[5 * R + i] = ux * th;
+  }
+}
+
+// the stage update of one field entry i (the modes of ns_mode_update)
+__device__ __forceinline__ void rbc_entry_update(long long i, float2 n, float2 E, float2 H, float dt, int mode,
+                                                 const float2* u0, const float2* s1, float2* acc, float2* out) {
+  if (mode == NS_RHS) {
+    out[i] = n;
+  } else if (mode == NS_STAGE1) {
+    const float2 v = u0[i];
+    out[i] = mul_pair(make_float2(v.x + dt * n.x, v.y + dt * n.y), E);
+  } else if (mode == NS_STAGE2) {
+    const float2 ea = mul_pair(u0[i], E), b1 = s1[i];
+    out[i] = make_float2(0.5f * (ea.x + (b1.x + dt * n.x)), 0.5f * (ea.y + (b1.y + dt * n.y)));
+  } else if (mode == NS_RK4_4) {
+    const float2 ac = acc[i];
+    out[i] = make_float2(fmaf(dt / 6.f, n.x, ac.x), fmaf(dt / 6.f, n.y, ac.y));
+  } else {
+    const float2 v = u0[i];
+    const float2 ea = mul_pair(v, E), ha = mul_pair(v, H), hn = mul_pair(n, H);
+    if (mode == NS_RK4_1) {
+      const float2 en = mul_pair(n, E);
+      acc[i] = make_float2(fmaf(dt / 6.f, en.x, ea.x), fmaf(dt / 6.f, en.y, ea.y));
+      out[i] = mul_pair(make_float2(v.x + 0.5f * dt * n.x, v.y + 0.5f * dt * n.y), H);
+    } else {
+      const float2 ac = acc[i];
+      acc[i] = make_float2(fmaf(dt / 3.f, hn.x, ac.x), fmaf(dt / 3.f, hn.y, ac.y));
+      out[i] = (mode == NS_RK4_2) ? make_float2(fmaf(0.5f * dt, n.x, ha.x), fmaf(0.5f * dt, n.y, ha.y))
+                                  : make_float2(fmaf(dt, hn.x, ea.x), fmaf(dt, hn.y, ea.y));
+    }
+  }
+}
+
+// w7 (spectra): [(u x omega)_x, (u_y theta), (u_z theta) in sine | (u x omega)_y,
+// (u x omega)_z, (u_x theta) in cosine].  v = u x omega + theta x, minus the
+// gradient of the cosine pressure p = -div v / k^2; N_theta = -div(u theta) + u_x.
+__global__ void k_rbc_sff_update(const float2* __restrict__ w7, const float2* x, const float2* u0, float2* s1,
+                                 float2* acc, float2* out, NSGeom g, RBCUpdate upd, int mode) {
+  const long long M = g.M, rowa = (long long)g.n * g.h1;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < M;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(idx % g.h1);
+    const long long ab = idx / g.h1;
+    const int b = (int)(ab % g.n), a = (int)(ab / g.n);
+    if (!sff_kept(a, b, c, g)) continue;
+    const int ky = kwav(b, g.n), kz = c, kx = a;
+    const int k2 = kx * kx + ky * ky + kz * kz;
+    const float fkx = (float)kx, fky = (float)ky, fkz = (float)kz;
+    const bool has_s = a >= 1;  // the sine entry of k_x = a (index a - 1)
+    const long long sidx = idx - rowa;
+    // velocity
+    float2 vx = make_float2(0.f, 0.f);
+    if (has_s) vx = cadd(w7[sidx], x[sidx + 3 * M]);  // (u x omega)_x + theta
+    float2 vy = w7[idx + 3 * M], vz = w7[idx + 4 * M];
+    if (k2 == 0) {
+      vy = vz = make_float2(0.f, 0.f);
+    } else {
+      const float inv = 1.f / (float)k2;
+      // div v = k_x v_x + i k_y v_y + i k_z v_z (cosine); p = -div / k^2
+      const float2 dv = make_float2(fkx * vx.x - fky * vy.y - fkz * vz.y, fkx * vx.y + fky * vy.x + fkz * vz.x);
+      const float2 pc = make_float2(-dv.x * inv, -dv.y * inv);
+      vy = csub(vy, mul_i(pc, fky));
+      vz = csub(vz, mul_i(pc, fkz));
+      vx = cadd(vx, cscale(pc, fkx));
+    }
+    float2 nt = make_float2(0.f, 0.f);
+    if (has_s) {
+      // -(d_x (u_x theta) + d_y (u_y theta) + d_z (u_z theta)) + u_x
+      const float2 cx = w7[idx + 5 * M], sy = w7[sidx + M], sz = w7[sidx + 2 * M];
+      const float2 ux = x[sidx];
+      const float2 d = csub(cadd(mul_i(sy, fky), mul_i(sz, fkz)), cscale(cx, fkx));
+      nt = cadd(make_float2(-d.x, -d.y), ux);
+    }
+    const float dt = upd.dt;
+    const float2 Eu = __ldg(&upd.tab[k2]), Et = __ldg(&upd.tab[upd.tab_len + k2]);
+    const float2 Hu = __ldg(&upd.tab[2 * upd.tab_len + k2]), Ht = __ldg(&upd.tab[3 * upd.tab_len + k2]);
+    rbc_entry_update(idx + M, vy, Eu, Hu, dt, mode, u0, s1, acc, out);
+    rbc_entry_update(idx + 2 * M, vz, Eu, Hu, dt, mode, u0, s1, acc, out);
+    if (has_s) {
+      rbc_entry_update(sidx, vx, Eu, Hu, dt, mode, u0, s1, acc, out);
+      rbc_entry_update(sidx + 3 * M, nt, Et, Ht, dt, mode, u0, s1, acc, out);
+    }
+  }
+}
+
 // One right-hand side of the stage input x and the update of `mode`.
 static cudaError_t rbc_stage(fftk_plan p, const float2* x, const float2* u0, float2* out, const RBCUpdate& upd,
-                             int mode, cudaStream_t st) {
+                             int mode, int basis, cudaStream_t st) {
   NSWork* s = p->ns;
   RBCWork* r = s->rbc;
   const NSGeom g = s->g;
   const long long R = (long long)g.n * g.n * g.n;
   const unsigned grid = 152 * 8;
+  if (basis == TARANG_RBC_SFF) {
+    static const int kS[3] = {FFTK_SINE, FFTK_FOURIER, FFTK_FOURIER};
+    static const int kC[3] = {FFTK_COSINE, FFTK_FOURIER, FFTK_FOURIER};
+    {
+      LaunchScope ls(p, KK_AUX, st);
+      k_rbc_sff_prep<<<grid, 256, 0, st>>>(x, r->w7, g);
+    }
+    if (fftk_inverse(p, kS, r->w7, r->r7, 4, st) != FFTK_OK) return cudaErrorLaunchFailure;
+    if (fftk_inverse(p, kC, r->w7 + 4 * g.M, r->r7 + 4 * R, 3, st) != FFTK_OK) return cudaErrorLaunchFailure;
+    {
+      LaunchScope ls(p, KK_AUX, st);
+      k_rbc_sff_products<<<grid, 256, 0, st>>>(r->r7, R);
+    }
+    if (fftk_forward(p, kS, r->r7, r->w7, 3, st) != FFTK_OK) return cudaErrorLaunchFailure;
+    if (fftk_forward(p, kC, r->r7 + 3 * R, r->w7 + 3 * g.M, 3, st) != FFTK_OK) return cudaErrorLaunchFailure;
+    {
+      LaunchScope ls(p, KK_AUX, st);
+      k_rbc_sff_update<<<grid, 256, 0, st>>>(r->w7, x, u0, r->s1, r->acc, out, g, upd, mode);
+    }
+    return cudaGetLastError();
+  }
   {
     LaunchScope ls(p, KK_AUX, st);
     k_rbc_prep<<<grid, 256, 0, st>>>(x, r->w7, g);
@@ -238,10 +401,11 @@ static fftk_status rbc_check(fftk_plan p, const void* state) {
 
 using namespace fftk;
 
-extern "C" fftk_status tarang_rbc_rhs(fftk_plan p, const void* state, void* out, void* cuda_stream) {
+extern "C" fftk_status tarang_rbc_rhs(fftk_plan p, int basis, const void* state, void* out, void* cuda_stream) {
   fftk_status s = rbc_check(p, state);
   if (s != FFTK_OK) return s;
   if (!out || out == state || misaligned16(out)) return FFTK_ERR_INVALID_ARG;
+  if (basis != TARANG_RBC_FFF && basis != TARANG_RBC_SFF) return FFTK_ERR_INVALID_ARG;
   s = rbc_ensure(p);
   if (s != FFTK_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
@@ -250,7 +414,7 @@ extern "C" fftk_status tarang_rbc_rhs(fftk_plan p, const void* state, void* out,
   RBCUpdate upd{p->ns->rbc->tab, p->ns->rbc->tab_len, 0.f};
   if (e == cudaSuccess)
     e = rbc_stage(p, static_cast<const float2*>(state), static_cast<const float2*>(state),
-                  static_cast<float2*>(out), upd, NS_RHS, st);
+                  static_cast<float2*>(out), upd, NS_RHS, basis, st);
   return from_cuda(e);
 }
 
@@ -259,7 +423,8 @@ extern "C" fftk_status tarang_rbc_step(fftk_plan p, void* state, const tarang_rb
   fftk_status s = rbc_check(p, state);
   if (s != FFTK_OK) return s;
   if (!prm || nsteps < 0 || !(prm->Ra > 0.0) || !(prm->Pr > 0.0) || !(prm->dt > 0.0) || !std::isfinite(prm->Ra) ||
-      !std::isfinite(prm->Pr) || !std::isfinite(prm->dt) || (prm->scheme != TARANG_RK2 && prm->scheme != TARANG_RK4))
+      !std::isfinite(prm->Pr) || !std::isfinite(prm->dt) || (prm->scheme != TARANG_RK2 && prm->scheme != TARANG_RK4) ||
+      (prm->basis != TARANG_RBC_FFF && prm->basis != TARANG_RBC_SFF))
     return FFTK_ERR_INVALID_ARG;
   s = rbc_ensure(p);
   if (s != FFTK_OK) return s;
@@ -272,11 +437,12 @@ extern "C" fftk_status tarang_rbc_step(fftk_plan p, void* state, const tarang_rb
   cudaError_t e = cudaSuccess;
   for (int it = 0; it < nsteps && e == cudaSuccess; ++it) {
     if (prm->scheme == TARANG_RK2) {
-      e = rbc_stage(p, u, u, r->s1, upd, NS_STAGE1, st);
-      if (e == cudaSuccess) e = rbc_stage(p, r->s1, u, u, upd, NS_STAGE2, st);
+      e = rbc_stage(p, u, u, r->s1, upd, NS_STAGE1, prm->basis, st);
+      if (e == cudaSuccess) e = rbc_stage(p, r->s1, u, u, upd, NS_STAGE2, prm->basis, st);
     } else {
       for (int stage = 0; stage < 4 && e == cudaSuccess; ++stage)
-        e = rbc_stage(p, stage == 0 ? u : r->s1, u, stage == 3 ? u : r->s1, upd, NS_RK4_1 + stage, st);
+        e = rbc_stage(p, stage == 0 ? u : r->s1, u, stage == 3 ? u : r->s1, upd, NS_RK4_1 + stage, prm->basis,
+                      st);
     }
   }
   return from_cuda(e);
