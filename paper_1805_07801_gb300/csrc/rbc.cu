@@ -313,9 +313,9 @@ __global__ void k_rbc_sff_update(const float2* __restrict__ w7, const float2* x,
     float2 vx = make_float2(0.f, 0.f);
     if (has_s) vx = cadd(w7[sidx], x[sidx + 3 * M]);  // (u x omega)_x + theta
     float2 vy = w7[idx + 3 * M], vz = w7[idx + 4 * M];
-    if (k2 == 0) {
-      vy = vz = make_float2(0.f, 0.f);
-    } else {
+    // k = 0 (cosine k_x = 0, k_y = k_z = 0): a uniform flow along the plates,
+    // with no pressure gradient to remove
+    if (k2 != 0) {
       const float inv = 1.f / (float)k2;
       // div v = k_x v_x + i k_y v_y + i k_z v_z (cosine); p = -div / k^2
       const float2 dv = make_float2(fkx * vx.x - fky * vy.y - fkz * vz.y, fkx * vx.y + fky * vy.x + fkz * vz.x);
