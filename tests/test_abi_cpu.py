@@ -108,3 +108,35 @@ def test_kernel_names(fk):
     assert len(set(names)) == n
     assert fk.fftk_kernel_name(n) == ""
     assert "ns_z_product" in names
+
+
+def test_null_plan_calls_of_the_later_entry_points(fk):
+    L = fk.lib()
+    bad = fk.FFTK_ERR_INVALID_ARG
+    assert L.tarang_transfer(None, None, None, None, None) == bad
+    assert L.tarang_shell_transfer(None, None, 1, None, None, None) == bad
+    assert L.fftk_forward(None, None, None, None, 1, None) == bad
+    assert L.fftk_inverse(None, None, None, None, 1, None) == bad
+    assert L.tarang_rbc_rhs(None, 0, None, None, None) == bad
+    assert L.tarang_rbc_step(None, None, None, 1, None) == bad
+    names = [fk.fftk_kernel_name(k) for k in range(fk.fftk_kernel_kinds())]
+    assert "sc_fwd" in names and "sc_inv" in names
+
+
+def _struct_fields(name):
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    m = re.search(r"typedef struct \{([^{}]*)\}\s*" + name + r";", text)
+    assert m, name
+    fields = []
+    for decl in m.group(1).split(";"):
+        decl = decl.strip()
+        if decl:
+            fields.append(re.findall(r"([A-Za-z_][A-Za-z0-9_]*)\s*(?:\[[^\]]*\])?\s*$", decl)[0])
+    return fields
+
+
+@pytest.mark.parametrize("name", ["tarang_params", "tarang_rbc_params", "tarang_sgs_model"])
+def test_binding_structs_follow_the_header(fk, name):
+    # the ctypes mirrors must list the C fields in the same order
+    cls = getattr(fk, name)
+    assert [f[0] for f in cls._fields_] == _struct_fields(name)
