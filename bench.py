@@ -526,7 +526,8 @@ def run_case(case: str):
     ('fft16:' in the split-FP16 mode); 'mlp:<batch>' = two training steps;
     'sgs:<n>' = two unforced steps with the learned subgrid force;
     'transfer:<n>' = random-phase field + one energy transfer spectrum;
-    'bases:<nx>,<ny>,<nz>' = one SFF and one CCS forward + inverse pair."""
+    'bases:<nx>,<ny>,<nz>' = one SFF and one CCS forward + inverse pair;
+    'rbc:<n>' / 'rbcsff:<n>' = two RK4 convection steps on the cube / between plates."""
     import torch
 
     import paper_1805_07801_gb300 as fk
@@ -556,6 +557,20 @@ def run_case(case: str):
         for basis in ("SFF", "CCS"):
             fk.fftk_forward(plan, basis, x.data_ptr(), F.data_ptr(), 1, st)
             fk.fftk_inverse(plan, basis, F.data_ptr(), y.data_ptr(), 1, st)
+    elif kind in ("rbc", "rbcsff"):  # two RK4 convection steps (periodic cube or plates)
+        n = int(arg)
+        plan = fk.fftk_plan_create(n, n, n)
+        nr = torch.empty((3, n, n, n), dtype=torch.float32, device=dev)
+        for f in range(3):
+            fk.fftk_fill_normal(nr[f].data_ptr(), n**3, SEED, f, st)
+        s4 = torch.empty((4, n, n, n // 2 + 1, 2), dtype=torch.float32, device=dev)
+        fk.tarang_ic_random(plan, nr.data_ptr(), s4.data_ptr(), K0, E0, st)
+        del nr
+        s4[3].copy_(s4[2])
+        basis = fk.TARANG_RBC_SFF if kind == "rbcsff" else fk.TARANG_RBC_FFF
+        if basis == fk.TARANG_RBC_SFF:
+            s4[:, (2 * n - 1) // 3:] = 0
+        fk.tarang_rbc_step(plan, s4.data_ptr(), 1e8, 1.0, 1e-3, 2, fk.TARANG_RK4, st, basis=basis)
     elif kind == "transfer":
         n = int(arg)
         plan = fk.fftk_plan_create(n, n, n)
