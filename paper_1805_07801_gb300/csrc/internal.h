@@ -95,11 +95,13 @@ struct LaunchScope {
 
 // ---------------------------------------------------------- FFT passes -----
 // z pass, real -> half complex, lines of nz reals -> nz/2+1 complex (scale applied).
+// kc: only k_z < kc is written (r2c) or read, the rest taken as 0 (c2r);
+// the default keeps every k_z
 cudaError_t launch_z_r2c(fftk_plan p, const float* in, float2* out, long long nlines, float scale,
-                         cudaStream_t st);
+                         cudaStream_t st, int kc = 1 << 30);
 // z pass, half complex -> real (unnormalised); Im of the k=0 and k=nz/2 terms ignored.
 cudaError_t launch_z_c2r(fftk_plan p, const float2* in, float* out, long long nlines,
-                         cudaStream_t st);
+                         cudaStream_t st, int kc = 1 << 30);
 // strided c2c pass: array [P][L][Q], transform along L (element stride Q),
 // in may equal out.  sign = -1 forward, +1 inverse; output multiplied by scale.
 cudaError_t launch_scpass(fftk_plan p, int L, bool sine, int dir, const float2* in, float2* out, long long P,
@@ -112,6 +114,15 @@ cudaError_t launch_cpass3(fftk_plan p, int L, int sign, const float2* in, float2
 cudaError_t launch_z3(fftk_plan p, bool fwd, const void* in, void* out, long long nlines, float scale,
                       cudaStream_t st);
 bool is_pow2_or_3x(long long v);
+// strided passes restricted to the 2/3-rule set of an n^3 cube (fft_pruned.cu):
+// the inverse x pass reads the kept k_x rows of the kept (k_y, k_z) columns
+// and writes whole lines; the inverse y pass reads kept k_y rows of the kept
+// k_z columns of every x; the forward passes mirror them and write only kept
+// rows.  B batch elements of [n][n][n/2+1].
+cudaError_t launch_pruned_x(fftk_plan p, int sign, const float2* in, float2* out, long long B, float scale,
+                            cudaStream_t st);
+cudaError_t launch_pruned_y(fftk_plan p, int sign, const float2* in, float2* out, long long B, float scale,
+                            cudaStream_t st);
 cudaError_t launch_cpass(fftk_plan p, int L, int sign, const float2* in, float2* out, long long P,
                          long long Q, float scale, int kind, cudaStream_t st);
 

@@ -93,6 +93,8 @@ __global__ void k_rbc_prep(const float2* __restrict__ x, float2* __restrict__ w7
     const int c = (int)(idx % g.h1);
     const long long ab = idx / g.h1;
     const int b = (int)(ab % g.n), a = (int)(ab / g.n);
+    // the pruned inverse passes read only the kept modes
+    if (!(kept_xy(a, g.n, g.kd) && kept_xy(b, g.n, g.kd) && c < g.kc)) continue;
     const int ka = kwav(a, g.n), kb = kwav(b, g.n);
     const float kx = (2 * abs(ka) == g.n) ? 0.f : (float)ka, ky = (2 * abs(kb) == g.n) ? 0.f : (float)kb;
     const float kz = (2 * c == g.n) ? 0.f : (float)c;
@@ -377,12 +379,19 @@ static cudaError_t rbc_stage(fftk_plan p, const float2* x, const float2* u0, flo
     LaunchScope ls(p, KK_AUX, st);
     k_rbc_prep<<<grid, 256, 0, st>>>(x, r->w7, g);
   }
-  if (fftk_c2r(p, r->w7, r->r7, 7, st) != FFTK_OK) return cudaErrorLaunchFailure;
+  // inverse transforms restricted to the 2/3 set, in place in w7, then the z c2r
+  cudaError_t e = launch_pruned_x(p, +1, r->w7, r->w7, 7, 1.f, st);
+  if (e == cudaSuccess) e = launch_pruned_y(p, +1, r->w7, r->w7, 7, 1.f, st);
+  if (e == cudaSuccess) e = launch_z_c2r(p, r->w7, r->r7, 7LL * g.n * g.n, st, g.kc);
+  if (e != cudaSuccess) return e;
   {
     LaunchScope ls(p, KK_AUX, st);
     k_rbc_products<<<grid, 256, 0, st>>>(r->r7, R);
   }
-  if (fftk_r2c(p, r->r7, r->w7, 6, st) != FFTK_OK) return cudaErrorLaunchFailure;
+  e = launch_z_r2c(p, r->r7, r->w7, 6LL * g.n * g.n, 1.f, st, g.kc);
+  if (e == cudaSuccess) e = launch_pruned_y(p, -1, r->w7, r->w7, 6, 1.f, st);
+  if (e == cudaSuccess) e = launch_pruned_x(p, -1, r->w7, r->w7, 6, (float)(1.0 / ((double)R)), st);
+  if (e != cudaSuccess) return e;
   {
     LaunchScope ls(p, KK_AUX, st);
     k_rbc_update<<<grid, 256, 0, st>>>(r->w7, x, u0, r->s1, r->acc, out, g, upd, mode);
