@@ -125,6 +125,87 @@ __global__ void __launch_bounds__(SCfg<L>::THREADS, SCfg<L>::MINB)
   }
 }
 
+// The strided pass restricted to the 2/3-rule set of an n^3 spectrum
+// (L = n along x): columns are the kept (k_y, k_z) only (k_y rows 0..kd and
+// n-kd..n-1, k_z < kd + 1), the inverse reads only coefficient rows with
+// 3 k_x < 2n (sine row s is k_x = s + 1, cosine row s is k_x = s) and the
+// forward writes only those; B batch elements of [n][n][n/2+1].
+template <int L, bool SINE, int DIR>
+__global__ void __launch_bounds__(SCfg<L>::THREADS, SCfg<L>::MINB)
+    k_scpass_pr(const float2* in, float2* out, int ktiles, const float2* __restrict__ tw,
+                const float2* __restrict__ tq, float scale) {
+  using C = SCfg<L>;
+  constexpr int G = C::G, S = C::S, T = C::T;
+  constexpr long long H1 = L / 2 + 1, M = (long long)L * L * H1, Q = (long long)L * H1;
+  constexpr int KD = (L - 1) / 3, KC = KD + 1, NK = 2 * KD + 1;
+  extern __shared__ float2 smc[];
+  const int c = threadIdx.x % T, j = threadIdx.x / T;
+  const long long blk = blockIdx.x;
+  const long long bo = blk / ktiles;
+  const int kt = (int)(blk - bo * ktiles);
+  const long long b = bo / NK;
+  const int o = (int)(bo - b * NK);
+  const int ay = o <= KD ? o : L - (NK - o);
+  const int kz = kt * T + c;
+  const bool valid = kz < KC;
+  const long long base = b * M + (long long)ay * H1 + kz;
+  const ColX<T> xc{smc, c};
+  auto kept_row = [](int row) { return 3 * (SINE ? row + 1 : row) < 2 * L; };
+  float2 v[G];
+  if (DIR < 0) {
+#pragma unroll
+    for (int m = 0; m < G; ++m) {
+      const int r = j + m * S;
+      float2 x = valid ? in[base + (long long)mk_perm(r, L) * Q] : make_float2(0.f, 0.f);
+      if (SINE && r >= L / 2) x = make_float2(-x.x, -x.y);
+      v[m] = x;
+    }
+    fft_line<L, G, -1>(v, j, xc, tw);
+#pragma unroll
+    for (int m = 0; m < G; ++m) xc.st(j + m * S, v[m]);
+    xc.sync();
+    if (valid) {
+#pragma unroll
+      for (int m = 0; m < G; ++m) {
+        const int k = j + m * S;
+        const int row = SINE ? L - 1 - k : k;
+        if (!kept_row(row)) continue;
+        const float2 ck = mk_post(v[m], xc.ld((L - k) & (L - 1)), __ldg(&tq[k]));
+        out[base + (long long)row * Q] = cscale(ck, (k == 0 ? 0.5f : 1.f) * scale);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int m = 0; m < G; ++m) {
+      const int k = j + m * S;
+      const int row = SINE ? L - 1 - k : k;
+      float2 x = (valid && kept_row(row)) ? in[base + (long long)row * Q] : make_float2(0.f, 0.f);
+      if (k == 0) x = cscale(x, 2.f);
+      v[m] = x;
+      xc.st(k, x);
+    }
+    xc.sync();
+    float2 w[G];
+#pragma unroll
+    for (int m = 0; m < G; ++m) {
+      const int k = j + m * S;
+      const float2 cn = k == 0 ? make_float2(0.f, 0.f) : xc.ld(L - k);
+      w[m] = mk_pre(v[m], cn, __ldg(&tq[k]));
+    }
+    xc.sync();
+    fft_line<L, G, +1>(w, j, xc, tw);
+    if (valid) {
+#pragma unroll
+      for (int m = 0; m < G; ++m) {
+        const int r = j + m * S;
+        float2 x = w[m];
+        if (SINE && r >= L / 2) x = make_float2(-x.x, -x.y);
+        out[base + (long long)mk_perm(r, L) * Q] = cscale(x, scale);
+      }
+    }
+  }
+}
+
 // ------------------------------------------------- contiguous real pass --
 template <int N>
 struct SZCfg {
@@ -243,6 +324,25 @@ static cudaError_t scz_n(fftk_plan p, const float* in, float* out, long long nli
   return cudaGetLastError();
 }
 
+template <int L, bool SINE, int DIR>
+static cudaError_t scpass_pr_l(fftk_plan p, const float2* in, float2* out, long long B, float scale,
+                               cudaStream_t st) {
+  using C = SCfg<L>;
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [] {
+    attr_err = cudaFuncSetAttribute(k_scpass_pr<L, SINE, DIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)C::SMEM);
+  });
+  if (attr_err != cudaSuccess) return attr_err;
+  constexpr int KD = (L - 1) / 3, KC = KD + 1;
+  const int ktiles = (KC + C::T - 1) / C::T;
+  LaunchScope ls(p, DIR < 0 ? KK_SC_FWD : KK_SC_INV, st);
+  k_scpass_pr<L, SINE, DIR><<<(unsigned)(B * (2 * KD + 1) * ktiles), C::THREADS, C::SMEM, st>>>(
+      in, out, ktiles, twiddles(p, L), twiddles(p, 4 * L), scale);
+  return cudaGetLastError();
+}
+
 #define FFTK_SC_SIZES(X) X(2) X(4) X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096)
 
 cudaError_t launch_scpass(fftk_plan p, int L, bool sine, int dir, const float2* in, float2* out, long long P,
@@ -271,6 +371,25 @@ cudaError_t launch_scz(fftk_plan p, bool sine, int dir, const float* in, float* 
     return dir < 0 ? scz_n<n, false, -1>(p, in, out, nlines, scale, kind, st)                     \
                    : scz_n<n, false, +1>(p, in, out, nlines, scale, kind, st);
   switch (p->nz) { FFTK_SC_SIZES(CASE) }
+#undef CASE
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace fftk
+
+namespace fftk {
+
+cudaError_t launch_scpass_pruned(fftk_plan p, bool sine, int dir, const float2* in, float2* out, long long B,
+                                 float scale, cudaStream_t st) {
+  if (B <= 0) return cudaSuccess;
+#define CASE(n)                                                                                   \
+  case n:                                                                                         \
+    if (sine)                                                                                     \
+      return dir < 0 ? scpass_pr_l<n, true, -1>(p, in, out, B, scale, st)                         \
+                     : scpass_pr_l<n, true, +1>(p, in, out, B, scale, st);                        \
+    return dir < 0 ? scpass_pr_l<n, false, -1>(p, in, out, B, scale, st)                          \
+                   : scpass_pr_l<n, false, +1>(p, in, out, B, scale, st);
+  switch (p->nx) { CASE(8) CASE(16) CASE(32) CASE(64) CASE(128) CASE(256) CASE(512) CASE(1024) }
 #undef CASE
   return cudaErrorInvalidValue;
 }

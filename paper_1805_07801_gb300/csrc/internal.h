@@ -123,6 +123,9 @@ cudaError_t launch_pruned_x(fftk_plan p, int sign, const float2* in, float2* out
                             cudaStream_t st);
 cudaError_t launch_pruned_y(fftk_plan p, int sign, const float2* in, float2* out, long long B, float scale,
                             cudaStream_t st);
+// the sine/cosine x pass restricted to the same set (3 k_x < 2n on the x axis)
+cudaError_t launch_scpass_pruned(fftk_plan p, bool sine, int dir, const float2* in, float2* out, long long B,
+                                 float scale, cudaStream_t st);
 cudaError_t launch_cpass(fftk_plan p, int L, int sign, const float2* in, float2* out, long long P,
                          long long Q, float scale, int kind, cudaStream_t st);
 

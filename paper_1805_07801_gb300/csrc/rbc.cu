@@ -228,6 +228,9 @@ __global__ void k_rbc_sff_prep(const float2* __restrict__ x, float2* __restrict_
     const int c = (int)(idx % g.h1);
     const long long ab = idx / g.h1;
     const int b = (int)(ab % g.n), a = (int)(ab / g.n);
+    // the pruned inverse passes read only the kept modes (the sine entry of
+    // k_x = a is kept with the cosine one; k_x = n never is)
+    if (!sff_kept(a, b, c, g)) continue;
     const int kb = kwav(b, g.n);
     const float ky = (2 * abs(kb) == g.n) ? 0.f : (float)kb, kz = (2 * c == g.n) ? 0.f : (float)c;
     const float2 uy = x[idx + M], uz = x[idx + 2 * M];
@@ -235,11 +238,12 @@ __global__ void k_rbc_sff_prep(const float2* __restrict__ x, float2* __restrict_
     w7[idx + 4 * M] = uy;
     w7[idx + 5 * M] = uz;
     w7[idx + 6 * M] = csub(mul_i(uz, ky), mul_i(uy, kz));  // omega_x = d_y u_z - d_z u_y
-    // sine entries of k_x = a at index a - 1; index n - 1 (k_x = n, no cosine partner) by a = 0
-    const long long sidx = a >= 1 ? idx - rowa : idx + (long long)(g.n - 1) * rowa;
-    const float kx = a >= 1 ? (float)a : 0.f;
+    // sine entries of k_x = a at index a - 1
+    if (a == 0) continue;
+    const long long sidx = idx - rowa;
+    const float kx = (float)a;
     const float2 ux = x[sidx], th = x[sidx + 3 * M];
-    const float2 uyc = a >= 1 ? uy : make_float2(0.f, 0.f), uzc = a >= 1 ? uz : make_float2(0.f, 0.f);
+    const float2 uyc = uy, uzc = uz;
     w7[sidx] = ux;
     w7[sidx + M] = cadd(mul_i(ux, kz), cscale(uzc, kx));      // omega_y = d_z u_x - d_x u_z
     w7[sidx + 2 * M] = csub(cscale(uyc, -kx), mul_i(ux, ky));  // omega_z = d_x u_y - d_y u_x
@@ -355,20 +359,34 @@ static cudaError_t rbc_stage(fftk_plan p, const float2* x, const float2* u0, flo
   const long long R = (long long)g.n * g.n * g.n;
   const unsigned grid = 152 * 8;
   if (basis == TARANG_RBC_SFF) {
-    static const int kS[3] = {FFTK_SINE, FFTK_FOURIER, FFTK_FOURIER};
-    static const int kC[3] = {FFTK_COSINE, FFTK_FOURIER, FFTK_FOURIER};
     {
       LaunchScope ls(p, KK_AUX, st);
       k_rbc_sff_prep<<<grid, 256, 0, st>>>(x, r->w7, g);
     }
-    if (fftk_inverse(p, kS, r->w7, r->r7, 4, st) != FFTK_OK) return cudaErrorLaunchFailure;
-    if (fftk_inverse(p, kC, r->w7 + 4 * g.M, r->r7 + 4 * R, 3, st) != FFTK_OK) return cudaErrorLaunchFailure;
+    // inverse transforms restricted to the kept set, in place in w7: the sine
+    // group (4 fields), then the cosine group (3)
+    cudaError_t e = cudaSuccess;
+    for (int grp = 0; grp < 2 && e == cudaSuccess; ++grp) {
+      const int nf = grp == 0 ? 4 : 3;
+      float2* w = r->w7 + (grp == 0 ? 0 : 4 * g.M);
+      e = launch_scpass_pruned(p, grp == 0, +1, w, w, nf, 1.f, st);
+      if (e == cudaSuccess) e = launch_pruned_y(p, +1, w, w, nf, 1.f, st);
+      if (e == cudaSuccess) e = launch_z_c2r(p, w, r->r7 + (grp == 0 ? 0 : 4 * R), (long long)nf * g.n * g.n, st, g.kc);
+    }
+    if (e != cudaSuccess) return e;
     {
       LaunchScope ls(p, KK_AUX, st);
       k_rbc_sff_products<<<grid, 256, 0, st>>>(r->r7, R);
     }
-    if (fftk_forward(p, kS, r->r7, r->w7, 3, st) != FFTK_OK) return cudaErrorLaunchFailure;
-    if (fftk_forward(p, kC, r->r7 + 3 * R, r->w7 + 3 * g.M, 3, st) != FFTK_OK) return cudaErrorLaunchFailure;
+    // forward transforms of the sine-parity products, then the cosine-parity ones
+    const float sc = (float)(1.0 / (double)R);
+    for (int grp = 0; grp < 2 && e == cudaSuccess; ++grp) {
+      float2* w = r->w7 + (grp == 0 ? 0 : 3 * g.M);
+      e = launch_z_r2c(p, r->r7 + (grp == 0 ? 0 : 3 * R), w, 3LL * g.n * g.n, 1.f, st, g.kc);
+      if (e == cudaSuccess) e = launch_pruned_y(p, -1, w, w, 3, 1.f, st);
+      if (e == cudaSuccess) e = launch_scpass_pruned(p, grp == 0, -1, w, w, 3, sc, st);
+    }
+    if (e != cudaSuccess) return e;
     {
       LaunchScope ls(p, KK_AUX, st);
       k_rbc_sff_update<<<grid, 256, 0, st>>>(r->w7, x, u0, r->s1, r->acc, out, g, upd, mode);
