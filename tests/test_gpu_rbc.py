@@ -310,3 +310,23 @@ def test_sff_full_size_energy_exchange(fk, oracle_mod):
         fk.fftk_plan_destroy(plan)
     assert abs(Eu1 - Eu0) > 1e-3 * Eu0
     assert abs((Eu1 - Et1) - (Eu0 - Et0)) < 1e-3 * abs(Eu1 - Eu0)
+
+
+def test_rbc_zero_steps_and_zero_state(fk, oracle_mod):
+    # nsteps = 0 leaves the state alone; the zero state stays zero (the
+    # conduction profile is a steady solution)
+    n = 16
+    s = _state(oracle_mod, n, 90)
+    plan = fk.fftk_plan_create(n, n, n)
+    try:
+        for basis in (fk.TARANG_RBC_FFF, fk.TARANG_RBC_SFF):
+            sd = to_dev_c64(s)
+            fk.tarang_rbc_step(plan, sd.data_ptr(), 1e5, 1.0, 1e-3, 0, fk.TARANG_RK4, stream(), basis=basis)
+            sync()
+            assert np.array_equal(from_dev_c64(sd), s)
+            z = to_dev_c64(np.zeros_like(s))
+            fk.tarang_rbc_step(plan, z.data_ptr(), 1e5, 1.0, 1e-3, 3, fk.TARANG_RK4, stream(), basis=basis)
+            sync()
+            assert not np.any(from_dev_c64(z))
+    finally:
+        fk.fftk_plan_destroy(plan)

@@ -244,3 +244,29 @@ def test_shell_transfer_argument_errors(fk):
         assert np.array_equal(np.array(T), np.zeros((2, 2)))
     finally:
         fk.fftk_plan_destroy(plan)
+
+
+def test_transfer_edge_cases(fk, oracle_mod):
+    # one shell holding every mode: the matrix is the 1x1 transfer of the
+    # whole field to itself, zero up to rounding; a split-FP16 plan gives the
+    # spectrum of its own (unfused) right-hand side
+    n = 32
+    u = _random_ic(oracle_mod, n, seed=90, k0=3.0)
+    plan = fk.fftk_plan_create(n, n, n)
+    plan16 = fk.fftk_plan_create(n, n, n, fk.FFTK_R32_SPLIT16)
+    try:
+        ud = to_dev_c64(u)
+        kmax = fk.tarang_diag_kmax(plan)
+        T1 = np.array(fk.tarang_shell_transfer(plan, ud.data_ptr(), [0, kmax + 1], _stream()))
+        Tfine = np.array(fk.tarang_shell_transfer(plan, ud.data_ptr(), [0, 2, 4, 8, kmax + 1], _stream()))
+        _, TK, _ = fk.tarang_transfer(plan, ud.data_ptr(), None, _stream())
+        _, TK16, _ = fk.tarang_transfer(plan16, ud.data_ptr(), None, _stream())
+    finally:
+        fk.fftk_plan_destroy(plan)
+        fk.fftk_plan_destroy(plan16)
+    assert T1.shape == (1, 1)
+    assert abs(T1[0, 0]) < 1e-5 * np.max(np.abs(Tfine))
+    TK, TK16 = np.array(TK), np.array(TK16)
+    bound = 3e-5 * _shell_norm_bound(u.astype(np.complex128), oracle_mod.ns_rhs(u.astype(np.complex128)), n,
+                                     len(TK))
+    assert np.all(np.abs(TK16 - TK) <= bound + 1e-300)
