@@ -217,10 +217,12 @@ fftk_status tarang_ns_step(fftk_plan p, void *uhat, const tarang_params *prm, in
  * the 2/3 set of tarang_ns_step; SFF: 3 k_x < 2n, 3|k_y| < n, 3 k_z < n),
  * zero elsewhere.  The right-hand side without diffusion,
  * N_u = P[u x omega + theta g] and N_theta = -div(u theta) + u.g, goes
- * through the plan's own transforms: seven inverse (u, omega, theta) and six
- * forward (u x omega, u theta) per stage, the paper's 52 transforms per RK4
- * step (Sec. 7); between plates the x passes are sine/cosine passes.
- * Device memory: 18 more fields (allocated on first use, kept by the plan). */
+ * through seven inverse (u, omega, theta) and six forward (u x omega,
+ * u theta) transforms per stage, the paper's 52 transforms per RK4 step
+ * (Sec. 7), restricted to the truncated set, with the products formed inside
+ * the z pass; between plates the x passes are sine/cosine passes.  FP32 in
+ * both plan dtypes.  Device memory: 15 more complex fields (allocated on
+ * first use, kept by the plan). */
 enum { TARANG_RBC_FFF = 0, TARANG_RBC_SFF = 1 };
 
 typedef struct {

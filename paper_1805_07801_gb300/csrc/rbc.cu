@@ -12,14 +12,15 @@
 // Sec. 2.2, Eqs. (12)-(13), non-dimensional, on the 2 pi-periodic cube with
 // gravity along z; state float2 [4][n][n][n/2+1] = (u_x, u_y, u_z, theta).
 //   N_u = P[F(u x omega) + theta z],   N_theta = -i k . F(u theta) + u_z,
-// evaluated through the plan's transforms: seven inverse (u, omega, theta),
-// six forward (u x omega, u theta) per right-hand side, 13 per stage and 52
-// per RK4 step as counted in the paper's Sec. 7.
+// evaluated with seven inverse transforms (u, omega, theta) and six forward
+// ones (u x omega, u theta) per right-hand side, 13 per stage and 52 per RK4
+// step as counted in the paper's Sec. 7: x and y passes restricted to the
+// 2/3 set (fft_pruned.cu, fft_sc.cu) and one fused z pass per stage that
+// forms the products in registers.
 namespace fftk {
 
 struct RBCWork {
-  float2* w7 = nullptr;   // spectra: u, omega, theta; then n (u x omega), u theta
-  float* r7 = nullptr;    // the same seven fields in real space
+  float2* w7 = nullptr;   // 7 spectra: u, omega, theta; then n (u x omega), u theta, in place
   float2* s1 = nullptr;   // stage state (4 fields)
   float2* acc = nullptr;  // RK4 accumulator (4 fields)
   float2* tab = nullptr;  // integrating factors, hi + lo by integer k^2: E_nu, E_kappa, H_nu, H_kappa
@@ -30,7 +31,6 @@ struct RBCWork {
 void rbc_free(RBCWork* r) {
   if (!r) return;
   cudaFree(r->w7);
-  cudaFree(r->r7);
   cudaFree(r->s1);
   cudaFree(r->acc);
   cudaFree(r->tab);
@@ -46,12 +46,11 @@ static fftk_status rbc_ensure(fftk_plan p) {
   RBCWork* r = new (std::nothrow) RBCWork;
   if (!r) return FFTK_ERR_OOM;
   const NSGeom g = s->g;
-  const size_t fb = sizeof(float2) * (size_t)g.M, rb = sizeof(float) * (size_t)g.n * g.n * g.n;
+  const size_t fb = sizeof(float2) * (size_t)g.M;
   // |k|^2 up to 3 kd^2 on the cube, (2n-1)/3 squared + 2 kd^2 between plates
   const int kxs = (2 * g.n - 1) / 3;
   r->tab_len = kxs * kxs + 2 * g.kd * g.kd + 1;
   cudaError_t e = cudaMalloc(&r->w7, 7 * fb);
-  if (e == cudaSuccess) e = cudaMalloc(&r->r7, 7 * rb);
   if (e == cudaSuccess) e = cudaMalloc(&r->s1, 4 * fb);
   if (e == cudaSuccess) e = cudaMemset(r->s1, 0, 4 * fb);
   if (e == cudaSuccess) e = cudaMalloc(&r->acc, 4 * fb);
@@ -106,21 +105,6 @@ __global__ void k_rbc_prep(const float2* __restrict__ x, float2* __restrict__ w7
     w7[idx + 4 * g.M] = csub(mul_i(ux, kz), mul_i(uz, kx));
     w7[idx + 5 * g.M] = csub(mul_i(uy, kx), mul_i(ux, ky));
     w7[idx + 6 * g.M] = x[idx + 3 * g.M];
-  }
-}
-
-// r7[0..2] = u x omega, r7[3..5] = u theta (in place, point by point)
-__global__ void k_rbc_products(float* __restrict__ r7, long long R) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < R;
-       i += (long long)gridDim.x * blockDim.x) {
-    const float ux = r7[i], uy = r7[R + i], uz = r7[2 * R + i];
-    const float wx = r7[3 * R + i], wy = r7[4 * R + i], wz = r7[5 * R + i], th = r7[6 * R + i];
-    r7[i] = uy * wz - uz * wy;
-    r7[R + i] = uz * wx - ux * wz;
-    r7[2 * R + i] = ux * wy - uy * wx;
-    r7[3 * R + i] = ux * th;
-    r7[4 * R + i] = uy * th;
-    r7[5 * R + i] = uz * th;
   }
 }
 
@@ -251,23 +235,6 @@ __global__ void k_rbc_sff_prep(const float2* __restrict__ x, float2* __restrict_
   }
 }
 
-// r7 = [u_x, omega_y, omega_z, theta, u_y, u_z, omega_x] -> in place
-// [(u x omega)_x, u_y theta, u_z theta | (u x omega)_y, (u x omega)_z, u_x theta]:
-// the sine-parity products first, then the cosine-parity ones
-__global__ void k_rbc_sff_products(float* __restrict__ r7, long long R) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < R;
-       i += (long long)gridDim.x * blockDim.x) {
-    const float ux = r7[i], wy = r7[R + i], wz = r7[2 * R + i], th = r7[3 * R + i];
-    const float uy = r7[4 * R + i], uz = r7[5 * R + i], wx = r7[6 * R + i];
-    r7[i] = uy * wz - uz * wy;
-    r7[R + i] = uy * th;
-    r7[2 * R + i] = uz * th;
-    r7[3 * R + i] = uz * wx - ux * wz;
-    r7[4 * R + i] = ux * wy - uy * wx;
-    r7[5 * R + i] = ux * th;
-  }
-}
-
 // the stage update of one field entry i (the modes of ns_mode_update)
 __device__ __forceinline__ void rbc_entry_update(long long i, float2 n, float2 E, float2 H, float dt, int mode,
                                                  const float2* u0, const float2* s1, float2* acc, float2* out) {
@@ -350,69 +317,210 @@ __global__ void k_rbc_sff_update(const float2* __restrict__ w7, const float2* x,
   }
 }
 
-// One right-hand side of the stage input x and the update of `mode`.
+// ---- fused z pass (both bases: z is Fourier in each) ----------------------
+// Per (x, y) line: c2r of u, theta (parked in shared memory) and of the three
+// vorticity components (folded into the accumulators of n = u x omega), then
+// r2c of n and of u theta.  Reads k_z < kc of the seven input slots, writes
+// k_z < kc of the six output slots, in place (every input of a line is read
+// before the line's first output is written).  Slot maps: in[7] = u_x, u_y,
+// u_z, omega_x, omega_y, omega_z, theta; out[6] = n_x, n_y, n_z, u_x theta,
+// u_y theta, u_z theta.
+struct RBCSlots {
+  int in[7];
+  int out[6];
+};
+
+template <int N>
+struct RZCfg {
+  static constexpr int H = N / 2;
+  static constexpr int G = H < 8 ? H : 8;
+  static constexpr int S = H / G;
+  static constexpr int LPC = S >= 128 ? 1 : 128 / S;
+  static constexpr int THREADS = LPC * S;
+  static constexpr bool WARP = S <= 32;
+  static constexpr size_t SMEM = sizeof(float2) * (size_t)LPC * H * 5;  // exchange + 4 parked fields
+};
+
+template <int N>
+__global__ void __launch_bounds__(RZCfg<N>::THREADS, 3)
+    k_rbc_z(float2* w, RBCSlots sl, const float2* __restrict__ tw) {
+  constexpr long long H1 = N / 2 + 1, MM = (long long)N * N * H1;
+  constexpr int KC = (N - 1) / 3 + 1;
+  using C = RZCfg<N>;
+  constexpr int H = C::H, G = C::G, S = C::S;
+  constexpr int LOGN = Log2<N>::value;
+  extern __shared__ float2 smr[];
+  const int li = threadIdx.x / S, j = threadIdx.x % S;
+  const long long line = (long long)blockIdx.x * C::LPC + li;
+  const bool valid = line < (long long)N * N;
+  const LineX<C::WARP> xc{smr + li * H};
+  float2* park = smr + C::LPC * H + li * 4 * H + j;  // [4][G][S]: u_x, u_y, u_z, theta
+
+  auto c2r = [&](int slot, float2(&U)[G]) {
+    const float2* src = w + slot * MM + line * H1;
+#pragma unroll
+    for (int m = 0; m < G; ++m) {
+      const int k = j + m * S;
+      float2 A = make_float2(0.f, 0.f), B = make_float2(0.f, 0.f);
+      if (valid && k < KC) A = src[k];
+      if (valid && H - k < KC) B = src[H - k];
+      if (k == 0) {
+        A.y = 0.f;
+        B.y = 0.f;
+      }
+      const float2 Bc = cconj(B);
+      const float2 E = cadd(A, Bc);
+      const float2 O = cmulc(csub(A, Bc), __ldg(&tw[k]));
+      U[m] = make_float2(E.x - O.y, E.y + O.x);
+    }
+    fft_line<H, G, +1, LOGN>(U, j, xc, tw);
+  };
+  auto r2c = [&](int slot, float2(&U)[G]) {
+    fft_line<H, G, -1, LOGN>(U, j, xc, tw);
+#pragma unroll
+    for (int m = 0; m < G; ++m) xc.st(j + m * S, U[m]);
+    xc.sync();
+    float2* dst = w + slot * MM + line * H1;
+#pragma unroll
+    for (int m = 0; m < G; ++m) {
+      const int k = j + m * S;
+      const float2 Bc = cconj(xc.ld((H - k) & (H - 1)));
+      const float2 E = cscale(cadd(U[m], Bc), 0.5f);
+      const float2 D = csub(U[m], Bc);
+      const float2 O = make_float2(0.5f * D.y, -0.5f * D.x);
+      if (valid && k < KC) dst[k] = cadd(E, cmul(__ldg(&tw[k]), O));
+    }
+    xc.sync();
+  };
+  auto pk = [&](int f, int m) -> float2& { return park[(f * G + m) * S]; };
+  {
+    float2 U[G];
+#pragma unroll 1
+    for (int q = 0; q < 4; ++q) {
+      c2r(sl.in[q < 3 ? q : 6], U);
+#pragma unroll
+      for (int m = 0; m < G; ++m) pk(q, m) = U[m];
+    }
+  }
+  // n = u x omega, two real points per slot
+  float2 Nx[G], Ny[G], Nz[G];
+  {
+    float2 W[G];
+    c2r(sl.in[3], W);  // omega_x
+#pragma unroll
+    for (int m = 0; m < G; ++m) {
+      const float2 uy = pk(1, m), uz = pk(2, m);
+      Ny[m] = make_float2(uz.x * W[m].x, uz.y * W[m].y);
+      Nz[m] = make_float2(-uy.x * W[m].x, -uy.y * W[m].y);
+    }
+    c2r(sl.in[4], W);  // omega_y
+#pragma unroll
+    for (int m = 0; m < G; ++m) {
+      const float2 ux = pk(0, m), uz = pk(2, m);
+      Nx[m] = make_float2(-uz.x * W[m].x, -uz.y * W[m].y);
+      Nz[m] = make_float2(fmaf(ux.x, W[m].x, Nz[m].x), fmaf(ux.y, W[m].y, Nz[m].y));
+    }
+    c2r(sl.in[5], W);  // omega_z
+#pragma unroll
+    for (int m = 0; m < G; ++m) {
+      const float2 ux = pk(0, m), uy = pk(1, m);
+      Nx[m] = make_float2(fmaf(uy.x, W[m].x, Nx[m].x), fmaf(uy.y, W[m].y, Nx[m].y));
+      Ny[m] = make_float2(fmaf(-ux.x, W[m].x, Ny[m].x), fmaf(-ux.y, W[m].y, Ny[m].y));
+    }
+  }
+  // every input slot of this line has been read: the outputs may overwrite them
+  __syncthreads();
+  r2c(sl.out[0], Nx);
+  r2c(sl.out[1], Ny);
+  r2c(sl.out[2], Nz);
+#pragma unroll 1
+  for (int i = 0; i < 3; ++i) {
+    float2 P[G];
+#pragma unroll
+    for (int m = 0; m < G; ++m) {
+      const float2 ui = pk(i, m), th = pk(3, m);
+      P[m] = make_float2(ui.x * th.x, ui.y * th.y);
+    }
+    r2c(sl.out[3 + i], P);
+  }
+}
+
+template <int N>
+static cudaError_t rbc_z_n(fftk_plan p, float2* w, const RBCSlots& sl, cudaStream_t st) {
+  using C = RZCfg<N>;
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [] {
+    attr_err = cudaFuncSetAttribute(k_rbc_z<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+  });
+  if (attr_err != cudaSuccess) return attr_err;
+  const long long lines = (long long)N * N;
+  LaunchScope ls(p, KK_AUX, st);
+  k_rbc_z<N><<<(unsigned)((lines + C::LPC - 1) / C::LPC), C::THREADS, C::SMEM, st>>>(w, sl, twiddles(p, N));
+  return cudaGetLastError();
+}
+
+static cudaError_t rbc_z(fftk_plan p, float2* w, const RBCSlots& sl, cudaStream_t st) {
+  switch (p->nz) {
+#define CASE(n) \
+  case n:       \
+    return rbc_z_n<n>(p, w, sl, st);
+    CASE(8) CASE(16) CASE(32) CASE(64) CASE(128) CASE(256) CASE(512) CASE(1024)
+#undef CASE
+  }
+  return cudaErrorInvalidValue;
+}
+
+// One right-hand side of the stage input x and the update of `mode`:
+// spectral preparation, inverse x and y passes restricted to the kept set,
+// the fused z pass (products in registers), forward y and x passes, update.
 static cudaError_t rbc_stage(fftk_plan p, const float2* x, const float2* u0, float2* out, const RBCUpdate& upd,
                              int mode, int basis, cudaStream_t st) {
   NSWork* s = p->ns;
   RBCWork* r = s->rbc;
   const NSGeom g = s->g;
   const long long R = (long long)g.n * g.n * g.n;
+  const float scale = (float)(1.0 / (double)R);
   const unsigned grid = 152 * 8;
+  float2* w = r->w7;
+  cudaError_t e = cudaSuccess;
   if (basis == TARANG_RBC_SFF) {
+    // w7 = [u_x, omega_y, omega_z, theta | u_y, u_z, omega_x]: sine group, cosine group
     {
       LaunchScope ls(p, KK_AUX, st);
-      k_rbc_sff_prep<<<grid, 256, 0, st>>>(x, r->w7, g);
+      k_rbc_sff_prep<<<grid, 256, 0, st>>>(x, w, g);
     }
-    // inverse transforms restricted to the kept set, in place in w7: the sine
-    // group (4 fields), then the cosine group (3)
-    cudaError_t e = cudaSuccess;
-    for (int grp = 0; grp < 2 && e == cudaSuccess; ++grp) {
-      const int nf = grp == 0 ? 4 : 3;
-      float2* w = r->w7 + (grp == 0 ? 0 : 4 * g.M);
-      e = launch_scpass_pruned(p, grp == 0, +1, w, w, nf, 1.f, st);
-      if (e == cudaSuccess) e = launch_pruned_y(p, +1, w, w, nf, 1.f, st);
-      if (e == cudaSuccess) e = launch_z_c2r(p, w, r->r7 + (grp == 0 ? 0 : 4 * R), (long long)nf * g.n * g.n, st, g.kc);
-    }
+    e = launch_scpass_pruned(p, true, +1, w, w, 4, 1.f, st);
+    if (e == cudaSuccess) e = launch_scpass_pruned(p, false, +1, w + 4 * g.M, w + 4 * g.M, 3, 1.f, st);
+    if (e == cudaSuccess) e = launch_pruned_y(p, +1, w, w, 7, 1.f, st);
+    // products: [(u x omega)_x, u_y theta, u_z theta | (u x omega)_y, (u x omega)_z, u_x theta]
+    const RBCSlots sl{{0, 4, 5, 6, 1, 2, 3}, {0, 3, 4, 5, 1, 2}};
+    if (e == cudaSuccess) e = rbc_z(p, w, sl, st);
+    if (e == cudaSuccess) e = launch_pruned_y(p, -1, w, w, 6, 1.f, st);
+    if (e == cudaSuccess) e = launch_scpass_pruned(p, true, -1, w, w, 3, scale, st);
+    if (e == cudaSuccess) e = launch_scpass_pruned(p, false, -1, w + 3 * g.M, w + 3 * g.M, 3, scale, st);
     if (e != cudaSuccess) return e;
     {
       LaunchScope ls(p, KK_AUX, st);
-      k_rbc_sff_products<<<grid, 256, 0, st>>>(r->r7, R);
-    }
-    // forward transforms of the sine-parity products, then the cosine-parity ones
-    const float sc = (float)(1.0 / (double)R);
-    for (int grp = 0; grp < 2 && e == cudaSuccess; ++grp) {
-      float2* w = r->w7 + (grp == 0 ? 0 : 3 * g.M);
-      e = launch_z_r2c(p, r->r7 + (grp == 0 ? 0 : 3 * R), w, 3LL * g.n * g.n, 1.f, st, g.kc);
-      if (e == cudaSuccess) e = launch_pruned_y(p, -1, w, w, 3, 1.f, st);
-      if (e == cudaSuccess) e = launch_scpass_pruned(p, grp == 0, -1, w, w, 3, sc, st);
-    }
-    if (e != cudaSuccess) return e;
-    {
-      LaunchScope ls(p, KK_AUX, st);
-      k_rbc_sff_update<<<grid, 256, 0, st>>>(r->w7, x, u0, r->s1, r->acc, out, g, upd, mode);
+      k_rbc_sff_update<<<grid, 256, 0, st>>>(w, x, u0, r->s1, r->acc, out, g, upd, mode);
     }
     return cudaGetLastError();
   }
+  // w7 = [u_x, u_y, u_z, omega_x, omega_y, omega_z, theta] -> [n_x, n_y, n_z, u_x theta, ...]
   {
     LaunchScope ls(p, KK_AUX, st);
-    k_rbc_prep<<<grid, 256, 0, st>>>(x, r->w7, g);
+    k_rbc_prep<<<grid, 256, 0, st>>>(x, w, g);
   }
-  // inverse transforms restricted to the 2/3 set, in place in w7, then the z c2r
-  cudaError_t e = launch_pruned_x(p, +1, r->w7, r->w7, 7, 1.f, st);
-  if (e == cudaSuccess) e = launch_pruned_y(p, +1, r->w7, r->w7, 7, 1.f, st);
-  if (e == cudaSuccess) e = launch_z_c2r(p, r->w7, r->r7, 7LL * g.n * g.n, st, g.kc);
+  e = launch_pruned_x(p, +1, w, w, 7, 1.f, st);
+  if (e == cudaSuccess) e = launch_pruned_y(p, +1, w, w, 7, 1.f, st);
+  const RBCSlots sl{{0, 1, 2, 3, 4, 5, 6}, {0, 1, 2, 3, 4, 5}};
+  if (e == cudaSuccess) e = rbc_z(p, w, sl, st);
+  if (e == cudaSuccess) e = launch_pruned_y(p, -1, w, w, 6, 1.f, st);
+  if (e == cudaSuccess) e = launch_pruned_x(p, -1, w, w, 6, scale, st);
   if (e != cudaSuccess) return e;
   {
     LaunchScope ls(p, KK_AUX, st);
-    k_rbc_products<<<grid, 256, 0, st>>>(r->r7, R);
-  }
-  e = launch_z_r2c(p, r->r7, r->w7, 6LL * g.n * g.n, 1.f, st, g.kc);
-  if (e == cudaSuccess) e = launch_pruned_y(p, -1, r->w7, r->w7, 6, 1.f, st);
-  if (e == cudaSuccess) e = launch_pruned_x(p, -1, r->w7, r->w7, 6, (float)(1.0 / ((double)R)), st);
-  if (e != cudaSuccess) return e;
-  {
-    LaunchScope ls(p, KK_AUX, st);
-    k_rbc_update<<<grid, 256, 0, st>>>(r->w7, x, u0, r->s1, r->acc, out, g, upd, mode);
+    k_rbc_update<<<grid, 256, 0, st>>>(w, x, u0, r->s1, r->acc, out, g, upd, mode);
   }
   return cudaGetLastError();
 }
