@@ -484,6 +484,20 @@ def cpu_baseline():
             "sample": f"one full RK2-IF step of the 512^3 workload (FP64 oracle, OpenMP over lines), {t:.1f} s"}
 
 
+def oracle_beside(label, n, work, units):
+    """The FP64 oracle timed on the host cores beside a GPU measurement: one
+    run of work(), a bounded sample of the same kind of work at n^3 (no
+    warm-up run, to keep it short).  Returns the seconds, the rate in `units`
+    and the threads used."""
+    import oracle
+
+    t0 = time.perf_counter()
+    work()
+    t = time.perf_counter() - t0
+    return {"sample": f"{label}, n = {n}", "seconds": round(t, 3), "rate": round(1.0 / t, 4), "unit": units,
+            "cores": oracle.threads(), "kind": "oracle"}
+
+
 def run_reference(args, world, rank):
     """The oracle as the reference arm: each step is a bounded sample of the
     512^3 step, one inverse + one forward 3D transform of a velocity component
@@ -755,6 +769,14 @@ def run_transfer(n: int):
     T, Pi = np.array(T), np.array(Pi)
     kd = (n - 1) // 3
     kept = (2 * kd + 1) ** 2 * (kd + 1)
+    import oracle
+
+    uo = _oracle_state(64)
+    ocpu = oracle_beside("oracle right-hand side + T(K) of the decaying field's initial state", 64,
+                         lambda: oracle.transfer_spectrum(uo, oracle.ns_rhs(uo)), "calls/s")
+    ocpu_shell = oracle_beside("oracle shell-to-shell matrix, octave shells", 32,
+                               lambda: oracle.shell_transfer(_oracle_state(32), [0, 1, 2, 4, 8, 16, 29]),
+                               "calls/s")
     print(json.dumps({"workload": f"{n}^3 decaying field (k0={K0}, E={E0}, seed {SEED}) after 50 steps "
                                   f"nu={NU}, dt={DT}",
                       "ms_transfer": round(ms_transfer, 4), "ms_rhs": round(ms_rhs, 4),
@@ -763,6 +785,7 @@ def run_transfer(n: int):
                       "sum_T_over_sum_absT": tot / float(np.sum(np.abs(T))),
                       "flux_max": float(Pi.max()), "flux_argmax": int(Pi.argmax()),
                       "flux_K_0_to_63": [float(v) for v in Pi[:64]],
+                      "oracle_cpu": ocpu, "oracle_cpu_shell_transfer": ocpu_shell,
                       "shell_bounds": bounds, "ms_shell_transfer": round(ms_shell, 3),
                       "shell_antisymmetry": float(np.max(np.abs(S + S.T)) / np.max(np.abs(S))),
                       "shell_transfer": [[float(v) for v in row] for row in S]}), flush=True)
@@ -812,6 +835,10 @@ def run_schemes(n: int, steps: int):
                      "E": E, "eps": eps, "steps": steps + 3}
     fk.fftk_sync(plan, st)
     fk.fftk_plan_destroy(plan)
+    import oracle
+
+    uo = _oracle_state(64)
+    out["oracle_cpu"] = oracle_beside("oracle RK4 step", 64, lambda: oracle.ns_step_rk4(uo, NU, DT, 1), "steps/s")
     print(json.dumps({"workload": f"{n}^3 decaying turbulence, nu={NU}, dt={DT}, seed {SEED}",
                       "peak_GBps": hbm, "peak_kind": peak_kind, **out}), flush=True)
 
@@ -860,6 +887,11 @@ def run_rbc(n: int, steps: int):
                      "ms_per_transform_incl_pointwise": round(ms / ntr, 4), "finite": fin}
     fk.fftk_sync(plan, st)
     fk.fftk_plan_destroy(plan)
+    import oracle
+
+    so = np.concatenate([_oracle_state(64), _oracle_state(64)[2:3]])
+    out["oracle_cpu"] = oracle_beside("oracle RK4 convection step (cube)", 64,
+                                      lambda: oracle.rbc_step(so, 1e8, 1.0, 1e-3, 1, 1), "steps/s")
     print(json.dumps({"workload": f"{n}^3 Rayleigh-Benard (FFF), Ra=1e8, Pr=1, dt=1e-3, random-phase u (k0={K0}), "
                                   f"theta = u_z, seed {SEED}", **out}), flush=True)
 
@@ -911,8 +943,14 @@ def run_radix3():
         fk.fftk_plan_destroy(plan)
         del x, F, y
         torch.cuda.empty_cache()
+    import oracle
+    import synth
+
+    f96 = synth.normal(SEED, 0, (96, 96, 96)).astype(np.float64)
+    ocpu = oracle_beside("oracle R2C + C2R pair, lines of 3*2^m by the DFT's definition", 96,
+                         lambda: oracle.irfft3(oracle.rfft3(f96), 96), "pairs/s")
     print(json.dumps({"workload": "R2C+C2R pairs of normal(0,1), seed 0, 2^m and 3*2^m cubes", "peak_GBps": hbm,
-                      "peak_kind": peak_kind, "sizes": rows}), flush=True)
+                      "peak_kind": peak_kind, "sizes": rows, "oracle_cpu": ocpu}), flush=True)
 
 
 def run_bases(n: int):
@@ -961,8 +999,14 @@ def run_bases(n: int):
                      "pair_bytes": pair, "frac_pair": round(pair / (ms * 1e-3) / 1e9 / hbm, 4),
                      "round_trip_rel_l2": err})
     fk.fftk_plan_destroy(plan)
+    import oracle
+    import synth
+
+    f64 = synth.normal(SEED, 0, (64, 64, 64)).astype(np.float64)
+    ocpu = oracle_beside("oracle SFF forward + inverse pair (sine axis by its definition, O(n^4))", 64,
+                         lambda: oracle.itransform3(oracle.transform3(f64, "SFF"), 64, "SFF"), "pairs/s")
     print(json.dumps({"workload": f"{n}^3 forward + inverse pairs of normal(0,1), seed {SEED}, mixed bases",
-                      "peak_GBps": hbm, "peak_kind": peak_kind, "bases": rows}), flush=True)
+                      "peak_GBps": hbm, "peak_kind": peak_kind, "bases": rows, "oracle_cpu": ocpu}), flush=True)
 
 
 def run_fft_sweep(args):
