@@ -885,6 +885,17 @@ def run_rbc(n: int, steps: int):
         fin = bool(torch.isfinite(s).all())
         out[name] = {"steps_per_s": round(1e3 / ms, 3), "ms_per_step": round(ms, 4), "transforms_per_step": ntr,
                      "ms_per_transform_incl_pointwise": round(ms / ntr, 4), "finite": fin}
+        if name == "rk4":  # kinetic and thermal fluxes of the state reached (Sec. 7)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            (tu, Tu, Pu), (tt, Tt, Pt) = fk.tarang_rbc_transfer(plan, s.data_ptr(), st)
+            b.record()
+            b.synchronize()
+            out["flux"] = {"ms": round(a.elapsed_time(b), 3), "sum_Tu_over_sum_absTu": tu / sum(abs(v) for v in Tu),
+                           "sum_Ttheta_over_sum_absTtheta": tt / sum(abs(v) for v in Tt),
+                           "Pi_u_K_0_to_31": [float(v) for v in Pu[:32]],
+                           "Pi_theta_K_0_to_31": [float(v) for v in Pt[:32]]}
     fk.fftk_sync(plan, st)
     fk.fftk_plan_destroy(plan)
     import oracle

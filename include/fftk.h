@@ -243,6 +243,19 @@ fftk_status tarang_rbc_rhs(fftk_plan p, int basis, const void *state, void *out,
 fftk_status tarang_rbc_step(fftk_plan p, void *state, const tarang_rbc_params *prm, int nsteps,
                             void *cuda_stream);
 
+/* Kinetic and thermal energy transfer of convection on the periodic cube
+ * (FFF), the fluxes the paper plots for its convection run (Sec. 7,
+ * Pi_u(k) and Pi_theta(k)).  With N the right-hand side of tarang_rbc_rhs:
+ *   T_u(K) = sum_{nint|k| = K} w Re(conj(u) . N_u) - w Re(conj(u_z) theta),
+ *   T_theta(K) = sum_{nint|k| = K} w Re(conj(theta) N_theta) - w Re(conj(theta) u_z)
+ * (the buoyancy and conduction-source exchanges taken out, the advective
+ * transfer left; each sums to 0 over K up to rounding) and
+ * Pi(K) = -sum_{K' <= K} T(K').  out_host: 2 (1 + 2 (kmax + 1)) doubles:
+ * sum T_u, T_u(0..kmax), Pi_u(0..kmax), then the same for theta (kmax of
+ * tarang_diag_kmax).  FP64 reductions in a fixed order; synchronises; uses
+ * the plan's convection workspace (not concurrently with tarang_rbc_step). */
+fftk_status tarang_rbc_transfer(fftk_plan p, const void *state, double *out_host, void *cuda_stream);
+
 /* Largest shell index reported by the diagnostics for this plan. */
 int tarang_diag_kmax(fftk_plan p);
 

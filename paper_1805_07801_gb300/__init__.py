@@ -101,6 +101,7 @@ def lib() -> ctypes.CDLL:
             "tarang_diag": ([vp, vp, d, vp, vp], i),
             "tarang_diag_noalloc": ([i, vp, d, vp, vp], i),
             "tarang_rbc_rhs": ([vp, i, vp, vp, vp], i),
+            "tarang_rbc_transfer": ([vp, vp, vp, vp], i),
             "tarang_rbc_step": ([vp, vp, c.POINTER(tarang_rbc_params), i, vp], i),
             "fftk_forward": ([vp, vp, vp, vp, i, vp], i),
             "fftk_inverse": ([vp, vp, vp, vp, i, vp], i),
@@ -228,6 +229,17 @@ def tarang_rbc_step(plan: int, state_ptr, Ra: float, Pr: float, dt: float, nstep
     prm = tarang_rbc_params(float(Ra), float(Pr), float(dt), int(scheme), int(basis))
     _check(lib().tarang_rbc_step(_vp(plan), _vp(state_ptr), ctypes.byref(prm), int(nsteps), _vp(stream)),
            "tarang_rbc_step")
+
+
+def tarang_rbc_transfer(plan: int, state_ptr, stream=0):
+    """((sum T_u, T_u list, Pi_u list), (sum T_theta, T_theta list, Pi_theta list)); synchronises."""
+    nb = tarang_diag_kmax(plan) + 1
+    buf = (ctypes.c_double * (2 * (1 + 2 * nb)))()
+    _check(lib().tarang_rbc_transfer(_vp(plan), _vp(state_ptr), ctypes.cast(buf, ctypes.c_void_p), _vp(stream)),
+           "tarang_rbc_transfer")
+    v = list(buf)
+    h = 1 + 2 * nb
+    return tuple((v[o], v[o + 1:o + 1 + nb], v[o + 1 + nb:o + h]) for o in (0, h))
 
 
 FFTK_FOURIER, FFTK_SINE, FFTK_COSINE = 0, 1, 2

@@ -78,7 +78,7 @@ void rbc_free(RBCWork* r);
 // diagnostics (ns_diag.cu)
 int diag_blocks(int width);
 cudaError_t diag_attr();
-cudaError_t diag_launch(fftk_plan p, const float2* u, const float2* nh, double nu, cudaStream_t st);
+cudaError_t diag_launch(fftk_plan p, const float2* u, const float2* nh, double nu, cudaStream_t st, int nf = 3);
 
 inline bool misaligned16(const void* ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 15u) != 0; }
 

@@ -91,10 +91,11 @@ __device__ __forceinline__ float scale2(float v, int k) {
 // summed in block order by k_diag_final.
 // With nh == nullptr the per-mode value is the energy 1/2 w |u|^2 (slots:
 // E, eps, E(K)); otherwise it is the transfer w Re(conj(u) . nh) (slots:
-// sum_K T(K), 0, T(K)).  Slot 0 is the sum of the shells.
+// sum_K T(K), 0, T(K)).  Slot 0 is the sum of the shells.  nf: the number
+// of components (fields M apart) in the dot products, 1 to 3.
 __global__ void __launch_bounds__(DIAG_WARPS * 32)
     k_diag(const float2* __restrict__ u, const float2* __restrict__ nh, NSGeom g, double nu, int kmax,
-           double* part) {
+           double* part, int nf) {
   extern __shared__ double hist[];  // [DIAG_WARPS][kmax+1]
   __shared__ double wd[DIAG_WARPS];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -121,6 +122,7 @@ __global__ void __launch_bounds__(DIAG_WARPS * 32)
       const long long idx = ((long long)ax * g.n + ay) * g.h1 + kz;
 #pragma unroll
       for (int f = 0; f < 3; ++f) {
+        if (f >= nf) break;
         const float2 v = u[idx + f * g.M];
         a[2 * f] = v.x;
         a[2 * f + 1] = v.y;
@@ -232,12 +234,12 @@ cudaError_t diag_attr() {
   return e;
 }
 
-cudaError_t diag_launch(fftk_plan p, const float2* u, const float2* nh, double nu, cudaStream_t st) {
+cudaError_t diag_launch(fftk_plan p, const float2* u, const float2* nh, double nu, cudaStream_t st, int nf) {
   NSWork* s = p->ns;
   const int width = 2 + s->kmax + 1;
   {
     LaunchScope ls(p, KK_NS_REDUCE, st);
-    k_diag<<<diag_blocks(width), DIAG_WARPS * 32, s->diag_smem, st>>>(u, nh, s->g, nu, s->kmax, s->part);
+    k_diag<<<diag_blocks(width), DIAG_WARPS * 32, s->diag_smem, st>>>(u, nh, s->g, nu, s->kmax, s->part, nf);
   }
   {
     LaunchScope ls(p, KK_NS_REDUCE, st);
@@ -395,7 +397,7 @@ extern "C" fftk_status tarang_shell_transfer(fftk_plan p, const void* uhat, int 
     if (fftk_r2c(p, s->r3, ph, 3, cuda_stream) != FFTK_OK) return FFTK_ERR_CUDA;
     {
       LaunchScope ls(p, KK_NS_REDUCE, st);
-      k_diag<<<diag_blocks(width), DIAG_WARPS * 32, s->diag_smem, st>>>(u, ph, g, 0.0, s->kmax, s->part);
+      k_diag<<<diag_blocks(width), DIAG_WARPS * 32, s->diag_smem, st>>>(u, ph, g, 0.0, s->kmax, s->part, 3);
     }
     {
       LaunchScope ls(p, KK_NS_REDUCE, st);
@@ -483,7 +485,7 @@ extern "C" fftk_status tarang_diag_noalloc(int n, const void* uhat, double nu, d
   // in the same call, so nothing in the shared scratch needs clearing.
   const int smem = (int)(sizeof(double) * DIAG_WARPS * (kmax + 1));
   k_diag<<<diag_blocks(width), DIAG_WARPS * 32, smem, st>>>(static_cast<const float2*>(uhat), nullptr, g, nu, kmax,
-                                                   scratch);
+                                                   scratch, 3);
   k_diag_final<<<(width + 127) / 128, 128, 0, st>>>(scratch, width, diag_blocks(width), diag_dev);
   return from_cuda(cudaGetLastError());
 }

@@ -582,3 +582,58 @@ extern "C" fftk_status tarang_rbc_step(fftk_plan p, void* state, const tarang_rb
   }
   return from_cuda(e);
 }
+
+// Kinetic and thermal energy transfer of the periodic convection (the flux
+// computation of the paper's Sec. 7, Pi_u(k) and Pi_theta(k)): with N the
+// right-hand side of tarang_rbc_rhs,
+//   T_u(K) = sum_shell w Re(conj(u) . N_u) - sum_shell w Re(conj(u_z) theta),
+//   T_theta(K) = sum_shell w Re(conj(theta) N_theta) - sum_shell w Re(conj(theta) u_z)
+// (the buoyancy and conduction-source exchanges removed, advection left),
+// Pi(K) = -sum_{K' <= K} T(K').
+extern "C" fftk_status tarang_rbc_transfer(fftk_plan p, const void* state, double* out_host, void* cuda_stream) {
+  fftk_status s = rbc_check(p, state);
+  if (s != FFTK_OK) return s;
+  if (!out_host) return FFTK_ERR_INVALID_ARG;
+  s = rbc_ensure(p);
+  if (s != FFTK_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  NSWork* w = p->ns;
+  RBCWork* r = w->rbc;
+  const NSGeom g = w->g;
+  const float2* x = static_cast<const float2*>(state);
+  float2* nh = r->acc;  // free between steps
+  cudaError_t e = cudaMemsetAsync(nh, 0, sizeof(float2) * 4 * (size_t)g.M, st);
+  const RBCUpdate upd{r->tab, r->tab_len, 0.f};
+  if (e == cudaSuccess) e = rbc_stage(p, x, x, nh, upd, NS_RHS, TARANG_RBC_FFF, st);
+  const int nb = w->kmax + 1, width = 2 + nb;
+  // three reductions: u . N_u (3 components), u_z theta, theta N_theta
+  const float2* ua[3] = {x, x + 2 * g.M, x + 3 * g.M};
+  const float2* na[3] = {nh, x + 3 * g.M, nh + 3 * g.M};
+  const int nfs[3] = {3, 1, 1};
+  std::vector<double> h(3 * (size_t)width);
+  for (int q = 0; q < 3 && e == cudaSuccess; ++q) {
+    e = diag_launch(p, ua[q], na[q], 0.0, st, nfs[q]);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h.data() + (size_t)q * width, w->dout, sizeof(double) * width, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
+  if (e != cudaSuccess) return from_cuda(e);
+  // out: sum T_u, T_u(0..kmax), Pi_u(0..kmax), sum T_theta, T_theta(...), Pi_theta(...)
+  bool finite = true;
+  for (int fld = 0; fld < 2; ++fld) {
+    double* o = out_host + (size_t)fld * (1 + 2 * nb);
+    const double* adv = h.data() + (size_t)(fld == 0 ? 0 : 2) * width;
+    const double* buoy = h.data() + (size_t)width;
+    double pi = 0.0, tot = 0.0;
+    for (int K = 0; K < nb; ++K) {
+      const double t = adv[2 + K] - buoy[2 + K];
+      o[1 + K] = t;
+      pi -= t;
+      o[1 + nb + K] = pi;
+      tot += t;
+    }
+    o[0] = tot;
+    finite = finite && std::isfinite(tot);
+  }
+  return finite ? FFTK_OK : FFTK_ERR_NONFINITE;
+}

@@ -119,6 +119,7 @@ def test_null_plan_calls_of_the_later_entry_points(fk):
     assert L.fftk_inverse(None, None, None, None, 1, None) == bad
     assert L.tarang_rbc_rhs(None, 0, None, None, None) == bad
     assert L.tarang_rbc_step(None, None, None, 1, None) == bad
+    assert L.tarang_rbc_transfer(None, None, None, None) == bad
     names = [fk.fftk_kernel_name(k) for k in range(fk.fftk_kernel_kinds())]
     assert "sc_fwd" in names and "sc_inv" in names
 

@@ -330,3 +330,34 @@ def test_rbc_zero_steps_and_zero_state(fk, oracle_mod):
             assert not np.any(from_dev_c64(z))
     finally:
         fk.fftk_plan_destroy(plan)
+
+
+@pytest.mark.parametrize("n", [16, 32])
+def test_rbc_transfer_matches_oracle(fk, oracle_mod, n):
+    # T_u(K) = shell sums of w Re(u* . N_u) - w Re(u_z* theta); T_theta(K) of
+    # w Re(theta* N_theta) - w Re(theta* u_z): the oracle's transfer spectrum
+    # of the oracle's right-hand side, one component at a time where needed
+    s = _state(oracle_mod, n, 120 + n)
+    plan = fk.fftk_plan_create(n, n, n)
+    try:
+        sd = to_dev_c64(s)
+        (tu, Tu, Pu), (tt, Tt, Pt) = fk.tarang_rbc_transfer(plan, sd.data_ptr(), stream())
+    finally:
+        fk.fftk_plan_destroy(plan)
+    s64 = s.astype(np.complex128)
+    N = oracle_mod.rbc_rhs(s64)
+    z = np.zeros_like(s64[0])
+
+    def ts(a, b):
+        return oracle_mod.transfer_spectrum(np.stack([a, z, z]), np.stack([b, z, z]))
+
+    Tu_o = oracle_mod.transfer_spectrum(s64[:3], N[:3]) - ts(s64[2], s64[3])
+    Tt_o = ts(s64[3], N[3]) - ts(s64[3], s64[2])
+    Tu, Tt, Pu = np.array(Tu), np.array(Tt), np.array(Pu)
+    for got, want in ((Tu, Tu_o), (Tt, Tt_o)):
+        scale = np.max(np.abs(want))
+        assert scale > 1e-4
+        assert np.max(np.abs(got - want)) < 1e-5 * np.sum(np.abs(want))
+    # advection only moves energy between shells
+    assert abs(tu) < 1e-5 * np.sum(np.abs(Tu)) and abs(tt) < 1e-5 * np.sum(np.abs(Tt))
+    assert np.array_equal(Pu, -np.cumsum(Tu))
