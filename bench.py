@@ -850,6 +850,7 @@ def run_rbc(n: int, steps: int):
     and RK2, and between free-slip plates (the same coefficients read in the
     plates' bases) with RK4; CUDA events over `steps` steps after 3.  Prints
     one JSON line with steps/s and the time per transform."""
+    import numpy as np
     import torch
 
     import paper_1805_07801_gb300 as fk
@@ -971,6 +972,7 @@ def run_bases(n: int):
     pairs after 3, against the pair roofline: every pass reads and writes its
     field once (8R + 80M bytes with a Fourier z axis, 48R for SSS).  Prints
     one JSON line."""
+    import numpy as np
     import torch
 
     import paper_1805_07801_gb300 as fk
