@@ -495,7 +495,7 @@ def oracle_beside(label, n, work, units):
     work()
     t = time.perf_counter() - t0
     return {"sample": f"{label}, n = {n}", "seconds": round(t, 3), "rate": round(1.0 / t, 4), "unit": units,
-            "cores": oracle.threads(), "kind": "oracle"}
+            "grid_points_per_s": round(n**3 / t, 1), "cores": oracle.threads(), "kind": "oracle"}
 
 
 def run_reference(args, world, rank):
@@ -771,11 +771,12 @@ def run_transfer(n: int):
     kept = (2 * kd + 1) ** 2 * (kd + 1)
     import oracle
 
-    uo = _oracle_state(64)
-    ocpu = oracle_beside("oracle right-hand side + T(K) of the decaying field's initial state", 64,
+    uo = _oracle_state(256)
+    ocpu = oracle_beside("oracle right-hand side + T(K) of the decaying field's initial state", 256,
                          lambda: oracle.transfer_spectrum(uo, oracle.ns_rhs(uo)), "calls/s")
-    ocpu_shell = oracle_beside("oracle shell-to-shell matrix, octave shells", 32,
-                               lambda: oracle.shell_transfer(_oracle_state(32), [0, 1, 2, 4, 8, 16, 29]),
+    u128 = _oracle_state(128)
+    ocpu_shell = oracle_beside("oracle shell-to-shell matrix, octave shells", 128,
+                               lambda: oracle.shell_transfer(u128, [0, 1, 2, 4, 8, 16, 32, 64, 112]),
                                "calls/s")
     print(json.dumps({"workload": f"{n}^3 decaying field (k0={K0}, E={E0}, seed {SEED}) after 50 steps "
                                   f"nu={NU}, dt={DT}",
@@ -837,8 +838,8 @@ def run_schemes(n: int, steps: int):
     fk.fftk_plan_destroy(plan)
     import oracle
 
-    uo = _oracle_state(64)
-    out["oracle_cpu"] = oracle_beside("oracle RK4 step", 64, lambda: oracle.ns_step_rk4(uo, NU, DT, 1), "steps/s")
+    uo = _oracle_state(128)
+    out["oracle_cpu"] = oracle_beside("oracle RK4 step", 128, lambda: oracle.ns_step_rk4(uo, NU, DT, 1), "steps/s")
     print(json.dumps({"workload": f"{n}^3 decaying turbulence, nu={NU}, dt={DT}, seed {SEED}",
                       "peak_GBps": hbm, "peak_kind": peak_kind, **out}), flush=True)
 
@@ -878,14 +879,21 @@ def run_rbc(n: int, steps: int):
         torch.cuda.synchronize(dev)
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
+        fk.fftk_profile_enable(plan, True)
         a.record()
         fk.tarang_rbc_step(plan, s.data_ptr(), 1e8, 1.0, 1e-3, steps, scheme, st, basis=basis)
         b.record()
         b.synchronize()
         ms = a.elapsed_time(b) / steps
+        kern = {}
+        for k in range(fk.fftk_kernel_kinds()):
+            kms, cnt = fk.fftk_profile_read(plan, k)
+            if cnt:
+                kern[fk.fftk_kernel_name(k)] = {"launches": cnt, "ms_per_step": round(kms / steps, 4)}
+        fk.fftk_profile_enable(plan, False)
         fin = bool(torch.isfinite(s).all())
         out[name] = {"steps_per_s": round(1e3 / ms, 3), "ms_per_step": round(ms, 4), "transforms_per_step": ntr,
-                     "ms_per_transform_incl_pointwise": round(ms / ntr, 4), "finite": fin}
+                     "ms_per_transform_incl_pointwise": round(ms / ntr, 4), "finite": fin, "kernels": kern}
         if name == "rk4":  # kinetic and thermal fluxes of the state reached (Sec. 7)
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
@@ -901,8 +909,8 @@ def run_rbc(n: int, steps: int):
     fk.fftk_plan_destroy(plan)
     import oracle
 
-    so = np.concatenate([_oracle_state(64), _oracle_state(64)[2:3]])
-    out["oracle_cpu"] = oracle_beside("oracle RK4 convection step (cube)", 64,
+    so = np.concatenate([_oracle_state(128), _oracle_state(128)[2:3]])
+    out["oracle_cpu"] = oracle_beside("oracle RK4 convection step (cube)", 128,
                                       lambda: oracle.rbc_step(so, 1e8, 1.0, 1e-3, 1, 1), "steps/s")
     print(json.dumps({"workload": f"{n}^3 Rayleigh-Benard (FFF), Ra=1e8, Pr=1, dt=1e-3, random-phase u (k0={K0}), "
                                   f"theta = u_z, seed {SEED}", **out}), flush=True)
@@ -958,9 +966,9 @@ def run_radix3():
     import oracle
     import synth
 
-    f96 = synth.normal(SEED, 0, (96, 96, 96)).astype(np.float64)
-    ocpu = oracle_beside("oracle R2C + C2R pair, lines of 3*2^m by the DFT's definition", 96,
-                         lambda: oracle.irfft3(oracle.rfft3(f96), 96), "pairs/s")
+    f192 = synth.normal(SEED, 0, (192, 192, 192)).astype(np.float64)
+    ocpu = oracle_beside("oracle R2C + C2R pair, lines of 3*2^m by the DFT's definition", 192,
+                         lambda: oracle.irfft3(oracle.rfft3(f192), 192), "pairs/s")
     print(json.dumps({"workload": "R2C+C2R pairs of normal(0,1), seed 0, 2^m and 3*2^m cubes", "peak_GBps": hbm,
                       "peak_kind": peak_kind, "sizes": rows, "oracle_cpu": ocpu}), flush=True)
 
@@ -1015,9 +1023,9 @@ def run_bases(n: int):
     import oracle
     import synth
 
-    f64 = synth.normal(SEED, 0, (64, 64, 64)).astype(np.float64)
-    ocpu = oracle_beside("oracle SFF forward + inverse pair (sine axis by its definition, O(n^4))", 64,
-                         lambda: oracle.itransform3(oracle.transform3(f64, "SFF"), 64, "SFF"), "pairs/s")
+    f128 = synth.normal(SEED, 0, (128, 128, 128)).astype(np.float64)
+    ocpu = oracle_beside("oracle SFF forward + inverse pair (sine axis by its definition, O(n^4))", 128,
+                         lambda: oracle.itransform3(oracle.transform3(f128, "SFF"), 128, "SFF"), "pairs/s")
     print(json.dumps({"workload": f"{n}^3 forward + inverse pairs of normal(0,1), seed {SEED}, mixed bases",
                       "peak_GBps": hbm, "peak_kind": peak_kind, "bases": rows, "oracle_cpu": ocpu}), flush=True)
 

@@ -12,7 +12,7 @@ namespace fftk {
 const char* const kKernelNames[KK_COUNT] = {
     "z_r2c", "y_fwd", "x_fwd", "x_inv", "y_inv", "z_c2r",
     "ns_invx_curl", "ns_invy", "ns_z_product", "ns_fwdy", "ns_fwdx_update",
-    "ns_reduce", "aux", "sc_fwd", "sc_inv"};
+    "ns_reduce", "aux", "sc_fwd", "sc_inv", "rbc_prep", "rbc_z", "rbc_update"};
 
 bool is_pow2(long long v) { return v >= 1 && (v & (v - 1)) == 0; }
 bool is_pow2_or_3x(long long v) { return is_pow2(v) || (v % 3 == 0 && is_pow2(v / 3)); }

@@ -31,6 +31,9 @@ enum KernelKind : int {
   KK_AUX,
   KK_SC_FWD,
   KK_SC_INV,
+  KK_RBC_PREP,
+  KK_RBC_Z,
+  KK_RBC_UPDATE,
   KK_COUNT
 };
 extern const char* const kKernelNames[KK_COUNT];

@@ -455,7 +455,7 @@ static cudaError_t rbc_z_n(fftk_plan p, float2* w, const RBCSlots& sl, cudaStrea
   });
   if (attr_err != cudaSuccess) return attr_err;
   const long long lines = (long long)N * N;
-  LaunchScope ls(p, KK_AUX, st);
+  LaunchScope ls(p, KK_RBC_Z, st);
   k_rbc_z<N><<<(unsigned)((lines + C::LPC - 1) / C::LPC), C::THREADS, C::SMEM, st>>>(w, sl, twiddles(p, N));
   return cudaGetLastError();
 }
@@ -487,7 +487,7 @@ static cudaError_t rbc_stage(fftk_plan p, const float2* x, const float2* u0, flo
   if (basis == TARANG_RBC_SFF) {
     // w7 = [u_x, omega_y, omega_z, theta | u_y, u_z, omega_x]: sine group, cosine group
     {
-      LaunchScope ls(p, KK_AUX, st);
+      LaunchScope ls(p, KK_RBC_PREP, st);
       k_rbc_sff_prep<<<grid, 256, 0, st>>>(x, w, g);
     }
     e = launch_scpass_pruned(p, true, +1, w, w, 4, 1.f, st);
@@ -501,14 +501,14 @@ static cudaError_t rbc_stage(fftk_plan p, const float2* x, const float2* u0, flo
     if (e == cudaSuccess) e = launch_scpass_pruned(p, false, -1, w + 3 * g.M, w + 3 * g.M, 3, scale, st);
     if (e != cudaSuccess) return e;
     {
-      LaunchScope ls(p, KK_AUX, st);
+      LaunchScope ls(p, KK_RBC_UPDATE, st);
       k_rbc_sff_update<<<grid, 256, 0, st>>>(w, x, u0, r->s1, r->acc, out, g, upd, mode);
     }
     return cudaGetLastError();
   }
   // w7 = [u_x, u_y, u_z, omega_x, omega_y, omega_z, theta] -> [n_x, n_y, n_z, u_x theta, ...]
   {
-    LaunchScope ls(p, KK_AUX, st);
+    LaunchScope ls(p, KK_RBC_PREP, st);
     k_rbc_prep<<<grid, 256, 0, st>>>(x, w, g);
   }
   e = launch_pruned_x(p, +1, w, w, 7, 1.f, st);
@@ -519,7 +519,7 @@ static cudaError_t rbc_stage(fftk_plan p, const float2* x, const float2* u0, flo
   if (e == cudaSuccess) e = launch_pruned_x(p, -1, w, w, 6, scale, st);
   if (e != cudaSuccess) return e;
   {
-    LaunchScope ls(p, KK_AUX, st);
+    LaunchScope ls(p, KK_RBC_UPDATE, st);
     k_rbc_update<<<grid, 256, 0, st>>>(w, x, u0, r->s1, r->acc, out, g, upd, mode);
   }
   return cudaGetLastError();
