@@ -29,7 +29,7 @@ struct ZCfg {
 template <int N>
 __global__ void __launch_bounds__(ZCfg<N>::THREADS, ZCfg<N>::MINB)
     k_z_r2c(const float* __restrict__ in, float2* __restrict__ out, long long nlines,
-            const float2* __restrict__ tw, float scale, int kc) {  // tw: size-N table; k < kc stored
+            const float2* __restrict__ tw, float scale) {  // tw: size-N table
   using C = ZCfg<N>;
   constexpr int H = C::H, G = C::G, S = C::S;
   constexpr int LOGN = Log2<N>::value;
@@ -57,9 +57,9 @@ __global__ void __launch_bounds__(ZCfg<N>::THREADS, ZCfg<N>::MINB)
       const float2 D = csub(A, Bc);
       const float2 O = make_float2(0.5f * D.y, -0.5f * D.x);  // D / (2i)
       const float2 W = __ldg(&tw[k]);                          // exp(-2 pi i k / N)
-      if (k < kc) dst[k] = cscale(cadd(E, cmul(W, O)), scale);
+      dst[k] = cscale(cadd(E, cmul(W, O)), scale);
     }
-    if (j == 0 && H < kc) dst[H] = make_float2((v[0].x - v[0].y) * scale, 0.f);
+    if (j == 0) dst[H] = make_float2((v[0].x - v[0].y) * scale, 0.f);
   }
 }
 
@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(ZCfg<N>::THREADS, ZCfg<N>::MINB)
 template <int N>
 __global__ void __launch_bounds__(ZCfg<N>::THREADS, ZCfg<N>::MINB)
     k_z_c2r(const float2* __restrict__ in, float* __restrict__ out, long long nlines,
-            const float2* __restrict__ tw, int kc) {  // tw: size-N table; entries k >= kc read as 0
+            const float2* __restrict__ tw) {  // tw: size-N table
   using C = ZCfg<N>;
   constexpr int H = C::H, G = C::G, S = C::S;
   constexpr int LOGN = Log2<N>::value;
@@ -86,8 +86,8 @@ __global__ void __launch_bounds__(ZCfg<N>::THREADS, ZCfg<N>::MINB)
     const int k = j + m * S;
     float2 A = make_float2(0.f, 0.f), B = make_float2(0.f, 0.f);
     if (valid) {
-      if (k < kc) A = src[k];
-      if (H - k < kc) B = src[H - k];
+      A = src[k];
+      B = src[H - k];
     }
     if (k == 0) {
       A.y = 0.f;
@@ -149,22 +149,22 @@ __global__ void __launch_bounds__(CCfg<L>::THREADS, CCfg<L>::MINB)
 
 // ----------------------------------------------------------- launchers -----
 template <int N>
-static cudaError_t z_r2c_n(fftk_plan p, const float* in, float2* out, long long nl, float scale, int kc,
+static cudaError_t z_r2c_n(fftk_plan p, const float* in, float2* out, long long nl, float scale,
                            cudaStream_t st) {
   using C = ZCfg<N>;
   const long long blocks = (nl + C::LPC - 1) / C::LPC;
   LaunchScope ls(p, KK_Z_R2C, st);
-  k_z_r2c<N><<<(unsigned)blocks, C::THREADS, 0, st>>>(in, out, nl, twiddles(p, N), scale, kc);
+  k_z_r2c<N><<<(unsigned)blocks, C::THREADS, 0, st>>>(in, out, nl, twiddles(p, N), scale);
   return cudaGetLastError();
 }
 
 template <int N>
-static cudaError_t z_c2r_n(fftk_plan p, const float2* in, float* out, long long nl, int kc,
+static cudaError_t z_c2r_n(fftk_plan p, const float2* in, float* out, long long nl,
                            cudaStream_t st) {
   using C = ZCfg<N>;
   const long long blocks = (nl + C::LPC - 1) / C::LPC;
   LaunchScope ls(p, KK_Z_C2R, st);
-  k_z_c2r<N><<<(unsigned)blocks, C::THREADS, 0, st>>>(in, out, nl, twiddles(p, N), kc);
+  k_z_c2r<N><<<(unsigned)blocks, C::THREADS, 0, st>>>(in, out, nl, twiddles(p, N));
   return cudaGetLastError();
 }
 
@@ -189,13 +189,13 @@ static cudaError_t cpass_l(fftk_plan p, const float2* in, float2* out, long long
 #define FFTK_SIZES(X) X(2) X(4) X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096)
 
 cudaError_t launch_z_r2c(fftk_plan p, const float* in, float2* out, long long nlines, float scale,
-                         cudaStream_t st, int kc) {
+                         cudaStream_t st) {
   if (nlines <= 0) return cudaSuccess;
   if (!is_pow2(p->nz)) return launch_z3(p, true, in, out, nlines, scale, st);
   switch (p->nz) {
 #define CASE(n) \
   case n:       \
-    return z_r2c_n<n>(p, in, out, nlines, scale, kc, st);
+    return z_r2c_n<n>(p, in, out, nlines, scale, st);
     FFTK_SIZES(CASE)
 #undef CASE
   }
@@ -203,13 +203,13 @@ cudaError_t launch_z_r2c(fftk_plan p, const float* in, float2* out, long long nl
 }
 
 cudaError_t launch_z_c2r(fftk_plan p, const float2* in, float* out, long long nlines,
-                         cudaStream_t st, int kc) {
+                         cudaStream_t st) {
   if (nlines <= 0) return cudaSuccess;
   if (!is_pow2(p->nz)) return launch_z3(p, false, in, out, nlines, 1.f, st);
   switch (p->nz) {
 #define CASE(n) \
   case n:       \
-    return z_c2r_n<n>(p, in, out, nlines, kc, st);
+    return z_c2r_n<n>(p, in, out, nlines, st);
     FFTK_SIZES(CASE)
 #undef CASE
   }

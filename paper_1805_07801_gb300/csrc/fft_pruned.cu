@@ -1,15 +1,15 @@
 // Strided passes of an n^3 transform restricted to the 2/3-rule set (the
 // dealiasing of Sec. 2.2: modes with 3|k| >= n on any axis are zero), for
-// the solvers that run through the library's transforms (convection).
+// the convection solver (its z pass is fused with the products, rbc.cu).
 //
 // Inverse (spectrum -> real): the x pass reads only the kept k_x rows of the
 // kept (k_y, k_z) columns and writes whole x lines; the y pass reads the kept
 // k_y rows of the kept k_z columns for every x and writes whole y lines; the
-// z pass (fft_passes.cu with kc) reads k_z < kc.  Each pass reads exactly
-// what the previous one wrote.  Forward: the z pass writes k_z < kc, the y
-// pass reads whole y lines of those columns and writes the kept k_y rows,
-// the x pass writes the kept k_x rows of the kept columns; entries outside
-// the kept set are left undefined.
+// z pass then reads k_z < kc.  Each pass reads exactly what the previous one
+// wrote.  Forward: after a z pass that writes k_z < kc, the y pass reads
+// whole y lines of those columns and writes the kept k_y rows, the x pass
+// writes the kept k_x rows of the kept columns; entries outside the kept set
+// are left undefined.
 #include <mutex>
 
 #include "fft_engine.cuh"

@@ -98,13 +98,11 @@ struct LaunchScope {
 
 // ---------------------------------------------------------- FFT passes -----
 // z pass, real -> half complex, lines of nz reals -> nz/2+1 complex (scale applied).
-// kc: only k_z < kc is written (r2c) or read, the rest taken as 0 (c2r);
-// the default keeps every k_z
 cudaError_t launch_z_r2c(fftk_plan p, const float* in, float2* out, long long nlines, float scale,
-                         cudaStream_t st, int kc = 1 << 30);
+                         cudaStream_t st);
 // z pass, half complex -> real (unnormalised); Im of the k=0 and k=nz/2 terms ignored.
 cudaError_t launch_z_c2r(fftk_plan p, const float2* in, float* out, long long nlines,
-                         cudaStream_t st, int kc = 1 << 30);
+                         cudaStream_t st);
 // strided c2c pass: array [P][L][Q], transform along L (element stride Q),
 // in may equal out.  sign = -1 forward, +1 inverse; output multiplied by scale.
 cudaError_t launch_scpass(fftk_plan p, int L, bool sine, int dir, const float2* in, float2* out, long long P,
