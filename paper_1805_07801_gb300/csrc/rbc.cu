@@ -87,13 +87,15 @@ static fftk_status rbc_tables(fftk_plan p, double Ra, double Pr, double dt) {
 
 // w7 = (u, i k x u, theta) of the stage input x; the Nyquist derivative is 0
 __global__ void k_rbc_prep(const float2* __restrict__ x, float2* __restrict__ w7, NSGeom g) {
-  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < g.M;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int c = (int)(idx % g.h1);
-    const long long ab = idx / g.h1;
-    const int b = (int)(ab % g.n), a = (int)(ab / g.n);
-    // the pruned inverse passes read only the kept modes
-    if (!(kept_xy(a, g.n, g.kd) && kept_xy(b, g.n, g.kd) && c < g.kc)) continue;
+  // the kept modes only (the pruned inverse passes read nothing else),
+  // k_z fastest so that neighbouring threads touch neighbouring entries
+  const long long items = (long long)g.nk * g.nk * g.kc;
+  for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < items;
+       it += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(it % g.kc);
+    const long long ab = it / g.kc;
+    const int a = dense_to_a((int)(ab / g.nk), g.n, g.kd), b = dense_to_a((int)(ab % g.nk), g.n, g.kd);
+    const long long idx = ((long long)a * g.n + b) * g.h1 + c;
     const int ka = kwav(a, g.n), kb = kwav(b, g.n);
     const float kx = (2 * abs(ka) == g.n) ? 0.f : (float)ka, ky = (2 * abs(kb) == g.n) ? 0.f : (float)kb;
     const float kz = (2 * c == g.n) ? 0.f : (float)c;
@@ -123,12 +125,13 @@ __device__ __forceinline__ float2 mul_pair(float2 v, float2 E) {  // v * (hi + l
 // temperature with its own factors).  Outside the kept set nothing is written.
 __global__ void k_rbc_update(const float2* __restrict__ w7, const float2* x, const float2* u0, float2* s1,
                              float2* acc, float2* out, NSGeom g, RBCUpdate upd, int mode) {
-  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < g.M;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int c = (int)(idx % g.h1);
-    const long long ab = idx / g.h1;
-    const int b = (int)(ab % g.n), a = (int)(ab / g.n);
-    if (!(kept_xy(a, g.n, g.kd) && kept_xy(b, g.n, g.kd) && c < g.kc)) continue;
+  const long long items = (long long)g.nk * g.nk * g.kc;  // the kept modes, k_z fastest
+  for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < items;
+       it += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(it % g.kc);
+    const long long ab = it / g.kc;
+    const int a = dense_to_a((int)(ab / g.nk), g.n, g.kd), b = dense_to_a((int)(ab % g.nk), g.n, g.kd);
+    const long long idx = ((long long)a * g.n + b) * g.h1 + c;
     const int kx = kwav(a, g.n), ky = kwav(b, g.n), kz = c;
     const int k2 = kx * kx + ky * ky + kz * kz;
     const long long M = g.M;
@@ -199,22 +202,20 @@ __global__ void k_rbc_update(const float2* __restrict__ w7, const float2* x, con
 // 3 k_z < n.  A thread owns the wavenumber triple (k_x = a, k_y, k_z): the
 // cosine entry at index a and the sine entry at index a - 1.
 
-__device__ __forceinline__ bool sff_kept(int kx, int b, int c, const NSGeom& g) {
-  return 3 * kx < 2 * g.n && kept_xy(b, g.n, g.kd) && c < g.kc;
-}
-
 // w7 = [u_x, omega_y, omega_z, theta | u_y, u_z, omega_x]: sine group, then
 // cosine group (each contiguous, for one batched transform per group)
 __global__ void k_rbc_sff_prep(const float2* __restrict__ x, float2* __restrict__ w7, NSGeom g) {
   const long long M = g.M, rowa = (long long)g.n * g.h1;  // one step of the x index
-  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < M;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int c = (int)(idx % g.h1);
-    const long long ab = idx / g.h1;
-    const int b = (int)(ab % g.n), a = (int)(ab / g.n);
-    // the pruned inverse passes read only the kept modes (the sine entry of
-    // k_x = a is kept with the cosine one; k_x = n never is)
-    if (!sff_kept(a, b, c, g)) continue;
+  // the kept modes only (the pruned inverse passes read nothing else; the
+  // sine entry of k_x = a is kept with the cosine one, k_x = n never is)
+  const int nx = (2 * g.n - 1) / 3 + 1;  // k_x = 0 .. nx - 1 (3 k_x < 2n)
+  const long long items = (long long)nx * g.nk * g.kc;
+  for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < items;
+       it += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(it % g.kc);
+    const long long ab = it / g.kc;
+    const int a = (int)(ab / g.nk), b = dense_to_a((int)(ab % g.nk), g.n, g.kd);
+    const long long idx = ((long long)a * g.n + b) * g.h1 + c;
     const int kb = kwav(b, g.n);
     const float ky = (2 * abs(kb) == g.n) ? 0.f : (float)kb, kz = (2 * c == g.n) ? 0.f : (float)c;
     const float2 uy = x[idx + M], uz = x[idx + 2 * M];
@@ -271,12 +272,14 @@ __device__ __forceinline__ void rbc_entry_update(long long i, float2 n, float2 E
 __global__ void k_rbc_sff_update(const float2* __restrict__ w7, const float2* x, const float2* u0, float2* s1,
                                  float2* acc, float2* out, NSGeom g, RBCUpdate upd, int mode) {
   const long long M = g.M, rowa = (long long)g.n * g.h1;
-  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < M;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int c = (int)(idx % g.h1);
-    const long long ab = idx / g.h1;
-    const int b = (int)(ab % g.n), a = (int)(ab / g.n);
-    if (!sff_kept(a, b, c, g)) continue;
+  const int nx = (2 * g.n - 1) / 3 + 1;  // the kept modes, k_z fastest
+  const long long items = (long long)nx * g.nk * g.kc;
+  for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < items;
+       it += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(it % g.kc);
+    const long long ab = it / g.kc;
+    const int a = (int)(ab / g.nk), b = dense_to_a((int)(ab % g.nk), g.n, g.kd);
+    const long long idx = ((long long)a * g.n + b) * g.h1 + c;
     const int ky = kwav(b, g.n), kz = c, kx = a;
     const int k2 = kx * kx + ky * ky + kz * kz;
     const float fkx = (float)kx, fky = (float)ky, fkz = (float)kz;
