@@ -140,10 +140,11 @@ fftk_status fftk_inverse(fftk_plan p, const int *basis, const void *in, float *o
  * zero; the solver never reads them.
  * FP32 plans run the right-hand side in five fused kernels (inverse x with
  * the curl, inverse y, z transforms with u x omega, forward y, forward x with
- * projection and update).  FFTK_R32_SPLIT16 plans run it unfused through
- * fftk_c2r / fftk_r2c of the plan (radix-16 stages on the tensor cores, split
- * FP16 operands): curl, c2r of six fields, u x omega, r2c of three fields,
- * update; they use six more real fields of device memory. */
+ * projection and update).  FFTK_R32_SPLIT16 plans (n of 256 to 1024) run the
+ * x and y passes on the tensor cores (split FP16 radix-16 stages, restricted
+ * to the 2/3-rule set) around the same fused FP32 z kernel: curl on the kept
+ * modes, inverse x and y of six fields, z with u x omega, forward y and x of
+ * three fields, update. */
 /* Learned subgrid-stress model (not in the paper; see tarang_mlp_*): the
  * network maps the 5 invariants of the resolved velocity gradient A
  * (tr S^2, tr R^2, tr S^3, tr R^2 S, tr R^2 S^2 with S, R the symmetric and

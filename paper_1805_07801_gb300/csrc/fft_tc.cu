@@ -171,9 +171,15 @@ static void build_dft16_operands(int sign, std::vector<__half>& out) {
 
 
 // Strided pass [P][L][Q] along L with split-FP16 tensor-core radix-16 stages.
-template <int L, int SIGN>
+// PM = 0: every column q < Q.  PM = 1, 2: the pass of an L^3 spectrum
+// restricted to its 2/3-rule set, as the FP32 k_pcpass: x lines (rows of
+// stride L (L/2+1)) over the kept (k_y, k_z) columns (PM = 1), or y lines
+// (stride L/2+1) over the kept k_z columns of every x (PM = 2); the inverse
+// reads only kept rows, the forward writes only kept rows.  `outer` is the
+// number of k_y (PM = 1) or x (PM = 2) indices per batch element.
+template <int L, int SIGN, int PM>
 __global__ void __launch_bounds__(TC2<L>::THREADS, TC2<L>::MINB)
-    k_cpass_tc(const float2* in, float2* out, long long Q, long long qtiles, long long ntiles,
+    k_cpass_tc(const float2* in, float2* out, long long Q, long long qtiles, long long ntiles, int outer,
                const float2* __restrict__ tw, float out_scale,  // tw: size-L table
                const __half* __restrict__ bops, int* err) {
   using C = TC2<L>;
@@ -261,20 +267,46 @@ __global__ void __launch_bounds__(TC2<L>::THREADS, TC2<L>::MINB)
     return all;
   };
 
+  constexpr int KD = (L - 1) / 3;  // the 2/3 rule (PM > 0)
+  auto kept = [](int row) { return row <= KD || row >= L - KD; };
   for (long long tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
-    const long long pl = tile / qtiles;
-    const long long q0 = (tile - pl * qtiles) * T;
-    const bool valid = q0 + c < Q;
-    float2* dst = out + pl * (long long)L * Q + q0 + c;
+    long long col0, rs;
+    bool valid;
+    if constexpr (PM == 0) {
+      const long long pl = tile / qtiles;
+      const long long q0 = (tile - pl * qtiles) * T;
+      valid = q0 + c < Q;
+      col0 = pl * (long long)L * Q + q0 + c;
+      rs = Q;
+    } else {
+      constexpr long long H1 = L / 2 + 1, MM = (long long)L * L * H1;
+      const long long bo = tile / qtiles;
+      const int kz = (int)(tile - bo * qtiles) * T + c;
+      const long long b = bo / outer;
+      const int o = (int)(bo - b * outer);
+      valid = kz < KD + 1;
+      if constexpr (PM == 1) {
+        const int ay = o <= KD ? o : L - (2 * KD + 1 - o);
+        col0 = b * MM + (long long)ay * H1 + kz;
+        rs = (long long)L * H1;
+      } else {
+        col0 = b * MM + (long long)o * L * H1 + kz;
+        rs = H1;
+      }
+    }
+    float2* dst = out + col0;
     // ---- stage 0: R0-point DFTs of x[a + 256 m] for a = a0 + 16 (A1 u + i)
     float2 z[A1][R0];
     {
-      const float2* src = in + pl * (long long)L * Q + q0 + c;
+      const float2* src = in + col0;
 #pragma unroll
       for (int i = 0; i < A1; ++i) {
         const int a = a0 + 16 * (A1 * u + i);
 #pragma unroll
-        for (int m = 0; m < R0; ++m) z[i][m] = valid ? src[(long long)(a + 256 * m) * Q] : make_float2(0.f, 0.f);
+        for (int m = 0; m < R0; ++m) {
+          const bool rd = valid && (PM == 0 || SIGN < 0 || kept(a + 256 * m));
+          z[i][m] = rd ? src[(long long)(a + 256 * m) * rs] : make_float2(0.f, 0.f);
+        }
       }
     }
     float mx = 0.f;
@@ -341,8 +373,11 @@ __global__ void __launch_bounds__(TC2<L>::THREADS, TC2<L>::MINB)
       tc::ld32(row_addr, d);
       if (valid) {
 #pragma unroll
-        for (int k1 = 0; k1 < 16; ++k1)
-          dst[(long long)(R0 * (a0 + 16 * k1) + u) * Q] = make_float2(d[2 * k1] * f, d[2 * k1 + 1] * f);
+        for (int k1 = 0; k1 < 16; ++k1) {
+          const int row = R0 * (a0 + 16 * k1) + u;
+          if (PM == 0 || SIGN > 0 || kept(row))
+            dst[(long long)row * rs] = make_float2(d[2 * k1] * f, d[2 * k1 + 1] * f);
+        }
       }
     }
   }
@@ -354,7 +389,8 @@ __global__ void __launch_bounds__(TC2<L>::THREADS, TC2<L>::MINB)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(C::COLS));
 }
 
-template <int L, int SIGN>
+// P: batch (PM = 0: P lines of Q columns; PM > 0: P spectra of L^3)
+template <int L, int SIGN, int PM>
 static cudaError_t cpass_tc_l(fftk_plan p, const float2* in, float2* out, long long P, long long Q,
                               float scale, int kind, cudaStream_t st) {
   using C = TC2<L>;
@@ -362,10 +398,10 @@ static cudaError_t cpass_tc_l(fftk_plan p, const float2* in, float2* out, long l
   static cudaError_t attr_err = cudaSuccess;
   static int per_sm = 1;
   std::call_once(once, [] {
-    attr_err = cudaFuncSetAttribute(k_cpass_tc<L, SIGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    attr_err = cudaFuncSetAttribute(k_cpass_tc<L, SIGN, PM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)C::SMEM);
     if (attr_err == cudaSuccess &&
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cpass_tc<L, SIGN>, C::THREADS, C::SMEM) !=
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cpass_tc<L, SIGN, PM>, C::THREADS, C::SMEM) !=
             cudaSuccess)
       per_sm = 1;
     if (per_sm > 512 / C::COLS) per_sm = 512 / C::COLS;  // TMEM: 512 columns per SM
@@ -375,14 +411,16 @@ static cudaError_t cpass_tc_l(fftk_plan p, const float2* in, float2* out, long l
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const long long qtiles = (Q + C::T - 1) / C::T;
-  const long long ntiles = P * qtiles;
+  constexpr int KD = (L - 1) / 3;
+  const int outer = PM == 1 ? 2 * KD + 1 : L;
+  const long long qtiles = PM == 0 ? (Q + C::T - 1) / C::T : (KD + 1 + C::T - 1) / C::T;
+  const long long ntiles = PM == 0 ? P * qtiles : P * outer * qtiles;
   const long long cap = (long long)per_sm * sms;
   const int blocks = (int)(ntiles < cap ? ntiles : cap);
   const __half* bops = p->d_dft16 + (SIGN < 0 ? 0 : 2 * 32 * 64);
   LaunchScope ls(p, kind, st);
-  k_cpass_tc<L, SIGN><<<blocks, C::THREADS, C::SMEM, st>>>(in, out, Q, qtiles, ntiles, twiddles(p, L), scale,
-                                                         bops, p->d_err);
+  k_cpass_tc<L, SIGN, PM><<<blocks, C::THREADS, C::SMEM, st>>>(in, out, Q, qtiles, ntiles, outer, twiddles(p, L),
+                                                             scale, bops, p->d_err);
   return cudaGetLastError();
 }
 
@@ -393,13 +431,32 @@ cudaError_t launch_cpass_tc(fftk_plan p, int L, int sign, const float2* in, floa
   if (P <= 0 || Q <= 0) return cudaSuccess;
 #define TC_CASE(n)                                                              \
   case n:                                                                       \
-    return sign < 0 ? cpass_tc_l<n, -1>(p, in, out, P, Q, scale, kind, st)      \
-                    : cpass_tc_l<n, +1>(p, in, out, P, Q, scale, kind, st);
+    return sign < 0 ? cpass_tc_l<n, -1, 0>(p, in, out, P, Q, scale, kind, st)   \
+                    : cpass_tc_l<n, +1, 0>(p, in, out, P, Q, scale, kind, st);
   switch (L) {
     TC_CASE(256)
     TC_CASE(512)
     TC_CASE(1024)
     TC_CASE(2048)
+  }
+#undef TC_CASE
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_cpass_tc_pruned(fftk_plan p, int axis, int sign, const float2* in, float2* out, long long B,
+                                   float scale, int kind, cudaStream_t st) {
+  if (B <= 0) return cudaSuccess;
+#define TC_CASE(n)                                                                                   \
+  case n:                                                                                            \
+    if (axis == 0)                                                                                   \
+      return sign < 0 ? cpass_tc_l<n, -1, 1>(p, in, out, B, 0, scale, kind, st)                      \
+                      : cpass_tc_l<n, +1, 1>(p, in, out, B, 0, scale, kind, st);                     \
+    return sign < 0 ? cpass_tc_l<n, -1, 2>(p, in, out, B, 0, scale, kind, st)                        \
+                    : cpass_tc_l<n, +1, 2>(p, in, out, B, 0, scale, kind, st);
+  switch (axis == 0 ? p->nx : p->ny) {
+    TC_CASE(256)
+    TC_CASE(512)
+    TC_CASE(1024)
   }
 #undef TC_CASE
   return cudaErrorInvalidValue;

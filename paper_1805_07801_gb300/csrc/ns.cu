@@ -617,6 +617,19 @@ struct NSLaunch {
     return err;
   }
 
+  // The fused z pass alone (c2r of the six fields in s->w, u x omega, r2c of
+  // n into fields 0..2), for the split-precision right-hand side.
+  static cudaError_t z(fftk_plan p, cudaStream_t st) {
+    using Z = NZCfg<N>;
+    cudaError_t e = attrs();
+    if (e != cudaSuccess) return e;
+    NSWork* s = p->ns;
+    LaunchScope ls(p, KK_NS_Z, st);
+    const long long lines = (long long)N * N;
+    k_ns_z<N><<<(unsigned)((lines + Z::LPC - 1) / Z::LPC), Z::THREADS, Z::SMEM, st>>>(s->w, s->g, twiddles(p, N));
+    return cudaGetLastError();
+  }
+
   // One evaluation of N(u) followed by the update selected by `mode`.
   static cudaError_t rhs(fftk_plan p, const float2* u, const float2* u0, const float2* u1,
                          float2* out, const NSUpdate& upd, int mode, const float2* extra,
@@ -662,18 +675,21 @@ struct NSLaunch {
 };
 
 // ---------------------------------------------- split-precision NS step ----
-// Plans of dtype FFTK_R32_SPLIT16 evaluate the right-hand side unfused through
-// the library's own transforms, whose radix-16 stages then run on the tensor
-// cores: u and omega = i k x u on the spectrum, c2r of the six fields, n = u x
-// omega in real space, r2c of n, and the per-mode update of the fused path.
+// Plans of dtype FFTK_R32_SPLIT16 evaluate the right-hand side with the x and
+// y passes on the tensor cores (split FP16 radix-16 stages, restricted to the
+// 2/3-rule set): u and omega = i k x u on the kept modes, inverse x and y
+// passes of the six fields, the fused FP32 z pass (u x omega in registers),
+// forward y and x passes of n, and the per-mode update of the fused path.
 
-// w6 = (u, i k x u); the derivative of the Nyquist wavenumber is 0
+// w6 = (u, i k x u) on the kept modes; the derivative of the Nyquist wavenumber is 0
 __global__ void k_curl_full(const float2* __restrict__ u, float2* __restrict__ w6, NSGeom g) {
-  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < g.M;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int c = (int)(idx % g.h1);
-    const long long ab = idx / g.h1;
-    const int b = (int)(ab % g.n), a = (int)(ab / g.n);
+  const long long items = (long long)g.nk * g.nk * g.kc;  // k_z fastest
+  for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < items;
+       it += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(it % g.kc);
+    const long long ab = it / g.kc;
+    const int a = dense_to_a((int)(ab / g.nk), g.n, g.kd), b = dense_to_a((int)(ab % g.nk), g.n, g.kd);
+    const long long idx = ((long long)a * g.n + b) * g.h1 + c;
     const int ka = kwav(a, g.n), kb = kwav(b, g.n);
     const float kx = (2 * abs(ka) == g.n) ? 0.f : (float)ka, ky = (2 * abs(kb) == g.n) ? 0.f : (float)kb;
     const float kz = (2 * c == g.n) ? 0.f : (float)c;
@@ -687,18 +703,6 @@ __global__ void k_curl_full(const float2* __restrict__ u, float2* __restrict__ w
   }
 }
 
-// n = u x omega in place of u (fields 0..2 of the six real fields)
-__global__ void k_cross_real(float* __restrict__ r6, long long R) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < R;
-       i += (long long)gridDim.x * blockDim.x) {
-    const float ux = r6[i], uy = r6[R + i], uz = r6[2 * R + i];
-    const float wx = r6[3 * R + i], wy = r6[4 * R + i], wz = r6[5 * R + i];
-    r6[i] = uy * wz - uz * wy;
-    r6[R + i] = uz * wx - ux * wz;
-    r6[2 * R + i] = ux * wy - uy * wx;
-  }
-}
-
 // the update of every kept mode from n_hat (already scaled by the transform)
 __global__ void k_update_full(const float2* __restrict__ nh, const float2* u0, const float2* u1, float2* out,
                               NSGeom g, NSUpdate upd, int mode, const float2* __restrict__ extra) {
@@ -707,37 +711,44 @@ __global__ void k_update_full(const float2* __restrict__ nh, const float2* u0, c
     const double ef = *upd.ef;
     gforce = ef > 0.0 ? (float)(upd.feps / (2.0 * ef)) : 0.f;
   }
-  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < g.M;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int c = (int)(idx % g.h1);
-    const long long ab = idx / g.h1;
-    const int b = (int)(ab % g.n), a = (int)(ab / g.n);
-    if (!(kept_xy(a, g.n, g.kd) && kept_xy(b, g.n, g.kd) && c < g.kc)) continue;
+  const long long items = (long long)g.nk * g.nk * g.kc;  // the kept modes, k_z fastest
+  for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < items;
+       it += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(it % g.kc);
+    const long long ab = it / g.kc;
+    const int a = dense_to_a((int)(ab / g.nk), g.n, g.kd), b = dense_to_a((int)(ab % g.nk), g.n, g.kd);
+    const long long idx = ((long long)a * g.n + b) * g.h1 + c;
     ns_mode_update(nh[idx], nh[idx + g.M], nh[idx + 2 * g.M], kwav(a, g.n), kwav(b, g.n), c, idx, g.M, upd, mode,
                    gforce, u0, u1, extra, out);
   }
 }
 
+static cudaError_t ns_z_dispatch(fftk_plan p, cudaStream_t st);
+
 static cudaError_t ns_rhs_split(fftk_plan p, const float2* u, const float2* u0, const float2* u1, float2* out,
                                 const NSUpdate& upd, int mode, const float2* extra, cudaStream_t st) {
   NSWork* s = p->ns;
   const NSGeom g = s->g;
-  const long long R = (long long)g.n * g.n * g.n;
-  if (!s->r6) {
-    cudaError_t e = cudaMalloc(&s->r6, sizeof(float) * 6 * (size_t)R);
-    if (e != cudaSuccess) return e;
-  }
   const unsigned grid = 152 * 8;
+  const bool tc = cpass_tc_supported(g.n) && g.n <= 1024;
+  const float scale = (float)(1.0 / ((double)g.n * g.n * g.n));
   {
     LaunchScope ls(p, KK_AUX, st);
     k_curl_full<<<grid, 256, 0, st>>>(u, s->w, g);
   }
-  if (fftk_c2r(p, s->w, s->r6, 6, st) != FFTK_OK) return cudaErrorLaunchFailure;
-  {
-    LaunchScope ls(p, KK_AUX, st);
-    k_cross_real<<<grid, 256, 0, st>>>(s->r6, R);
-  }
-  if (fftk_r2c(p, s->r6, s->w, 3, st) != FFTK_OK) return cudaErrorLaunchFailure;
+  cudaError_t e = tc ? launch_cpass_tc_pruned(p, 0, +1, s->w, s->w, 6, 1.f, KK_X_INV, st)
+                     : launch_pruned_x(p, +1, s->w, s->w, 6, 1.f, st);
+  if (e == cudaSuccess)
+    e = tc ? launch_cpass_tc_pruned(p, 1, +1, s->w, s->w, 6, 1.f, KK_Y_INV, st)
+           : launch_pruned_y(p, +1, s->w, s->w, 6, 1.f, st);
+  if (e == cudaSuccess) e = ns_z_dispatch(p, st);
+  if (e == cudaSuccess)
+    e = tc ? launch_cpass_tc_pruned(p, 1, -1, s->w, s->w, 3, 1.f, KK_Y_FWD, st)
+           : launch_pruned_y(p, -1, s->w, s->w, 3, 1.f, st);
+  if (e == cudaSuccess)
+    e = tc ? launch_cpass_tc_pruned(p, 0, -1, s->w, s->w, 3, scale, KK_X_FWD, st)
+           : launch_pruned_x(p, -1, s->w, s->w, 3, scale, st);
+  if (e != cudaSuccess) return e;
   {
     LaunchScope ls(p, KK_AUX, st);
     k_update_full<<<grid, 256, 0, st>>>(s->w, u0, u1, out, g, upd, mode, extra);
@@ -746,6 +757,17 @@ static cudaError_t ns_rhs_split(fftk_plan p, const float2* u, const float2* u0, 
 }
 
 #define NS_SIZES(X) X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024)
+
+static cudaError_t ns_z_dispatch(fftk_plan p, cudaStream_t st) {
+  switch (p->nx) {
+#define CASE(n) \
+  case n:       \
+    return NSLaunch<n>::z(p, st);
+    NS_SIZES(CASE)
+#undef CASE
+  }
+  return cudaErrorInvalidValue;
+}
 
 static cudaError_t ns_rhs_dispatch(fftk_plan p, const float2* u, const float2* u0, const float2* u1,
                                    float2* out, const NSUpdate& upd, int mode, const float2* extra,

@@ -59,7 +59,7 @@ struct NSWork {
   double* dout = nullptr;  // diag result (device)
   double* hout = nullptr;  // diag result (pinned host)
   fftk_sgs_work* sgs = nullptr;  // learned-closure scratch
-  float* r6 = nullptr;     // 6 real fields (unfused split-precision right-hand side)
+  float* r6 = nullptr;     // 6 real fields (shell-to-shell transfer)
   float* r3 = nullptr;     // 3 real fields (shell-to-shell transfer: the advection term)
   float2* acc = nullptr;   // 3 fields (RK4 accumulator)
   RBCWork* rbc = nullptr;  // Rayleigh-Benard scratch (allocated on first use)
