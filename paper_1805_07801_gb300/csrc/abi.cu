@@ -238,6 +238,8 @@ static cudaError_t strided_pass(fftk_plan p, int L, int sign, const float2* in, 
   if (!is_pow2(L)) return launch_cpass3(p, L, sign, in, out, P, Q, scale, kind, st);
   if (p->dtype == FFTK_R32_SPLIT16 && cpass_tc_supported(L))
     return launch_cpass_tc(p, L, sign, in, out, P, Q, scale, kind, st);
+  cudaError_t e = cudaSuccess;
+  if (launch_cpass_tma(p, L, sign, in, out, P, Q, scale, kind, st, &e)) return e;
   return launch_cpass(p, L, sign, in, out, P, Q, scale, kind, st);
 }
 

@@ -132,6 +132,11 @@ cudaError_t launch_cpass(fftk_plan p, int L, int sign, const float2* in, float2*
 
 // split-FP16 tensor-core strided pass (FFTK_R32_SPLIT16), L in {256, 512, 1024, 2048}
 bool cpass_tc_supported(int L);
+// strided c2c pass with TMA tile loads for lines of 512 points: false
+// (nothing launched) where the layout does not allow TMA (row stride Q odd,
+// base not 16-byte aligned); otherwise true with the launch status in *e
+bool launch_cpass_tma(fftk_plan p, int L, int sign, const float2* in, float2* out, long long P, long long Q,
+                      float scale, int kind, cudaStream_t st, cudaError_t* e);
 // the split-FP16 pass restricted to the 2/3-rule set of an n^3 spectrum
 // (axis 0: x lines, 1: y lines; n of 256, 512 or 1024), as launch_pruned_x/y
 cudaError_t launch_cpass_tc_pruned(fftk_plan p, int axis, int sign, const float2* in, float2* out, long long B,

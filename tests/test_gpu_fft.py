@@ -68,6 +68,10 @@ SHAPES = [
     (1, 1, 2), (2, 2, 2), (1, 1, 8), (8, 4, 2), (4, 8, 16), (16, 1, 32), (64, 64, 64),
     (32, 128, 16), (128, 16, 256), (2, 512, 4), (1024, 2, 2), (8, 8, 4096), (4, 2048, 4),
     (2048, 2, 4), (4096, 1, 2), (1, 4096, 2), (256, 256, 8),
+    # 512-point x lines with an even row stride ny (nz/2+1) take the TMA
+    # pass (ragged last tile at 40 columns); the others are ragged tiles of
+    # the plain pass for 1024- and 2048-point lines
+    (1024, 2, 8), (512, 8, 8), (2048, 1, 8), (4, 1024, 8),
 ]
 
 
@@ -105,8 +109,8 @@ def test_c2r_non_hermitian_input_is_line_wise(fk, oracle_mod, shape):
     assert rel_l2(g, go) < REL
 
 
-def test_batched_equals_separate(fk, oracle_mod):
-    shape, B = (16, 32, 8), 3
+@pytest.mark.parametrize("shape, B", [((16, 32, 8), 3), ((512, 4, 4), 2), ((1024, 4, 4), 2), ((8, 512, 4), 2)])
+def test_batched_equals_separate(fk, oracle_mod, shape, B):
     f = np.stack([synth.uniform_pm1(0, b, shape) for b in range(B)])
     with Plan(fk, shape) as plan:
         Fg = gpu_r2c(fk, plan, f, batch=B)
