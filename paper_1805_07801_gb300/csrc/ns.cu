@@ -11,38 +11,11 @@
 //   5. ns_fwdx      : forward x pass + 1/N^3 + 2/3 dealias + projection
 //                     + forcing + the RK2 integrating-factor update
 //
-// Dealiasing (2/3 rule, "filling up only 2/3 of the array in each direction")
-// is exploited throughout: modes with 3|k| >= n on any axis are zero in the
-// state, so every pass reads only the rows and columns that can be nonzero
-// and writes only those a later pass reads.  The arrays keep the full
-// [n][n][n/2+1] layout; the untouched parts are never read.
-#include <cmath>
-#include <cstring>
-#include <mutex>
-#include <new>
-#include <vector>
-
-#include "fft_engine.cuh"
-#include "ns_common.cuh"
-
-// Pseudo-spectral incompressible Navier-Stokes (paper Sec. 2.2, Eqs. (7)-(8))
-// in rotational form, fused into the FFT passes of Sec. 3.
-//
-// One evaluation of the nonlinear term is five kernels:
-//   1. ns_invx_curl : uhat (3) -> inverse x pass of u and omega = i k x u (6)
-//   2. ns_invy      : inverse y pass of the 6 fields
-//   3. ns_z_product : per z line: c2r of the 6 fields, n = u x omega in
-//                     registers, r2c of the 3 products (real fields never
-//                     touch global memory)
-//   4. ns_fwdy      : forward y pass of the 3 fields
-//   5. ns_fwdx      : forward x pass + 1/N^3 + 2/3 dealias + projection
-//                     + forcing + the RK2 integrating-factor update
-//
-// Dealiasing (2/3 rule, "filling up only 2/3 of the array in each direction")
-// is exploited throughout: modes with 3|k| >= n on any axis are zero in the
-// state, so every pass reads only the rows and columns that can be nonzero
-// and writes only those a later pass reads.  The arrays keep the full
-// [n][n][n/2+1] layout; the untouched parts are never read.
+// The 2/3 rule is used throughout, not only to zero the products: modes
+// with 3|k| >= n on any axis are zero in the state, so every pass reads only
+// the rows and columns that can be nonzero and writes only those a later
+// pass reads.  The arrays keep the full [n][n][n/2+1] layout; the untouched
+// parts are never read.
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -51,6 +24,8 @@
 
 #include "fft_engine.cuh"
 #include "internal.h"
+#include "ns_common.cuh"
+#include "tcgen05.cuh"
 
 namespace fftk {
 // ------------------------------------------------------------ x/y config ---
