@@ -25,7 +25,6 @@
 #include "fft_engine.cuh"
 #include "internal.h"
 #include "ns_common.cuh"
-#include "tcgen05.cuh"
 
 namespace fftk {
 // ------------------------------------------------------------ x/y config ---
