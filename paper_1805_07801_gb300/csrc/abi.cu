@@ -5,6 +5,7 @@
 #include <new>
 #include <vector>
 
+#include "fft_engine.cuh"
 #include "internal.h"
 
 namespace fftk {
@@ -157,16 +158,32 @@ extern "C" fftk_status fftk_plan_create(int nx, int ny, int nz, fftk_dtype dtype
   // power of two L <= 4 LT, exp(-2 pi i m / L), m < L, at offset L (8 LT
   // values; the sizes above LT are the sine/cosine passes' quarter waves).
   const int ltab = 4 * lt;
-  std::vector<float2> h(2 * (size_t)ltab, make_float2(1.f, 0.f));
+  std::vector<float2> h((size_t)fftk::kStageTwiddles + 2 * (size_t)ltab, make_float2(1.f, 0.f));
+  float2* pyr = h.data() + fftk::kStageTwiddles;
   const double two_pi = 6.283185307179586476925286766559;
   for (int L = 1; L <= ltab; L *= 2)
     for (int m = 0; m < L; ++m) {
       const double ang = two_pi * (double)m / (double)L;
-      h[(size_t)L + m] = make_float2((float)std::cos(ang), (float)(-std::sin(ang)));
+      pyr[(size_t)L + m] = make_float2((float)std::cos(ang), (float)(-std::sin(ang)));
     }
-  e = cudaMalloc(&p->d_tw, sizeof(float2) * h.size());
-  if (e == cudaSuccess)
-    e = cudaMemcpy(p->d_tw, h.data(), sizeof(float2) * h.size(), cudaMemcpyHostToDevice);
+  // Below the pyramid, the line engine's per-stage tables: for each stage
+  // span M (a power of two up to the longest line) and radix R, the entry
+  // r (M/R) + k is exp(-2 pi i r k / M), r < R, k < M/R.
+  for (int M = 4; M <= lt && M <= 4096; M *= 2)
+    for (int R = 2; R <= 16 && R <= M / 2; R *= 2) {
+      const int ns = M / R;
+      for (int r = 0; r < R; ++r)
+        for (int k = 0; k < ns; ++k) {
+          const double ang = two_pi * (double)(r * k) / (double)M;
+          h[(size_t)fftk::stage_tw_offset(M, R) + (size_t)r * ns + k] =
+              make_float2((float)std::cos(ang), (float)(-std::sin(ang)));
+        }
+    }
+  e = cudaMalloc(&p->d_tw_alloc, sizeof(float2) * h.size());
+  if (e == cudaSuccess) {
+    p->d_tw = p->d_tw_alloc + fftk::kStageTwiddles;
+    e = cudaMemcpy(p->d_tw_alloc, h.data(), sizeof(float2) * h.size(), cudaMemcpyHostToDevice);
+  }
   // tables of size 3 * 2^j for the radix-3 lines, at offset L (2 L3 values)
   int lt3 = 0;
   for (int d : {nx, ny, nz})
@@ -188,7 +205,7 @@ extern "C" fftk_status fftk_plan_create(int nx, int ny, int nz, fftk_dtype dtype
   if (e != cudaSuccess) {
     fftk_status s = from_cuda(e);
     cudaGetLastError();
-    if (p->d_tw) cudaFree(p->d_tw);
+    if (p->d_tw_alloc) cudaFree(p->d_tw_alloc);
     if (p->d_tw3) cudaFree(p->d_tw3);
     if (p->d_err) cudaFree(p->d_err);
     if (p->d_dft16) cudaFree(p->d_dft16);
@@ -205,7 +222,7 @@ extern "C" fftk_status fftk_plan_destroy(fftk_plan p) {
   if (!p) return FFTK_ERR_INVALID_ARG;
   cudaDeviceSynchronize();
   ns_free(p);
-  if (p->d_tw) cudaFree(p->d_tw);
+  if (p->d_tw_alloc) cudaFree(p->d_tw_alloc);
   if (p->d_tw3) cudaFree(p->d_tw3);
   if (p->d_err) cudaFree(p->d_err);
   if (p->d_dft16) cudaFree(p->d_dft16);

@@ -196,11 +196,24 @@ struct LineX {
 };
 
 // ---------------------------------------------------------------- engine ---
-// Twiddle tables: the plan holds, for every power of two L' <= LT, the table
-// exp(-2 pi i m / L'), m < L', at offset L' of one array (entries computed in
-// FP64 on the host and rounded once to FP32).  A kernel gets the table of
-// size 2^TL >= L; the engine's index shift TL - log2(stage span) is a
-// compile-time constant.
+// Twiddle tables: the plan holds, for every power of two L' <= 4 LT, the
+// table exp(-2 pi i m / L'), m < L', at offset L' of one array (entries
+// computed in FP64 on the host and rounded once to FP32).  A kernel gets the
+// table of size 2^TL >= L, which locates the array's base at compile time.
+//
+// The stages read per-stage tables.  A stage of span M = NS R (radix R after
+// NS points) multiplies input r of butterfly k by exp(-2 pi i r k / M).  In a
+// z line one warp holds 32 butterflies, and a gather from the size-L table
+// at index r k L / M spreads each load over up to 32 scattered entries; so
+// the plan also stores, for every M <= 4096 and R in {2, 4, 8, 16}, the table
+// exp(-2 pi i r k / M) r-major (entry r NS + k), where a warp's k are
+// consecutive.  These tables lie kStageTwiddles entries below the base of
+// the pyramid (the same FP64-built values, rounded the same way).
+constexpr int kStageTwiddles = 32768;
+__host__ __device__ constexpr int stage_tw_offset(int M, int R) {
+  return 4 * M + (R == 2 ? 0 : (R == 4 ? 1 : (R == 8 ? 2 : 3))) * M;
+}
+
 template <int L, int G>
 struct Shape {
   static_assert(L >= 1 && (L & (L - 1)) == 0, "L must be a power of two");
@@ -223,7 +236,6 @@ struct Stage {
       constexpr int B = G / R;   // butterflies per thread
       constexpr int S = L / G;   // threads per line
       constexpr bool LAST = (NS * R == L);
-      constexpr int LOG_NSR = Log2<NS * R>::value;
 #pragma unroll
       for (int t = 0; t < B; ++t) {
         const int b = j + t * S;   // butterfly index in [0, L/R)
@@ -232,10 +244,12 @@ struct Stage {
 #pragma unroll
         for (int r = 0; r < R; ++r) a[r] = v[t + r * B];
         if constexpr (NS > 1) {
+          // this stage's table: tw is the size-2^TL table at offset 2^TL of the pyramid
+          const float2* ts = tw - (1 << TL) - kStageTwiddles + stage_tw_offset(NS * R, R);
 #pragma unroll
           for (int r = 1; r < R; ++r) {
             // exp(SIGN 2 pi i r k / (NS R))
-            const float2 w = __ldg(&tw[(r * k) << (TL - LOG_NSR)]);
+            const float2 w = __ldg(&ts[r * NS + k]);
             a[r] = SIGN < 0 ? cmul(a[r], w) : cmulc(a[r], w);
           }
         }

@@ -61,6 +61,7 @@ struct fftk_plan_s {
   fftk_dtype dtype;
   int device;
   int twlog;                 // LT = 2^twlog = max(nx, ny, nz)
+  float2* d_tw_alloc = nullptr;  // per-stage twiddle tables (kStageTwiddles entries), then the pyramid
   float2* d_tw = nullptr;    // twiddle tables: at offset L (L = 1, 2, 4, ..., 4 LT), exp(-2 pi i m / L), m < L
   float2* d_tw3 = nullptr;   // the same for L = 3, 6, 12, ... up to the largest 3 * 2^m dimension
   __half* d_dft16 = nullptr; // split-FP16 DFT-16 operands (FFTK_R32_SPLIT16): forward, inverse
