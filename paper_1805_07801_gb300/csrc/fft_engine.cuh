@@ -161,6 +161,7 @@ __device__ __forceinline__ int swz(int pos) {
 // Exchange buffer for a column tile: element (pos, c) of a [L][T] tile.
 template <int T>
 struct ColX {
+  static constexpr bool kStageTables = false;  // a warp spans 32/T butterflies: gathers are near-broadcasts
   float2* s;
   int c;
   __device__ __forceinline__ void st(int pos, float2 v) const { s[swz<T>(pos) + c] = v; }
@@ -184,6 +185,7 @@ __device__ __forceinline__ int swz_line(int pos) {
 // live in one warp.
 template <bool WARP_SYNC>
 struct LineX {
+  static constexpr bool kStageTables = true;  // a warp spans 32 consecutive butterflies
   float2* s;
   __device__ __forceinline__ void st(int pos, float2 v) const { s[swz_line(pos)] = v; }
   __device__ __forceinline__ float2 ld(int pos) const { return s[swz_line(pos)]; }
@@ -201,14 +203,16 @@ struct LineX {
 // computed in FP64 on the host and rounded once to FP32).  A kernel gets the
 // table of size 2^TL >= L, which locates the array's base at compile time.
 //
-// The stages read per-stage tables.  A stage of span M = NS R (radix R after
-// NS points) multiplies input r of butterfly k by exp(-2 pi i r k / M).  In a
-// z line one warp holds 32 butterflies, and a gather from the size-L table
-// at index r k L / M spreads each load over up to 32 scattered entries; so
-// the plan also stores, for every M <= 4096 and R in {2, 4, 8, 16}, the table
-// exp(-2 pi i r k / M) r-major (entry r NS + k), where a warp's k are
-// consecutive.  These tables lie kStageTwiddles entries below the base of
-// the pyramid (the same FP64-built values, rounded the same way).
+// A stage of span M = NS R (radix R after NS points) multiplies input r of
+// butterfly k by exp(-2 pi i r k / M).  In a contiguous line (LineX) one warp
+// holds 32 consecutive butterflies, and a gather from the size-L table at
+// index r k L / M spreads each load over up to 32 scattered entries; so the
+// plan also stores, for every M <= 4096 and R in {2, 4, 8, 16}, the table
+// exp(-2 pi i r k / M) r-major (entry r NS + k), which those stages read.
+// These tables lie kStageTwiddles entries below the base of the pyramid (the
+// same FP64-built values, rounded the same way).  Column tiles (ColX) keep the
+// pyramid: their warps span 32/T butterflies, so the gathers are already
+// near-broadcasts.
 constexpr int kStageTwiddles = 32768;
 __host__ __device__ constexpr int stage_tw_offset(int M, int R) {
   return 4 * M + (R == 2 ? 0 : (R == 4 ? 1 : (R == 8 ? 2 : 3))) * M;
@@ -236,6 +240,7 @@ struct Stage {
       constexpr int B = G / R;   // butterflies per thread
       constexpr int S = L / G;   // threads per line
       constexpr bool LAST = (NS * R == L);
+      constexpr int LOG_NSR = Log2<NS * R>::value;
 #pragma unroll
       for (int t = 0; t < B; ++t) {
         const int b = j + t * S;   // butterfly index in [0, L/R)
@@ -244,12 +249,13 @@ struct Stage {
 #pragma unroll
         for (int r = 0; r < R; ++r) a[r] = v[t + r * B];
         if constexpr (NS > 1) {
-          // this stage's table: tw is the size-2^TL table at offset 2^TL of the pyramid
+          // exp(SIGN 2 pi i r k / (NS R)): from this stage's r-major table for
+          // contiguous lines, else from the size-2^TL table (tw, at offset 2^TL
+          // of the pyramid) at index r k 2^TL / (NS R)
           const float2* ts = tw - (1 << TL) - kStageTwiddles + stage_tw_offset(NS * R, R);
 #pragma unroll
           for (int r = 1; r < R; ++r) {
-            // exp(SIGN 2 pi i r k / (NS R))
-            const float2 w = __ldg(&ts[r * NS + k]);
+            const float2 w = X::kStageTables ? __ldg(&ts[r * NS + k]) : __ldg(&tw[(r * k) << (TL - LOG_NSR)]);
             a[r] = SIGN < 0 ? cmul(a[r], w) : cmulc(a[r], w);
           }
         }
