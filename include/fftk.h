@@ -70,8 +70,11 @@ const char *fftk_status_string(fftk_status s);
 const char *fftk_last_cuda_error(void);
 
 /* Create a plan for nx x ny x nz transforms (paper Sec. 3).  Builds the
- * twiddle table exp(-2 pi i m / LT), LT = max(nx, ny, nz), in FP64 on the host
- * and rounds it once to FP32.  Binds the plan to the current CUDA device.
+ * twiddle tables in FP64 on the host and rounds them once to FP32: exp(-2 pi
+ * i m / L) for every power of two L <= 4 max(nx, ny, nz), the same factors
+ * laid out per radix stage of the line transforms (256 KB), and for 3 * 2^m
+ * dimensions the tables of length 3 * 2^j.  Binds the plan to the current
+ * CUDA device.
  * Errors: INVALID_ARG (out NULL, bad dtype), UNSUPPORTED_SIZE, NO_DEVICE, OOM,
  * CUDA.  On error *out is set to NULL. */
 fftk_status fftk_plan_create(int nx, int ny, int nz, fftk_dtype dtype, fftk_plan *out);
