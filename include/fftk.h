@@ -413,9 +413,23 @@ fftk_status tarang_sgs_train(tarang_mlp m, float *params, float *adam_m, float *
  * context's inference expired since the last call (the flag is cleared). */
 fftk_status tarang_mlp_sync(tarang_mlp m, void *cuda_stream);
 /* Mean-squared-error loss (1/(6B)) sum (y - t)^2 (device double, may be NULL)
- * and its gradient grad[9094] (device). */
+ * and its gradient grad[9094] (device), on the CUDA cores (128 samples per
+ * block, per-block partials summed in a fixed order). */
 fftk_status tarang_mlp_loss_grad(tarang_mlp m, const float *params, const float *x, const float *t,
                                  int B, float *grad, double *loss, void *cuda_stream);
+/* Layer-input precision of the CUDA-core training kernels: BF16 (the
+ * network's definition, used by every other MLP call) or FP32, a test mode
+ * with the BF16 roundings left out, so that the kernels' own arithmetic can
+ * be held to FP32 accuracy against an FP64 reference. */
+typedef enum { TARANG_ACT_BF16 = 0, TARANG_ACT_FP32 = 1 } tarang_act_mode;
+/* tarang_mlp_loss_grad with the layer inputs in act_mode (FFTK_ERR_INVALID_ARG
+ * for any other value); TARANG_ACT_BF16 is tarang_mlp_loss_grad itself. */
+fftk_status tarang_mlp_loss_grad_mode(tarang_mlp m, const float *params, const float *x, const float *t,
+                                      int B, float *grad, double *loss, int act_mode, void *cuda_stream);
+/* The forward pass of tarang_mlp_loss_grad alone (CUDA cores, FP32 weights,
+ * FP32 products and sums, layer inputs in act_mode): y[B][6] (device). */
+fftk_status tarang_mlp_forward_mode(tarang_mlp m, const float *params, const float *x, float *y, int B,
+                                    int act_mode, void *cuda_stream);
 /* One Adam step (Kingma and Ba 2015; step counted from 1) on 9094 values. */
 fftk_status tarang_mlp_adam(float *params, float *m, float *v, const float *grad, int step,
                             float lr, float beta1, float beta2, float eps, void *cuda_stream);

@@ -120,6 +120,8 @@ def lib() -> ctypes.CDLL:
             "tarang_mlp_sync": ([vp, vp], i),
             "tarang_sgs_train": ([vp, vp, vp, vp, i, i, vp, vp, ll, i, c.c_float, c.c_ulonglong, vp, i, vp], i),
             "tarang_mlp_loss_grad": ([vp, vp, vp, vp, i, vp, vp, vp], i),
+            "tarang_mlp_loss_grad_mode": ([vp, vp, vp, vp, i, vp, vp, i, vp], i),
+            "tarang_mlp_forward_mode": ([vp, vp, vp, vp, i, i, vp], i),
             "tarang_mlp_adam": ([vp, vp, vp, vp, i, c.c_float, c.c_float, c.c_float, c.c_float, vp], i),
             "tarang_mlp_train_step": ([vp, vp, vp, vp, i, vp, vp, i, c.c_float, vp, vp], i),
             "fftk_launch_count": ([vp], ll),
@@ -360,6 +362,20 @@ def tarang_mlp_sync(m: int, stream=0) -> None:
 def tarang_mlp_loss_grad(m: int, params_ptr, x_ptr, t_ptr, B: int, grad_ptr, loss_ptr, stream=0) -> None:
     _check(lib().tarang_mlp_loss_grad(_vp(m), _vp(params_ptr), _vp(x_ptr), _vp(t_ptr), int(B), _vp(grad_ptr),
                                       _vp(loss_ptr), _vp(stream)), "tarang_mlp_loss_grad")
+
+
+TARANG_ACT_BF16, TARANG_ACT_FP32 = 0, 1
+
+
+def tarang_mlp_loss_grad_mode(m: int, params_ptr, x_ptr, t_ptr, B: int, grad_ptr, loss_ptr, act_mode: int,
+                              stream=0) -> None:
+    _check(lib().tarang_mlp_loss_grad_mode(_vp(m), _vp(params_ptr), _vp(x_ptr), _vp(t_ptr), int(B), _vp(grad_ptr),
+                                           _vp(loss_ptr), int(act_mode), _vp(stream)), "tarang_mlp_loss_grad_mode")
+
+
+def tarang_mlp_forward_mode(m: int, params_ptr, x_ptr, y_ptr, B: int, act_mode: int, stream=0) -> None:
+    _check(lib().tarang_mlp_forward_mode(_vp(m), _vp(params_ptr), _vp(x_ptr), _vp(y_ptr), int(B), int(act_mode),
+                                         _vp(stream)), "tarang_mlp_forward_mode")
 
 
 def tarang_mlp_adam(params_ptr, m_ptr, v_ptr, grad_ptr, step: int, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,

@@ -252,6 +252,12 @@ __device__ __constant__ int kWOff[4] = {0, 384, 4544, 8704};
 __device__ __constant__ int kBOff[4] = {320, 4480, 8640, 9088};
 
 __device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+// a layer input as the network defines it (BF16), or unrounded in the FP32
+// test mode that isolates the kernels' arithmetic from the BF16 rounding
+template <bool BF16>
+__device__ __forceinline__ float act_round(float x) {
+  return BF16 ? bf16r(x) : x;
+}
 
 struct MLPSmem {
   float w[kNP];
@@ -263,11 +269,13 @@ struct MLPSmem {
 };
 
 // forward of the chunk; y written for samples < nb; returns nothing
+template <bool BF16>
 __device__ void mlp_chunk_forward(MLPSmem& s, const float* __restrict__ x, int nb, int base, float* y6) {
   const int b = threadIdx.x;
   if (b < kChunk) {
 #pragma unroll
-    for (int i = 0; i < 5; ++i) s.act(0)[i * kAStride + b] = b < nb ? bf16r(x[(long long)(base + b) * 5 + i]) : 0.f;
+    for (int i = 0; i < 5; ++i)
+      s.act(0)[i * kAStride + b] = b < nb ? act_round<BF16>(x[(long long)(base + b) * 5 + i]) : 0.f;
   }
   __syncthreads();
   for (int l = 0; l < 4; ++l) {
@@ -278,7 +286,7 @@ __device__ void mlp_chunk_forward(MLPSmem& s, const float* __restrict__ x, int n
       float z = bias[o];
       for (int i = 0; i < din; ++i) z = fmaf(W[o * din + i], s.act(l)[i * kAStride + b], z);
       if (l < 3)
-        s.act(l + 1)[o * kAStride + b] = bf16r(tanhf(z));
+        s.act(l + 1)[o * kAStride + b] = act_round<BF16>(tanhf(z));
       else
         y6[o] = z;
     }
@@ -287,7 +295,9 @@ __device__ void mlp_chunk_forward(MLPSmem& s, const float* __restrict__ x, int n
 }
 
 // one CTA: forward + backward of 128 samples; writes its gradient partial and
-// its loss partial (sum of squared errors)
+// its loss partial (sum of squared errors).  BF16: layer inputs rounded to
+// bfloat16 (the network's definition); false in the FP32 test mode.
+template <bool BF16>
 __global__ void __launch_bounds__(kChunk) k_mlp_grad(const float* __restrict__ params, const float* __restrict__ x,
                                                      const float* __restrict__ t, int B, float* __restrict__ part,
                                                      double* __restrict__ loss_part) {
@@ -299,7 +309,7 @@ __global__ void __launch_bounds__(kChunk) k_mlp_grad(const float* __restrict__ p
   for (int i = b; i < kNP; i += kChunk) s.w[i] = params[i];
   __syncthreads();
   float y[6];
-  mlp_chunk_forward(s, x, nb, base, y);
+  mlp_chunk_forward<BF16>(s, x, nb, base, y);
   // output error: dL/dz4 = 2 (y - t) / (6 B)
   __shared__ double lsum[kChunk];
   double l2 = 0.0;
@@ -348,6 +358,26 @@ __global__ void __launch_bounds__(kChunk) k_mlp_grad(const float* __restrict__ p
     double acc = 0.0;
     for (int k = 0; k < kChunk; ++k) acc += lsum[k];
     loss_part[blockIdx.x] = acc;
+  }
+}
+
+// the forward pass alone on the CUDA cores (128 samples per CTA), the
+// arithmetic of k_mlp_grad's forward: y[B][6]
+template <bool BF16>
+__global__ void __launch_bounds__(kChunk) k_mlp_forward_cc(const float* __restrict__ params,
+                                                           const float* __restrict__ x, float* __restrict__ y, int B) {
+  extern __shared__ float smem_mlp[];
+  MLPSmem& s = *reinterpret_cast<MLPSmem*>(smem_mlp);
+  const int b = threadIdx.x;
+  const int base = blockIdx.x * kChunk;
+  const int nb = min(kChunk, B - base);
+  for (int i = b; i < kNP; i += kChunk) s.w[i] = params[i];
+  __syncthreads();
+  float y6[6];
+  mlp_chunk_forward<BF16>(s, x, nb, base, y6);
+  if (b < nb) {
+#pragma unroll
+    for (int o = 0; o < 6; ++o) y[(long long)(base + b) * 6 + o] = y6[o];
   }
 }
 
@@ -698,16 +728,24 @@ static int grid_for(long long work, int threads) {
 static size_t mlp_smem() { return sizeof(MLPSmem); }
 
 static cudaError_t mlp_attrs() {
-  static std::once_flag once;
-  static cudaError_t err = cudaSuccess;
-  std::call_once(once, [] {
-    err = cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mlp_smem());
+  static PerDevice once;
+  return once.run([](int) {
+    cudaError_t err = cudaFuncSetAttribute(k_mlp_grad<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)mlp_smem());
+    if (err == cudaSuccess)
+      err = cudaFuncSetAttribute(k_mlp_grad<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mlp_smem());
+    if (err == cudaSuccess)
+      err = cudaFuncSetAttribute(k_mlp_forward_cc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)mlp_smem());
+    if (err == cudaSuccess)
+      err = cudaFuncSetAttribute(k_mlp_forward_cc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)mlp_smem());
     if (err == cudaSuccess)
       err = cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, mlptc::kSmem);
     if (err == cudaSuccess)
       err = cudaFuncSetAttribute(k_sgs_pointwise_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, mlptc::kSmem);
+    return err;
   });
-  return err;
 }
 
 // persistent grid of the tensor-core inference kernels: two CTAs per SM
@@ -882,14 +920,36 @@ extern "C" fftk_status tarang_mlp_sync(tarang_mlp m, void* cuda_stream) {
   return FFTK_OK;
 }
 
-extern "C" fftk_status tarang_mlp_loss_grad(tarang_mlp m, const float* params, const float* x, const float* t,
-                                            int B, float* grad, double* loss, void* cuda_stream) {
+extern "C" fftk_status tarang_mlp_loss_grad_mode(tarang_mlp m, const float* params, const float* x, const float* t,
+                                                 int B, float* grad, double* loss, int act_mode, void* cuda_stream) {
   if (!m || !params || !x || !t || !grad || B < 1 || B > m->max_batch) return FFTK_ERR_INVALID_ARG;
+  if (act_mode != TARANG_ACT_BF16 && act_mode != TARANG_ACT_FP32) return FFTK_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   const int nblk = (B + kChunk - 1) / kChunk;
-  k_mlp_grad<<<nblk, kChunk, mlp_smem(), st>>>(params, x, t, B, m->part, m->loss_part);
+  if (act_mode == TARANG_ACT_BF16)
+    k_mlp_grad<true><<<nblk, kChunk, mlp_smem(), st>>>(params, x, t, B, m->part, m->loss_part);
+  else
+    k_mlp_grad<false><<<nblk, kChunk, mlp_smem(), st>>>(params, x, t, B, m->part, m->loss_part);
   k_mlp_reduce<<<(kNP + 255) / 256, 256, 0, st>>>(m->part, nblk, grad, m->loss_part, loss,
                                                  1.0 / (6.0 * (double)B));
+  return from_cuda(cudaGetLastError());
+}
+
+extern "C" fftk_status tarang_mlp_loss_grad(tarang_mlp m, const float* params, const float* x, const float* t,
+                                            int B, float* grad, double* loss, void* cuda_stream) {
+  return tarang_mlp_loss_grad_mode(m, params, x, t, B, grad, loss, TARANG_ACT_BF16, cuda_stream);
+}
+
+extern "C" fftk_status tarang_mlp_forward_mode(tarang_mlp m, const float* params, const float* x, float* y, int B,
+                                               int act_mode, void* cuda_stream) {
+  if (!m || !params || !x || !y || B < 1) return FFTK_ERR_INVALID_ARG;
+  if (act_mode != TARANG_ACT_BF16 && act_mode != TARANG_ACT_FP32) return FFTK_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  const int nblk = (B + kChunk - 1) / kChunk;
+  if (act_mode == TARANG_ACT_BF16)
+    k_mlp_forward_cc<true><<<nblk, kChunk, mlp_smem(), st>>>(params, x, y, B);
+  else
+    k_mlp_forward_cc<false><<<nblk, kChunk, mlp_smem(), st>>>(params, x, y, B);
   return from_cuda(cudaGetLastError());
 }
 

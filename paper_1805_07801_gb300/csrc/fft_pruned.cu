@@ -72,11 +72,10 @@ __global__ void __launch_bounds__(PCfg<N>::THREADS, PCfg<N>::MINB)
 template <int N, int SIGN, bool XPASS>
 static cudaError_t pcpass_n(fftk_plan p, const float2* in, float2* out, long long B, float scale, cudaStream_t st) {
   using C = PCfg<N>;
-  static std::once_flag once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(once, [] {
-    attr_err = cudaFuncSetAttribute(k_pcpass<N, SIGN, XPASS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)C::SMEM);
+  static PerDevice once;
+  const cudaError_t attr_err = once.run([](int) {
+    return cudaFuncSetAttribute(k_pcpass<N, SIGN, XPASS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)C::SMEM);
   });
   if (attr_err != cudaSuccess) return attr_err;
   constexpr int KD = (N - 1) / 3, KC = KD + 1;

@@ -210,10 +210,9 @@ template <int P, int SIGN>
 static cudaError_t cpass3_p(fftk_plan p, const float2* in, float2* out, long long B, long long Q, float scale,
                             int kind, cudaStream_t st) {
   using C = C3Cfg<P>;
-  static std::once_flag once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(once, [] {
-    attr_err = cudaFuncSetAttribute(k_cpass3<P, SIGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+  static PerDevice once;
+  const cudaError_t attr_err = once.run([](int) {
+    return cudaFuncSetAttribute(k_cpass3<P, SIGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
   });
   if (attr_err != cudaSuccess) return attr_err;
   const long long qtiles = (Q + C::T - 1) / C::T;

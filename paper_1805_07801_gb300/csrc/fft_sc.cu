@@ -299,11 +299,9 @@ template <int L, bool SINE, int DIR>
 static cudaError_t scpass_l(fftk_plan p, const float2* in, float2* out, long long P, long long Q, float scale,
                             int kind, cudaStream_t st) {
   using C = SCfg<L>;
-  static std::once_flag once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(once, [] {
-    attr_err = cudaFuncSetAttribute(k_scpass<L, SINE, DIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)C::SMEM);
+  static PerDevice once;
+  const cudaError_t attr_err = once.run([](int) {
+    return cudaFuncSetAttribute(k_scpass<L, SINE, DIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
   });
   if (attr_err != cudaSuccess) return attr_err;
   const long long qtiles = (Q + C::T - 1) / C::T;
@@ -328,11 +326,10 @@ template <int L, bool SINE, int DIR>
 static cudaError_t scpass_pr_l(fftk_plan p, const float2* in, float2* out, long long B, float scale,
                                cudaStream_t st) {
   using C = SCfg<L>;
-  static std::once_flag once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(once, [] {
-    attr_err = cudaFuncSetAttribute(k_scpass_pr<L, SINE, DIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)C::SMEM);
+  static PerDevice once;
+  const cudaError_t attr_err = once.run([](int) {
+    return cudaFuncSetAttribute(k_scpass_pr<L, SINE, DIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)C::SMEM);
   });
   if (attr_err != cudaSuccess) return attr_err;
   constexpr int KD = (L - 1) / 3, KC = KD + 1;

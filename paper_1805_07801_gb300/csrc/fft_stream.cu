@@ -83,8 +83,16 @@ __global__ void __launch_bounds__(PFCfg<L>::THREADS, PFCfg<L>::MINB)
   for (; t < ntiles; t += gridDim.x) {
     if (tid == 0) ok_flag = tcg::mbar_wait(bar, phase) ? 1 : 0;
     __syncthreads();
-    if (!ok_flag) {  // the tile never arrived: report and leave (no other copy is in flight)
-      if (tid == 0) atomicOr(err, 1);
+    if (!ok_flag) {
+      // The tile never arrived: its copy may still be pending, writing into
+      // this CTA's shared memory and completing on the mbarrier there.  Thread
+      // 0 reports, then waits once more (bounded) for that copy before the
+      // CTA's shared memory is released; the other threads may leave.  The
+      // error word is the only signal: the host treats it as fatal for the plan.
+      if (tid == 0) {
+        atomicOr(err, 1);
+        tcg::mbar_wait(bar, phase);
+      }
       return;
     }
     phase ^= 1;
@@ -149,22 +157,24 @@ template <int L, int SIGN>
 static cudaError_t cpass_tma_l(fftk_plan p, const CUtensorMap& m, float2* out, long long P, long long Q, float scale,
                                int kind, cudaStream_t st) {
   using C = PFCfg<L>;
-  static std::once_flag once;
-  static cudaError_t attr_err = cudaSuccess;
-  static int per_sm = 0, nsm = 0;
-  std::call_once(once, [] {
-    attr_err = cudaFuncSetAttribute(k_cpass_tma<L, SIGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
-    if (attr_err == cudaSuccess)
-      attr_err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cpass_tma<L, SIGN>, C::THREADS, C::SMEM);
-    int dev = 0;
-    if (attr_err == cudaSuccess) attr_err = cudaGetDevice(&dev);
-    if (attr_err == cudaSuccess) attr_err = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (attr_err == cudaSuccess && per_sm < 1) attr_err = cudaErrorInvalidConfiguration;
-  });
+  static PerDevice once;
+  static int per_sm[kMaxDevices], nsm[kMaxDevices];
+  int dev = 0;
+  const cudaError_t attr_err = once.run(
+      [](int d) {
+        cudaError_t e =
+            cudaFuncSetAttribute(k_cpass_tma<L, SIGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+        if (e == cudaSuccess)
+          e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[d], k_cpass_tma<L, SIGN>, C::THREADS, C::SMEM);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm[d], cudaDevAttrMultiProcessorCount, d);
+        if (e == cudaSuccess && per_sm[d] < 1) e = cudaErrorInvalidConfiguration;
+        return e;
+      },
+      &dev);
   if (attr_err != cudaSuccess) return attr_err;
   const long long qtiles = (Q + C::T - 1) / C::T;
   const long long ntiles = P * qtiles;
-  const long long cap = (long long)nsm * per_sm;
+  const long long cap = (long long)nsm[dev] * per_sm[dev];
   const unsigned grid = (unsigned)(ntiles < cap ? ntiles : cap);
   LaunchScope ls(p, kind, st);
   k_cpass_tma<L, SIGN><<<grid, C::THREADS, C::SMEM, st>>>(m, out, (int)Q, (int)qtiles, (int)ntiles, twiddles(p, L),

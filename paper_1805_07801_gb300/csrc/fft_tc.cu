@@ -214,19 +214,12 @@ __global__ void __launch_bounds__(TC2<L>::THREADS, TC2<L>::MINB)
     wL[i] = w;
   }
   if (t < T) colmax[t] = 0.f;
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(tc::su32(tslot)),
-                 "r"(C::COLS));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
-  }
-  if (t == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(tc::su32(mbar)), "r"(1));
-    asm volatile("fence.mbarrier_init.release.cluster;\n");
-  }
-  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-  asm volatile("tcgen05.fence::before_thread_sync;\n");
+  if (warp == 0) tcg::tmem_alloc(tslot, C::COLS);
+  if (t == 0) tcg::mbar_init(mbar);
+  tcg::fence_smem_async();
+  tcg::fence_before_sync();
   __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;\n");
+  tcg::fence_after_sync();
   const uint32_t tmem = *tslot;
   const uint32_t a_sa = tc::su32(As), b1_sa = tc::su32(Bs), b2_sa = b1_sa + tc::kBBytes;
   // this thread's TMEM row: lane 32 (warp % 4) + lane id of M block warp / 4 = stage row t
@@ -235,10 +228,10 @@ __global__ void __launch_bounds__(TC2<L>::THREADS, TC2<L>::MINB)
   bool failed = false;
 
   auto run_mma = [&]() -> bool {
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;\n");
+    tcg::fence_smem_async();
+    tcg::fence_before_sync();
     __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    tcg::fence_after_sync();
     if (t == 0) {
 #pragma unroll
       for (int blk = 0; blk < C::BLOCKS; ++blk) {
@@ -249,8 +242,7 @@ __global__ void __launch_bounds__(TC2<L>::THREADS, TC2<L>::MINB)
 #pragma unroll
         for (int s = 0; s < 4; ++s) tc::mma(d, tc::desc(a + 256 * s), tc::desc(b2_sa + 256 * s), 1);
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-          tc::su32(mbar)));
+      tcg::commit(mbar);
     }
     // thread 0 alone polls the mbarrier; the others wait at the barrier
     // without taking issue slots, and the tcgen05 fences around it order their
@@ -258,12 +250,12 @@ __global__ void __launch_bounds__(TC2<L>::THREADS, TC2<L>::MINB)
     bool ok = true;
     if (t == 0) {
       ok = tc::mbar_wait(mbar, phase);
-      asm volatile("tcgen05.fence::after_thread_sync;\n");
-      asm volatile("tcgen05.fence::before_thread_sync;\n");
+      tcg::fence_after_sync();
+      tcg::fence_before_sync();
     }
     phase ^= 1;
     const bool all = __syncthreads_and(ok) != 0;
-    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    tcg::fence_after_sync();
     return all;
   };
 
@@ -383,10 +375,9 @@ __global__ void __launch_bounds__(TC2<L>::THREADS, TC2<L>::MINB)
   }
   if (failed && t == 0) atomicOr(err, 1);
   if (failed && t == 0) tc::mbar_wait(mbar, phase ^ 1);  // let in-flight MMAs drain (bounded) before freeing TMEM
-  asm volatile("tcgen05.fence::before_thread_sync;\n");
+  tcg::fence_before_sync();
   __syncthreads();
-  if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(C::COLS));
+  if (warp == 0) tcg::tmem_dealloc(tmem, C::COLS);
 }
 
 // P: batch (PM = 0: P lines of Q columns; PM > 0: P spectra of L^3)
@@ -394,22 +385,28 @@ template <int L, int SIGN, int PM>
 static cudaError_t cpass_tc_l(fftk_plan p, const float2* in, float2* out, long long P, long long Q,
                               float scale, int kind, cudaStream_t st) {
   using C = TC2<L>;
-  static std::once_flag once;
-  static cudaError_t attr_err = cudaSuccess;
-  static int per_sm = 1;
-  std::call_once(once, [] {
-    attr_err = cudaFuncSetAttribute(k_cpass_tc<L, SIGN, PM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)C::SMEM);
-    if (attr_err == cudaSuccess &&
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cpass_tc<L, SIGN, PM>, C::THREADS, C::SMEM) !=
-            cudaSuccess)
-      per_sm = 1;
-    if (per_sm > 512 / C::COLS) per_sm = 512 / C::COLS;  // TMEM: 512 columns per SM
-    if (per_sm < 1) per_sm = 1;
-  });
+  static PerDevice once;
+  static int per_sm_dev[kMaxDevices];
+  int dev = 0;
+  const cudaError_t attr_err = once.run(
+      [](int d) {
+        const cudaError_t e = cudaFuncSetAttribute(k_cpass_tc<L, SIGN, PM>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+        int n = 1;
+        if (e == cudaSuccess &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_cpass_tc<L, SIGN, PM>, C::THREADS, C::SMEM) !=
+                cudaSuccess) {
+          cudaGetLastError();
+          n = 1;
+        }
+        if (n > 512 / C::COLS) n = 512 / C::COLS;  // TMEM: 512 columns per SM
+        per_sm_dev[d] = n < 1 ? 1 : n;
+        return e;
+      },
+      &dev);
   if (attr_err != cudaSuccess) return attr_err;
-  int dev = 0, sms = 1;
-  cudaGetDevice(&dev);
+  const int per_sm = per_sm_dev[dev];
+  int sms = 1;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   constexpr int KD = (L - 1) / 3;
   const int outer = PM == 1 ? 2 * KD + 1 : L;

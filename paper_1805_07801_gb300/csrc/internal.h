@@ -87,6 +87,32 @@ inline const float2* twiddles3(const fftk_plan_s* p, int L) { return p->d_tw3 + 
 // Tables beyond LT serve the quarter-wave factors of the sine/cosine passes.
 inline const float2* twiddles(const fftk_plan_s* p, int L) { return p->d_tw + L; }
 
+// One-time set-up for each device.  Kernel attributes (the dynamic
+// shared-memory limit) and occupancy figures belong to a function on the
+// device that is current when they are set or queried, so a process that
+// drives several devices repeats them on each.  run(f) calls f(dev) once per
+// device (the current one) and returns that status on every later call.
+constexpr int kMaxDevices = 64;
+struct PerDevice {
+  std::mutex mu;
+  bool done[kMaxDevices] = {};
+  cudaError_t err[kMaxDevices] = {};
+  template <class F>
+  cudaError_t run(F&& f, int* dev_out = nullptr) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    if (dev_out) *dev_out = dev;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!done[dev]) {
+      err[dev] = f(dev);
+      done[dev] = true;
+    }
+    return err[dev];
+  }
+};
+
 // Launch bracketing: counts the launch and records profiling events.
 struct LaunchScope {
   fftk_plan p;

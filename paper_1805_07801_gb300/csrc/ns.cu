@@ -571,12 +571,11 @@ static fftk_status ns_etab(fftk_plan p, double nu, double dt) {
 template <int N>
 struct NSLaunch {
   static cudaError_t attrs() {
-    static std::once_flag once;
-    static cudaError_t err = cudaSuccess;
-    std::call_once(once, [] {
+    static PerDevice once;
+    return once.run([](int) {
       const int sx = (int)NXCfg<N>::SMEM;
-      err = cudaFuncSetAttribute(k_ns_invx<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)NICfg<N>::SMEM);
+      cudaError_t err = cudaFuncSetAttribute(k_ns_invx<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)NICfg<N>::SMEM);
       if (err == cudaSuccess)
         err = cudaFuncSetAttribute(k_ns_ypass<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sx);
       if (err == cudaSuccess)
@@ -587,8 +586,8 @@ struct NSLaunch {
       if (err == cudaSuccess)
         err = cudaFuncSetAttribute(k_ns_z<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)NZCfg<N>::SMEM);
+      return err;
     });
-    return err;
   }
 
   // The fused z pass alone (c2r of the six fields in s->w, u x omega, r2c of

@@ -451,10 +451,9 @@ __global__ void __launch_bounds__(RZCfg<N>::THREADS, 3)
 template <int N>
 static cudaError_t rbc_z_n(fftk_plan p, float2* w, const RBCSlots& sl, cudaStream_t st) {
   using C = RZCfg<N>;
-  static std::once_flag once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(once, [] {
-    attr_err = cudaFuncSetAttribute(k_rbc_z<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+  static PerDevice once;
+  const cudaError_t attr_err = once.run([](int) {
+    return cudaFuncSetAttribute(k_rbc_z<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
   });
   if (attr_err != cudaSuccess) return attr_err;
   const long long lines = (long long)N * N;

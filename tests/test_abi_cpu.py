@@ -124,6 +124,14 @@ def test_null_plan_calls_of_the_later_entry_points(fk):
     assert "sc_fwd" in names and "sc_inv" in names
 
 
+def test_mlp_mode_entry_points_check_arguments_first(fk):
+    L = fk.lib()
+    bad = fk.FFTK_ERR_INVALID_ARG
+    assert L.tarang_mlp_loss_grad_mode(None, None, None, None, 1, None, None, fk.TARANG_ACT_FP32, None) == bad
+    assert L.tarang_mlp_forward_mode(None, None, None, None, 1, fk.TARANG_ACT_BF16, None) == bad
+    assert fk.TARANG_ACT_BF16 == 0 and fk.TARANG_ACT_FP32 == 1
+
+
 def _struct_fields(name):
     text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
     m = re.search(r"typedef struct \{([^{}]*)\}\s*" + name + r";", text)

@@ -158,6 +158,87 @@ def test_mlp_forward_gradient_adam_match_oracle(fk, oracle_mod):
     assert np.max(np.abs(pg - po)) < 1e-6
 
 
+# the parameter tensors of the 5-64-64-64-6 network in the 9094-value layout
+TENSORS = {"W1": (0, 320), "b1": (320, 384), "W2": (384, 4480), "b2": (4480, 4544),
+           "W3": (4544, 8640), "b3": (8640, 8704), "W4": (8704, 9088), "b4": (9088, 9094)}
+
+
+@pytest.mark.parametrize("mode", ["bf16", "fp32"])
+def test_mlp_gradient_of_every_tensor_matches_oracle(fk, oracle_mod, mode):
+    """Each parameter tensor's gradient, the loss and the forward output of the
+    CUDA-core training kernels against the FP64 oracle.  BF16 mode (the
+    network's definition): both sides round every layer input to BF16, so
+    they differ only where an FP32 and an FP64 pre-activation fall on opposite
+    sides of a BF16 rounding boundary (2^-8 relative for that activation):
+    1e-2 per tensor.  FP32 test mode (no roundings on either side): only FP32
+    arithmetic separates the two, 1e-5 per tensor."""
+    import torch
+
+    bf16 = mode == "bf16"
+    act = fk.TARANG_ACT_BF16 if bf16 else fk.TARANG_ACT_FP32
+    tol = 1e-2 if bf16 else 1e-5
+    B = 1000  # not a multiple of the 128-sample chunk
+    rng = np.random.default_rng(14)
+    p = _params(15)
+    x = rng.standard_normal((B, 5)).astype(np.float32)
+    t = rng.standard_normal((B, 6)).astype(np.float32) * 0.5
+    ctx = fk.tarang_mlp_create(B)
+    try:
+        pd, xd, td = _f32(p), _f32(x), _f32(t)
+        y = torch.empty((B, 6), dtype=torch.float32, device="cuda:0")
+        fk.tarang_mlp_forward_mode(ctx, pd.data_ptr(), xd.data_ptr(), y.data_ptr(), B, act, stream())
+        g = torch.empty(9094, dtype=torch.float32, device="cuda:0")
+        loss = torch.zeros(1, dtype=torch.float64, device="cuda:0")
+        fk.tarang_mlp_loss_grad_mode(ctx, pd.data_ptr(), xd.data_ptr(), td.data_ptr(), B, g.data_ptr(),
+                                     loss.data_ptr(), act, stream())
+        sync()
+        yg, gg, lg = y.cpu().numpy(), g.cpu().numpy(), float(loss.item())
+    finally:
+        fk.tarang_mlp_destroy(ctx)
+    p64, x64, t64 = p.astype(np.float64), x.astype(np.float64), t.astype(np.float64)
+    yo = oracle_mod.mlp_forward(p64, x64, bf16_acts=bf16)
+    lo, go = oracle_mod.mlp_loss_grad(p64, x64, t64, bf16_acts=bf16)
+    errs = {name: rel_l2(gg[a:b], go[a:b]) for name, (a, b) in TENSORS.items()}
+    print(f"\nMEASURED mlp {mode} forward {rel_l2(yg, yo):.2e} loss {abs(lg - lo) / lo:.2e} "
+          + " ".join(f"{k} {v:.2e}" for k, v in errs.items()))
+    assert rel_l2(yg, yo) < (1e-3 if bf16 else 1e-6)
+    assert abs(lg - lo) < (1e-3 if bf16 else 1e-6) * lo
+    for name, e in errs.items():
+        assert e < tol, (name, e)
+
+
+def test_mlp_fp32_mode_gradient_sees_a_planted_bias_error(fk, oracle_mod):
+    """The per-tensor check at 1e-5 resolves an error confined to b4: the
+    oracle's gradient with b4's six values perturbed by 1e-4 of their size
+    (everything else exact) must fail it, while a single norm over all 9094
+    values at the BF16 bound of 1e-3 would let it pass."""
+    import torch
+
+    B = 512
+    rng = np.random.default_rng(21)
+    p = _params(22)
+    x = rng.standard_normal((B, 5)).astype(np.float32)
+    t = rng.standard_normal((B, 6)).astype(np.float32) * 0.5
+    ctx = fk.tarang_mlp_create(B)
+    try:
+        pd, xd, td = _f32(p), _f32(x), _f32(t)
+        g = torch.empty(9094, dtype=torch.float32, device="cuda:0")
+        fk.tarang_mlp_loss_grad_mode(ctx, pd.data_ptr(), xd.data_ptr(), td.data_ptr(), B, g.data_ptr(), 0,
+                                     fk.TARANG_ACT_FP32, stream())
+        sync()
+        gg = g.cpu().numpy()
+    finally:
+        fk.tarang_mlp_destroy(ctx)
+    _, go = oracle_mod.mlp_loss_grad(p.astype(np.float64), x.astype(np.float64), t.astype(np.float64),
+                                     bf16_acts=False)
+    a, b = TENSORS["b4"]
+    planted = go.copy()
+    planted[a:b] *= 1.0 + 1e-4
+    assert rel_l2(gg[a:b], go[a:b]) < 1e-5
+    assert rel_l2(gg[a:b], planted[a:b]) > 1e-5
+    assert rel_l2(gg, planted) < 1e-3
+
+
 def test_mlp_training_reduces_loss(fk):
     import torch
 
