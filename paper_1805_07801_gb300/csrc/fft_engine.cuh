@@ -19,11 +19,33 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+// Complex sums and real scalings use the paired FP32 instructions of sm_100
+// and later (two correctly rounded operations per instruction: the results
+// are those of the scalar operations).  They cut the instruction count of
+// the issue-bound kernels (the fused Navier-Stokes passes); a translation
+// unit whose kernels are bound by their global accesses instead (the plain
+// strided passes, measured slower with them) defines FFTK_PAIRED_FP32 as 0
+// before including this header.  The engine lives in an inline namespace
+// named after the choice, so the two forms never meet at link time.
+#ifndef FFTK_PAIRED_FP32
+#define FFTK_PAIRED_FP32 1
+#endif
+
 namespace fftk {
+#if FFTK_PAIRED_FP32
+inline namespace paired_fp32 {
+#else
+inline namespace scalar_fp32 {
+#endif
 
 // ---------------------------------------------------------------- complex --
+#if FFTK_PAIRED_FP32
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+#else
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+#endif
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
@@ -31,7 +53,11 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
   return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
 }
+#if FFTK_PAIRED_FP32
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return __fmul2_rn(a, make_float2(s, s)); }
+#else
 __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+#endif
 __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 // a * (SIGN * i)
 template <int SIGN>
@@ -292,4 +318,5 @@ __device__ __forceinline__ void fft_line(float2 (&v)[G], int j, const X& xc, con
 // Elements per thread used by the passes for a line of length L.
 __host__ __device__ constexpr int elems_per_thread(int L) { return L < 16 ? L : 16; }
 
+}  // inline namespace
 }  // namespace fftk

@@ -5,6 +5,9 @@
 // (the transpose-free layout of Appendix A), so no reorder pass exists.
 #include <mutex>
 
+// these passes are bound by their 8-byte global accesses; scalar FP32 sums
+// measured faster here than the paired ones (see fft_engine.cuh)
+#define FFTK_PAIRED_FP32 0
 #include "fft_engine.cuh"
 #include "internal.h"
 

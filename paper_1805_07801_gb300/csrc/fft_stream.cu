@@ -44,10 +44,7 @@ __device__ __forceinline__ void tma_load3(void* dst, const CUtensorMap* map, int
       : "memory");
 }
 
-__device__ __forceinline__ void mbar_expect(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(tcg::su32(bar)), "r"(bytes)
-               : "memory");
-}
+using tcg::mbar_expect;
 
 // Array [P][L][Q] of complex values, transform along L (element stride Q);
 // tile t = (p, q-tile); in may equal out (tiles are disjoint column sets).

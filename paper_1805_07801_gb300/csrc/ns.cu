@@ -25,6 +25,7 @@
 #include "fft_engine.cuh"
 #include "internal.h"
 #include "ns_common.cuh"
+#include "tcgen05.cuh"
 
 namespace fftk {
 // ------------------------------------------------------------ x/y config ---
@@ -176,59 +177,138 @@ __global__ void __launch_bounds__(NICfg<N>::THREADS)
 }
 
 // ------------------------------------------------------------- z product ---
+// The z kernel holds a 256-point line (n = 512) as 16 values per thread on 16
+// threads, two lines per warp: each transform is two radix-16 stages with one
+// exchange through shared memory (8 values per thread would need three stages
+// and two exchanges, and the exchanges dominated the L1 traffic).  A thread
+// holds up to four such arrays (u x omega accumulators and a vorticity
+// component), 241 registers at n = 512: two CTAs of 128 threads per SM.
 template <int N>
 struct NZCfg {
   static constexpr int H = N / 2;
-  static constexpr int G = H < 8 ? H : 8;
+  static constexpr int G = H < 16 ? H : 16;
   static constexpr int S = H / G;
   static constexpr int LPC = S >= 128 ? 1 : 128 / S;
   static constexpr int THREADS = LPC * S;
   static constexpr bool WARP = S <= 32;
-  static constexpr size_t SMEM = sizeof(float2) * (size_t)LPC * H * 4;  // exchange + 3 parked fields
+  static constexpr int KC = (N - 1) / 3 + 1;      // kept k_z count (2/3 rule)
+  static constexpr int KCP = (KC + 2) & ~1;       // staged values per line and buffer (KC + alignment slack)
+  static constexpr size_t FIELDS = sizeof(float2) * (size_t)LPC * H * 4;  // exchange + 3 parked fields
+  static constexpr size_t STAGE = sizeof(float2) * (size_t)LPC * 2 * KCP;  // two staging buffers per line
+  static constexpr size_t SMEM = FIELDS + STAGE + sizeof(uint64_t) * 2 * LPC;  // + one mbarrier per buffer
+  static constexpr int MINB = G == 16 ? 2 : 4;    // CTAs per SM the registers must allow
 };
+
+// cos and sin of pi/16 and 3 pi/16
+#define FFTK_C32A 0.98078528040323044913f
+#define FFTK_S32A 0.19509032201612826785f
+#define FFTK_C32B 0.83146961230254523708f
+#define FFTK_S32B 0.55557023301960222474f
+
+// a * exp(-2 pi i q / 32) for a q (0 <= q < 32) known at compile time after
+// unrolling: the eighth-turn remainder by its (cos, sin) constants, then the
+// quarter and half turns exactly
+__device__ __forceinline__ float2 mul_root32(float2 a, int q) {
+  float2 r;
+  switch (q & 7) {
+    case 0: r = a; break;
+    case 1: r = rot<-1>(a, FFTK_C32A, FFTK_S32A); break;
+    case 2: r = rot<-1>(a, FFTK_C16, FFTK_S16); break;
+    case 3: r = rot<-1>(a, FFTK_C32B, FFTK_S32B); break;
+    case 4: r = rot<-1>(a, FFTK_C8, FFTK_C8); break;
+    case 5: r = rot<-1>(a, FFTK_S32B, FFTK_C32B); break;
+    case 6: r = rot<-1>(a, FFTK_S16, FFTK_C16); break;
+    default: r = rot<-1>(a, FFTK_S32A, FFTK_C32A); break;
+  }
+  if (q & 8) r = mul_si<-1>(r);
+  return (q & 16) ? make_float2(-r.x, -r.y) : r;
+}
 
 // 3. per (x, y) line: the six c2r transforms, the product n = u x omega and
 //    the three r2c transforms.  Reads k_z < kc of fields 0..5, writes k_z < kc
 //    of fields 0..2 (in place: a line is fully read before it is written).
 //    The three velocity components are parked in real space in shared memory;
 //    each vorticity component is then transformed and folded into the
-//    accumulators of n, so at most 3 fields are held in registers.
+//    accumulators of n, so at most 4 fields are held in registers.
+//    A line's kept coefficients of each input field arrive by one bulk
+//    asynchronous copy into one of two staging buffers, issued two fields
+//    ahead of their use, so the global loads' latency overlaps the transforms
+//    of the field before; the c2r reads X[k] and its mirror X[H - k] from there.
 template <int N>
-__global__ void __launch_bounds__(NZCfg<N>::THREADS, 3)
-    k_ns_z(float2* w, NSGeom g, const float2* __restrict__ tw) {
+__global__ void __launch_bounds__(NZCfg<N>::THREADS, NZCfg<N>::MINB)
+    k_ns_z(float2* w, NSGeom g, const float2* __restrict__ tw, int* err) {
   constexpr long long H1 = N / 2 + 1, MM = (long long)N * N * H1;  // geometry of the n^3 grid
-  constexpr int KD = (N - 1) / 3;                                  // largest kept |k| (2/3 rule)
   using C = NZCfg<N>;
   constexpr int H = C::H, G = C::G, S = C::S;
   constexpr int LOGN = Log2<N>::value;
-  constexpr int KC = KD + 1;  // kept k_z count
-  extern __shared__ float2 smz[];
+  constexpr int KC = C::KC;  // kept k_z count
+  extern __shared__ __align__(16) float2 smz[];
   const int li = threadIdx.x / S, j = threadIdx.x % S;
   const long long line = (long long)blockIdx.x * C::LPC + li;
   const bool valid = line < (long long)N * N;
   const LineX<C::WARP> xc{smz + li * H};
   float2* park = smz + C::LPC * H + li * 3 * H + j;  // [3][G][S] per line, this thread's column
+  float2* stage = smz + C::FIELDS / sizeof(float2) + li * 2 * C::KCP;  // this line's two buffers
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smz + (C::FIELDS + C::STAGE) / sizeof(float2)) + 2 * li;
+
+  // Field f's element k of this line sits at element f MM + line H1 + k.  MM
+  // is even and H1 odd, so the line starts 16-byte aligned for even lines and
+  // 8 bytes past a 16-byte boundary for odd ones: the copy starts `lead`
+  // elements early (the previous line's last value, k_z = n/2, which this
+  // kernel never writes) and ends at k_z <= kc, inside the line.
+  const int lead = (int)(line & 1);
+  const uint32_t bytes = (uint32_t)(sizeof(float2) * ((KC + lead + 1) & ~1));
+  auto issue = [&](int f) {  // one thread of the line; buffer f & 1 was last read two fields ago
+    uint64_t* b = bar + (f & 1);
+    tcg::fence_smem_async();
+    tcg::mbar_expect(b, bytes);
+    tcg::bulk_g2s(stage + (f & 1) * C::KCP, w + f * MM + line * H1 - lead, bytes, b);
+  };
+  bool ok = true;
+  auto arrive = [&](int f) {  // wait for field f's copy (bounded; an expired wait is reported)
+    if (!valid) return;
+    if (!tcg::mbar_wait(bar + (f & 1), (uint32_t)((f >> 1) & 1))) {
+      if (j == 0 && ok) atomicOr(err, 1);
+      ok = false;
+      tcg::mbar_wait(bar + (f & 1), (uint32_t)((f >> 1) & 1));  // once more for the copy still in flight
+    }
+  };
+  if (j == 0 && valid) {
+    tcg::mbar_init(bar);
+    tcg::mbar_init(bar + 1);
+    issue(0);
+    issue(1);
+  }
+  xc.sync();  // the barriers are initialised before anyone polls them
+  // exp(-2 pi i k / N) at k = j + m S is Wj exp(-2 pi i m / (2G)) (N = 2 G S):
+  // one table load per thread instead of one per value
+  const float2 Wj = __ldg(&tw[j]);
+  auto twk = [&](int m) { return mul_root32(Wj, m * (16 / G)); };
 
   // inverse z transform of field f (half-complex -> N real points, two per slot)
   auto c2r = [&](int f, float2 (&U)[G]) {
-    const float2* src = w + f * MM + line * H1;
+    const float2* src = stage + (f & 1) * C::KCP + lead;
+    arrive(f);
 #pragma unroll
     for (int m = 0; m < G; ++m) {
       const int k = j + m * S;
       float2 A = make_float2(0.f, 0.f), B = make_float2(0.f, 0.f);
-      if (valid && k < KC) A = src[k];
-      if (valid && H - k < KC) B = src[H - k];
+      if (k < KC) A = src[k];
+      if (H - k < KC) B = src[H - k];
       if (k == 0) {
         A.y = 0.f;
         B.y = 0.f;
       }
       const float2 Bc = cconj(B);
       const float2 E = cadd(A, Bc);
-      const float2 W = __ldg(&tw[k]);
-      const float2 O = cmulc(csub(A, Bc), W);
+      const float2 O = cmulc(csub(A, Bc), twk(m));
       U[m] = make_float2(E.x - O.y, E.y + O.x);
     }
+    if constexpr (S == 1) xc.sync();  // (one thread per line: the transform has no exchange)
     fft_line<H, G, +1, LOGN>(U, j, xc, tw);
+    // every thread of the line has passed an exchange barrier since it read
+    // the buffer: refill it with field f + 2
+    if (f + 2 < 6 && j == 0 && valid) issue(f + 2);
   };
 
   {
@@ -255,14 +335,15 @@ __global__ void __launch_bounds__(NZCfg<N>::THREADS, 3)
       const float2 E = cscale(cadd(A, Bc), 0.5f);
       const float2 D = csub(A, Bc);
       const float2 O = make_float2(0.5f * D.y, -0.5f * D.x);
-      const float2 W = __ldg(&tw[k]);
-      if (valid && k < KC) dst[k] = cadd(E, cmul(W, O));
+      if (valid && k < KC) dst[k] = cadd(E, cmul(twk(m), O));
     }
     xc.sync();
   };
-  // n = u x omega at the two real points held by each slot:
+  // n = u x omega at the two real points held by each slot (elementwise
+  // products of the (even, odd) point pairs, paired FP32 instructions):
   //   n_x = u_y w_z - u_z w_y,  n_y = u_z w_x - u_x w_z,  n_z = u_x w_y - u_y w_x
   // n_z is complete after omega_y and is transformed before omega_z is loaded.
+  auto neg = [](float2 a) { return make_float2(-a.x, -a.y); };
   float2 Ny[G], Nx[G];
   {
     float2 Nz[G];
@@ -272,15 +353,15 @@ __global__ void __launch_bounds__(NZCfg<N>::THREADS, 3)
 #pragma unroll
       for (int m = 0; m < G; ++m) {
         const float2 uy = park[(1 * G + m) * S], uz = park[(2 * G + m) * S];
-        Ny[m] = make_float2(uz.x * W[m].x, uz.y * W[m].y);
-        Nz[m] = make_float2(-uy.x * W[m].x, -uy.y * W[m].y);
+        Ny[m] = __fmul2_rn(uz, W[m]);
+        Nz[m] = __fmul2_rn(neg(uy), W[m]);
       }
       c2r(4, W);  // omega_y
 #pragma unroll
       for (int m = 0; m < G; ++m) {
         const float2 ux = park[(0 * G + m) * S], uz = park[(2 * G + m) * S];
-        Nx[m] = make_float2(-uz.x * W[m].x, -uz.y * W[m].y);
-        Nz[m] = make_float2(fmaf(ux.x, W[m].x, Nz[m].x), fmaf(ux.y, W[m].y, Nz[m].y));
+        Nx[m] = __fmul2_rn(neg(uz), W[m]);
+        Nz[m] = __ffma2_rn(ux, W[m], Nz[m]);
       }
     }
     r2c(2, Nz);
@@ -291,8 +372,8 @@ __global__ void __launch_bounds__(NZCfg<N>::THREADS, 3)
 #pragma unroll
     for (int m = 0; m < G; ++m) {
       const float2 ux = park[(0 * G + m) * S], uy = park[(1 * G + m) * S];
-      Nx[m] = make_float2(fmaf(uy.x, W[m].x, Nx[m].x), fmaf(uy.y, W[m].y, Nx[m].y));
-      Ny[m] = make_float2(fmaf(-ux.x, W[m].x, Ny[m].x), fmaf(-ux.y, W[m].y, Ny[m].y));
+      Nx[m] = __ffma2_rn(uy, W[m], Nx[m]);
+      Ny[m] = __ffma2_rn(neg(ux), W[m], Ny[m]);
     }
   }
   r2c(0, Nx);
@@ -599,7 +680,8 @@ struct NSLaunch {
     NSWork* s = p->ns;
     LaunchScope ls(p, KK_NS_Z, st);
     const long long lines = (long long)N * N;
-    k_ns_z<N><<<(unsigned)((lines + Z::LPC - 1) / Z::LPC), Z::THREADS, Z::SMEM, st>>>(s->w, s->g, twiddles(p, N));
+    k_ns_z<N><<<(unsigned)((lines + Z::LPC - 1) / Z::LPC), Z::THREADS, Z::SMEM, st>>>(s->w, s->g, twiddles(p, N),
+                                                                                    p->d_err);
     return cudaGetLastError();
   }
 
@@ -631,8 +713,8 @@ struct NSLaunch {
     {
       LaunchScope ls(p, KK_NS_Z, st);
       const long long lines = (long long)N * N;
-      k_ns_z<N><<<(unsigned)((lines + Z::LPC - 1) / Z::LPC), Z::THREADS, Z::SMEM, st>>>(s->w, g,
-                                                                                       twiddles(p, N));
+      k_ns_z<N><<<(unsigned)((lines + Z::LPC - 1) / Z::LPC), Z::THREADS, Z::SMEM, st>>>(s->w, g, twiddles(p, N),
+                                                                                       p->d_err);
     }
     {
       LaunchScope ls(p, KK_NS_FWDY, st);

@@ -38,7 +38,10 @@ def test_stage_tables_fit_and_do_not_overlap(tmp_path):
     src = tmp_path / "probe.cu"
     src.write_text(PROBE)
     exe = tmp_path / "probe"
-    subprocess.run([nvcc, "-std=c++17", "-I", CSRC, str(src), "-o", str(exe)], check=True, capture_output=True)
+    # built for the library's target, whose engine uses sm_100+ paired FP32
+    # instructions; the probe itself runs on the host only
+    subprocess.run([nvcc, "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a", "-I", CSRC, str(src), "-o",
+                    str(exe)], check=True, capture_output=True)
     out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
     total = int(out[0])
     spans = []
