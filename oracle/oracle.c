@@ -96,6 +96,9 @@ int oracle_dft1d(const cplx *in, cplx *out, long n, int sign) {
  * n = 3 * 2^m (the paper's 768, 1536, 3072 grids) by the DFT's definition,
  * O(n^2), with the phase j k reduced mod n. */
 static int ok_len(long n) { return is_pow2(n) || (n % 3 == 0 && is_pow2(n / 3)); }
+/* Cubic grids of the solver: an even length the 1D transforms take (2^m, or
+ * 3 * 2^m as in the paper's 768^3 - 3072^3 runs of Sec. 6-7). */
+static int ok_grid(long n) { return n >= 2 && n % 2 == 0 && ok_len(n); }
 
 static cplx *make_line_table(long n, int sign) {
   if (is_pow2(n)) return make_twiddles(n, sign);
@@ -560,7 +563,7 @@ static double forced_energy(const cplx *u, int n, const oracle_ns_params *p) {
 }
 
 int oracle_ns_rhs(const cplx *uhat, cplx *nhat, int n, const oracle_ns_params *p) {
-  if (!is_pow2(n) || n < 2) return -1;
+  if (!ok_grid(n)) return -1;
   const long N = n, HZ = n / 2 + 1, M = N * N * HZ, R = N * N * N;
   cplx *what = (cplx *)malloc(sizeof(cplx) * 3 * (size_t)M);
   double *ur = (double *)malloc(sizeof(double) * 3 * (size_t)R);
@@ -620,7 +623,7 @@ int oracle_ns_rhs(const cplx *uhat, cplx *nhat, int n, const oracle_ns_params *p
 }
 
 int oracle_ns_rhs_divergence(const cplx *uhat, cplx *nhat, int n) {
-  if (!is_pow2(n) || n < 2) return -1;
+  if (!ok_grid(n)) return -1;
   const long N = n, HZ = n / 2 + 1, M = N * N * HZ, R = N * N * N;
   double *ur = (double *)malloc(sizeof(double) * 3 * (size_t)R);
   double *pr = (double *)malloc(sizeof(double) * (size_t)R);
@@ -655,7 +658,7 @@ int oracle_ns_rhs_divergence(const cplx *uhat, cplx *nhat, int n) {
 /* RK2 (Heun) with integrating factor E = exp(-nu |k|^2 dt):
  *   u1 = E (u + dt N(u)),   u_new = 1/2 E u + 1/2 (u1 + dt N(u1)). */
 int oracle_ns_step(cplx *uhat, int n, const oracle_ns_params *p, int nsteps) {
-  if (!is_pow2(n) || n < 2 || !p) return -1;
+  if (!ok_grid(n) || !p) return -1;
   const long N = n, HZ = n / 2 + 1, M = N * N * HZ;
   cplx *u1 = (cplx *)malloc(sizeof(cplx) * 3 * (size_t)M);
   cplx *nh = (cplx *)malloc(sizeof(cplx) * 3 * (size_t)M);
@@ -697,7 +700,7 @@ int oracle_ns_step(cplx *uhat, int n, const oracle_ns_params *p, int nsteps) {
  *   N4 = N(uc),
  *   u <- E u + dt/6 (E N1 + 2 H N2 + 2 H N3 + N4). */
 int oracle_ns_step_rk4(cplx *uhat, int n, const oracle_ns_params *p, int nsteps) {
-  if (!is_pow2(n) || n < 2 || !p) return -1;
+  if (!ok_grid(n) || !p) return -1;
   const long N = n, HZ = n / 2 + 1, M = N * N * HZ;
   cplx *us = (cplx *)malloc(sizeof(cplx) * 3 * (size_t)M);
   cplx *nh = (cplx *)malloc(sizeof(cplx) * 3 * (size_t)M);
@@ -1220,7 +1223,7 @@ static int ic_from_real(const double *ur, cplx *uhat, int n) {
 }
 
 int oracle_ic_taylor_green(cplx *uhat, int n) {
-  if (!is_pow2(n) || n < 2) return -1;
+  if (!ok_grid(n)) return -1;
   const long N = n, R = N * N * N;
   double *ur = (double *)calloc(3 * (size_t)R, sizeof(double));
   if (!ur) return -2;
@@ -1238,7 +1241,7 @@ int oracle_ic_taylor_green(cplx *uhat, int n) {
 }
 
 int oracle_ic_abc(cplx *uhat, int n) {
-  if (!is_pow2(n) || n < 2) return -1;
+  if (!ok_grid(n)) return -1;
   const long N = n, R = N * N * N;
   double *ur = (double *)malloc(3 * sizeof(double) * (size_t)R);
   if (!ur) return -2;
@@ -1281,7 +1284,7 @@ static void hermitianize(cplx *f, int n) {
 }
 
 int oracle_ic_random(const double *normals, cplx *uhat, int n, double k0, double E0) {
-  if (!is_pow2(n) || n < 2 || k0 <= 0.0 || E0 <= 0.0) return -1;
+  if (!ok_grid(n) || k0 <= 0.0 || E0 <= 0.0) return -1;
   const long N = n, HZ = n / 2 + 1, M = N * N * HZ;
   int rc = ic_from_real(normals, uhat, n);
   if (rc) return rc;

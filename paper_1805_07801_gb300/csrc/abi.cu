@@ -260,6 +260,26 @@ static cudaError_t strided_pass(fftk_plan p, int L, int sign, const float2* in, 
   return launch_cpass(p, L, sign, in, out, P, Q, scale, kind, st);
 }
 
+namespace fftk {
+cudaError_t r2c_scaled(fftk_plan p, const float* in, float2* out, long long B, float scale, cudaStream_t st) {
+  const bool do_y = p->ny > 1, do_x = p->nx > 1;
+  cudaError_t e = launch_z_r2c(p, in, out, B * p->nx * p->ny, (do_x || do_y) ? 1.f : scale, st);
+  if (e == cudaSuccess && do_y)
+    e = strided_pass(p, p->ny, -1, out, out, B * p->nx, p->hz, do_x ? 1.f : scale, KK_Y_FWD, st);
+  if (e == cudaSuccess && do_x)
+    e = strided_pass(p, p->nx, -1, out, out, B, (long long)p->ny * p->hz, scale, KK_X_FWD, st);
+  return e;
+}
+
+cudaError_t c2r_overwrite(fftk_plan p, float2* spec, float* out, long long B, cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  if (p->nx > 1) e = strided_pass(p, p->nx, +1, spec, spec, B, (long long)p->ny * p->hz, 1.f, KK_X_INV, st);
+  if (e == cudaSuccess && p->ny > 1) e = strided_pass(p, p->ny, +1, spec, spec, B * p->nx, p->hz, 1.f, KK_Y_INV, st);
+  if (e == cudaSuccess) e = launch_z_c2r(p, spec, out, B * p->nx * p->ny, st);
+  return e;
+}
+}  // namespace fftk
+
 extern "C" fftk_status fftk_r2c(fftk_plan p, const float* in, void* out, int batch,
                                 void* cuda_stream) {
   if (!p || !in || !out || batch < 1) return FFTK_ERR_INVALID_ARG;

@@ -36,15 +36,8 @@ struct PFCfg {
   static constexpr size_t SMEM = PBYTES + 16;                 // + the tile mbarrier
 };
 
-__device__ __forceinline__ void tma_load3(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-      "[%5];\n" ::"r"(tcg::su32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(tcg::su32(bar))
-      : "memory");
-}
-
 using tcg::mbar_expect;
+using tcg::tma_load3;
 
 // Array [P][L][Q] of complex values, transform along L (element stride Q);
 // tile t = (p, q-tile); in may equal out (tiles are disjoint column sets).
@@ -127,6 +120,29 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
       cudaGetLastError();
   });
   return fn;
+}
+
+bool encode_f32_map(CUtensorMap* m, const void* base, int rank, const uint64_t* dims, const uint64_t* strides,
+                    const uint32_t* box) {
+  if (rank < 1 || rank > 5 || reinterpret_cast<uintptr_t>(base) % 16 != 0) return false;
+  for (int i = 0; i + 1 < rank; ++i)
+    if (strides[i] % 16 != 0 || strides[i] >= (1ULL << 40)) return false;
+  if ((box[0] * 4u) % 16 != 0) return false;
+  auto enc = tensor_map_encoder();
+  if (!enc) return false;
+  std::memset(m, 0, sizeof(*m));
+  cuuint64_t d[5], s[4];
+  cuuint32_t b[5], e[5];
+  for (int i = 0; i < rank; ++i) {
+    d[i] = (cuuint64_t)dims[i];
+    b[i] = (cuuint32_t)box[i];
+    e[i] = 1;
+    if (i + 1 < rank) s[i] = (cuuint64_t)strides[i];
+  }
+  const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank, const_cast<void*>(base), d, s, b, e,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
 }
 
 // The 3D map [P][L][2Q] floats with boxes of 2T floats x 256 rows x 1; false

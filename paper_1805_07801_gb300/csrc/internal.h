@@ -1,6 +1,7 @@
 // Internal declarations shared by the library's translation units.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
@@ -171,6 +172,18 @@ cudaError_t launch_cpass_tc_pruned(fftk_plan p, int axis, int sign, const float2
 cudaError_t launch_cpass_tc(fftk_plan p, int L, int sign, const float2* in, float2* out, long long P,
                             long long Q, float scale, int kind, cudaStream_t st);
 cudaError_t upload_dft16_operands(fftk_plan p);
+// The plan's forward transform of B real fields without argument checks
+// (scale applied in the last pass), and its inverse of B spectra whose x and y
+// passes run in place (the spectra are overwritten) before the z pass into out.
+cudaError_t r2c_scaled(fftk_plan p, const float* in, float2* out, long long B, float scale, cudaStream_t st);
+cudaError_t c2r_overwrite(fftk_plan p, float2* spec, float* out, long long B, cudaStream_t st);
+// A tiled FP32 tensor map for TMA loads: dims[0] innermost (in floats),
+// strides[i] the byte stride of dimension i + 1 (a multiple of 16), box the
+// box extents (box[0] * 4 bytes a multiple of 16); out-of-range elements of a
+// box read as zero.  False (nothing encoded) where the driver entry point is
+// missing or a rule is broken.
+bool encode_f32_map(CUtensorMap* m, const void* base, int rank, const uint64_t* dims, const uint64_t* strides,
+                    const uint32_t* box);
 }  // namespace fftk
 
 struct fftk_sgs_work;

@@ -97,6 +97,7 @@ struct NICfg {
   static constexpr int S = N / G;
   static constexpr int T = N == 512 ? 16 : (N == 1024 ? 8 : NFCfg<N>::T);
   static constexpr int THREADS = T * S;
+  static constexpr int MINB = THREADS <= 256 ? 2 : 1;
   static constexpr size_t SMEM = sizeof(float2) * (size_t)N * T;
 };
 
@@ -118,7 +119,7 @@ struct NUCfg {
 //    omega_z = D_y - i k_y U_x   (five transforms instead of six).
 //    Output field order: u_x, u_y, u_z, omega_x, omega_y, omega_z.
 template <int N>
-__global__ void __launch_bounds__(NICfg<N>::THREADS)
+__global__ void __launch_bounds__(NICfg<N>::THREADS, NICfg<N>::MINB)
     k_ns_invx(const float2* __restrict__ u, float2* __restrict__ w, NSGeom g, int ktiles,
               const float2* __restrict__ tw) {
   constexpr long long H1 = N / 2 + 1, MM = (long long)N * N * H1;  // geometry of the n^3 grid
@@ -811,6 +812,62 @@ static cudaError_t ns_rhs_split(fftk_plan p, const float2* u, const float2* u0, 
   return cudaGetLastError();
 }
 
+// ------------------------------------------- right-hand side on 3 * 2^m -----
+// Grids of 3 * 2^m points (the paper's XC40 runs use 768^3, 1536^3 and 3072^3)
+// have no fused passes: the right-hand side runs through the plan's
+// transforms, whose 1D passes take one radix-3 step over power-of-two
+// sub-lines, with u x omega formed pointwise in real space:
+//   (u, omega = i k x u) on the kept modes -> c2r of the six fields ->
+//   n = u x omega -> r2c of n -> the per-mode update of the fused path
+//   (2/3 rule, projection, forcing, integrating-factor stage).
+
+// r: six real fields u_x, u_y, u_z, omega_x, omega_y, omega_z (R points each);
+// n = u x omega overwrites fields 0..2 (each point is read before it is written)
+__global__ void k_cross(float* __restrict__ r, long long R) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < R; i += (long long)gridDim.x * blockDim.x) {
+    const float ux = r[i], uy = r[i + R], uz = r[i + 2 * R];
+    const float wx = r[i + 3 * R], wy = r[i + 4 * R], wz = r[i + 5 * R];
+    r[i] = fmaf(uy, wz, -uz * wy);
+    r[i + R] = fmaf(uz, wx, -ux * wz);
+    r[i + 2 * R] = fmaf(ux, wy, -uy * wx);
+  }
+}
+
+static cudaError_t ns_rhs_unfused(fftk_plan p, const float2* u, const float2* u0, const float2* u1, float2* out,
+                                  const NSUpdate& upd, int mode, const float2* extra, cudaStream_t st) {
+  NSWork* s = p->ns;
+  const NSGeom g = s->g;
+  const long long R = (long long)g.n * g.n * g.n;
+  if (!s->r6) {
+    cudaError_t ea = cudaMalloc(&s->r6, sizeof(float) * 6 * (size_t)R);
+    if (ea != cudaSuccess) {
+      cudaGetLastError();
+      s->r6 = nullptr;
+      return ea;
+    }
+  }
+  const unsigned grid = 152 * 8;
+  cudaError_t e = cudaMemsetAsync(s->w, 0, sizeof(float2) * 6 * (size_t)g.M, st);
+  if (e != cudaSuccess) return e;
+  {
+    LaunchScope ls(p, KK_AUX, st);
+    k_curl_full<<<grid, 256, 0, st>>>(u, s->w, g);
+  }
+  e = c2r_overwrite(p, s->w, s->r6, 6, st);
+  if (e != cudaSuccess) return e;
+  {
+    LaunchScope ls(p, KK_AUX, st);
+    k_cross<<<grid, 256, 0, st>>>(s->r6, R);
+  }
+  e = r2c_scaled(p, s->r6, s->w, 3, (float)(1.0 / ((double)g.n * g.n * g.n)), st);
+  if (e != cudaSuccess) return e;
+  {
+    LaunchScope ls(p, KK_AUX, st);
+    k_update_full<<<grid, 256, 0, st>>>(s->w, u0, u1, out, g, upd, mode, extra);
+  }
+  return cudaGetLastError();
+}
+
 #define NS_SIZES(X) X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024)
 
 static cudaError_t ns_z_dispatch(fftk_plan p, cudaStream_t st) {
@@ -827,6 +884,7 @@ static cudaError_t ns_z_dispatch(fftk_plan p, cudaStream_t st) {
 static cudaError_t ns_rhs_dispatch(fftk_plan p, const float2* u, const float2* u0, const float2* u1,
                                    float2* out, const NSUpdate& upd, int mode, const float2* extra,
                                    cudaStream_t st) {
+  if (!is_pow2(p->nx)) return ns_rhs_unfused(p, u, u0, u1, out, upd, mode, extra, st);
   if (p->dtype == FFTK_R32_SPLIT16) return ns_rhs_split(p, u, u0, u1, out, upd, mode, extra, st);
   switch (p->nx) {
 #define CASE(n) \
@@ -851,10 +909,11 @@ static cudaError_t forced_energy(fftk_plan p, const float2* u, const tarang_para
 fftk_status ns_check(fftk_plan p, const tarang_params* prm, bool need_dt) {
   if (!p || !prm) return FFTK_ERR_INVALID_ARG;
   if (p->nx != p->ny || p->nx != p->nz) return FFTK_ERR_UNSUPPORTED_SIZE;
-  if (p->nx < 8 || p->nx > 1024 || !is_pow2(p->nx)) return FFTK_ERR_UNSUPPORTED_SIZE;
+  if (!ns_size_ok(p->nx)) return FFTK_ERR_UNSUPPORTED_SIZE;
   if (!(prm->nu >= 0.0) || !std::isfinite(prm->nu)) return FFTK_ERR_INVALID_ARG;
   if (need_dt && (!(prm->dt > 0.0) || !std::isfinite(prm->dt))) return FFTK_ERR_INVALID_ARG;
   if (prm->sgs_model && !prm->sgs_model->params) return FFTK_ERR_INVALID_ARG;
+  if (prm->sgs_model && !is_pow2(p->nx)) return FFTK_ERR_UNSUPPORTED_SIZE;  // the learned closure: 2^m grids
   if (prm->scheme != TARANG_RK2 && prm->scheme != TARANG_RK4) return FFTK_ERR_INVALID_ARG;
   if (prm->force_eps != 0.0) {
     const int kd = (p->nx - 1) / 3;
@@ -1045,8 +1104,7 @@ extern "C" fftk_status tarang_ic_random(fftk_plan p, const float* normals, void*
   if (!p || !normals || !uhat || !(k0 > 0.0) || !(E0 > 0.0) || !std::isfinite(k0) ||
       !std::isfinite(E0))
     return FFTK_ERR_INVALID_ARG;
-  if (p->nx != p->ny || p->nx != p->nz || p->nx < 8 || p->nx > 1024 || !is_pow2(p->nx))
-    return FFTK_ERR_UNSUPPORTED_SIZE;
+  if (p->nx != p->ny || p->nx != p->nz || !ns_size_ok(p->nx)) return FFTK_ERR_UNSUPPORTED_SIZE;
   fftk_status s = ns_ensure(p);
   if (s != FFTK_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
@@ -1101,8 +1159,7 @@ extern "C" fftk_status tarang_ic_random(fftk_plan p, const float* normals, void*
 // a coarse grid, into a valid solver state.
 extern "C" fftk_status tarang_dealias_project(fftk_plan p, void* uhat, void* cuda_stream) {
   if (!p || !uhat || misaligned16(uhat)) return FFTK_ERR_INVALID_ARG;
-  if (p->nx != p->ny || p->nx != p->nz || p->nx < 8 || p->nx > 1024 || !is_pow2(p->nx))
-    return FFTK_ERR_UNSUPPORTED_SIZE;
+  if (p->nx != p->ny || p->nx != p->nz || !ns_size_ok(p->nx)) return FFTK_ERR_UNSUPPORTED_SIZE;
   fftk_status s = ns_ensure(p);
   if (s != FFTK_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);

@@ -70,6 +70,13 @@ struct NSWork {
 };
 
 int ns_kmax(int n);
+// Cubes the solver accepts: n a power of two in [8, 1024] (the fused passes),
+// or n = 3 * 2^m in [12, 768] (the paper's 768^3 runs; the right-hand side
+// runs through the plan's transforms with the radix-3 step, unfused).
+inline bool ns_size_ok(int n) {
+  if (n >= 8 && n <= 1024 && (n & (n - 1)) == 0) return true;
+  return n >= 12 && n <= 768 && n % 3 == 0 && ((n / 3) & (n / 3 - 1)) == 0;
+}
 NSGeom make_geom(int n);
 fftk_status ns_ensure(fftk_plan p);
 fftk_status ns_check(fftk_plan p, const tarang_params* prm, bool need_dt);

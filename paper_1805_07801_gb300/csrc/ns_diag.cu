@@ -285,8 +285,7 @@ extern "C" int tarang_diag_kmax(fftk_plan p) { return p ? ns_kmax(p->nx) : -1; }
 extern "C" fftk_status tarang_diag(fftk_plan p, const void* uhat, double nu, double* diag_host,
                                    void* cuda_stream) {
   if (!p || !uhat || !diag_host || misaligned16(uhat)) return FFTK_ERR_INVALID_ARG;
-  if (p->nx != p->ny || p->nx != p->nz || p->nx < 8 || p->nx > 1024 || !is_pow2(p->nx))
-    return FFTK_ERR_UNSUPPORTED_SIZE;
+  if (p->nx != p->ny || p->nx != p->nz || !ns_size_ok(p->nx)) return FFTK_ERR_UNSUPPORTED_SIZE;
   fftk_status s = ns_ensure(p);
   if (s != FFTK_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);

@@ -71,6 +71,17 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       : "memory");
 }
 
+// TMA tiled load of the box at coordinates (x, y, z) of a 3D tensor map into
+// shared memory, completing on `bar` (complete_tx); x (the innermost
+// coordinate) times the element size must be a multiple of 16 bytes
+__device__ __forceinline__ void tma_load3(void* dst, const void* map, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];\n" ::"r"(su32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(su32(bar))
+      : "memory");
+}
+
 // wait for the phase of parity `phase`; false after kSpinLimit polls
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
   uint32_t done = 0;

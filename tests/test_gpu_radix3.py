@@ -112,16 +112,27 @@ def test_full_size_768_sampled_coefficients(fk, oracle_mod):
         assert abs(got - want) < 1e-4 * scale, (a, b, c, got, want)
 
 
-def test_solver_rejects_radix3_grids(fk):
+def test_radix3_grids_outside_the_solver_and_bases(fk):
+    # the solver takes 3 * 2^m cubes up to 768 (tests/test_gpu_ns_radix3.py);
+    # the sine/cosine bases and the learned closure need power-of-two axes
     import torch
 
     plan = fk.fftk_plan_create(48, 48, 48)
     try:
         u = torch.zeros((3, 48, 48, 25, 2), device="cuda:0")
         with pytest.raises(fk.FFTKError):
-            fk.tarang_ns_step(plan, u.data_ptr(), fk.make_params(1e-3, 1e-3), 1, False, stream())
-        with pytest.raises(fk.FFTKError):
             fk.fftk_forward(plan, "SFF", u.data_ptr(), u.data_ptr() + 4 * 48**3, 1, stream())
+        model = fk.make_sgs_model(u.data_ptr(), np.zeros(5), np.ones(5), np.ones(6))
+        with pytest.raises(fk.FFTKError) as e:
+            fk.tarang_ns_step(plan, u.data_ptr(), fk.make_params(1e-3, 1e-3, sgs_model=model), 1, False, stream())
+        assert e.value.status == fk.FFTK_ERR_UNSUPPORTED_SIZE
+    finally:
+        fk.fftk_plan_destroy(plan)
+    plan = fk.fftk_plan_create(1536, 1536, 1536)
+    try:
+        with pytest.raises(fk.FFTKError) as e:
+            fk.tarang_ns_step(plan, u.data_ptr(), fk.make_params(1e-3, 1e-3), 1, False, stream())
+        assert e.value.status == fk.FFTK_ERR_UNSUPPORTED_SIZE
     finally:
         fk.fftk_plan_destroy(plan)
     for bad in ((5, 8, 8), (6, 6, 6), (8, 8, 9), (6144, 2, 12)):
