@@ -87,16 +87,18 @@ __device__ __forceinline__ float pow2_scale(float m) {
 //     Z_r[a0 + 16 a1]  -> U[k0'], times W_256^(a0 k0');
 //   stage 2 (tensor cores): for each (r, k0') the DFT-16 over a0
 //     -> X[R0 (k0' + 16 k1') + r]  (stored straight from TMEM).
-// One stage row per thread: T * L / 16 threads, 128-row M blocks, one TMEM
+// One stage row per thread: T * L / 16 = 1024 threads (T = 16384 / L columns:
+// 64 at L = 256 down to 8 at L = 2048, the widest row segments one CTA can
+// hold; 8-column tiles at L = 1024 and two CTAs per SM measured 0.64 of the
+// FP32 pair rate, 16 columns and one CTA 0.74), 128-row M blocks, one TMEM
 // lane per thread.  Every value handed to the tensor cores is scaled by the
 // same power of two per column: s brings the column's largest stage-0 output
 // component into [2^10, 2^11); stage-1 outputs are bounded by 16 times that,
 // so stage 2 takes them times 1/16 (folded into its twiddles).
-// The CTA is persistent (one TMEM allocation for all its tiles); two CTAs
-// per SM overlap one another's loads, MMAs and stores.
+// The CTA is persistent (one TMEM allocation for all its tiles).
 template <int L>
 struct TC2 {
-  static constexpr int T = L <= 512 ? 16 : 8192 / L;  // columns per tile
+  static constexpr int T = 16384 / L;  // columns per tile: the widest a 1024-thread CTA holds
   static constexpr int R0 = L / 256;                   // leading FP32 radix
   static constexpr int A1 = 16 / R0;                   // stage-0 butterflies per thread
   static constexpr int THREADS = T * L / 16;           // DFT-16 rows per stage
