@@ -28,6 +28,16 @@
 #include "tcgen05.cuh"
 
 namespace fftk {
+// ---------------------------------------------------- padded workspace ---
+// Row length of the fused passes' six-field workspace: n/2 + 1 rounded up to
+// a multiple of 16 complex values (272 at n = 512, 528 at n = 1024), so that
+// every (x, y) row starts on a 128-byte line and a tile of 16 (or 8) k_z
+// columns covers whole lines.  With rows of n/2 + 1 values each 128-byte row
+// segment straddles two lines: measured on the access patterns alone, the
+// inverse x pass's writes ran at 2.5 TB/s against 4.3 TB/s on lines, the y
+// passes' at 5.2 against 6.4 TB/s.  The caller's spectra keep n/2 + 1.
+__host__ __device__ constexpr long long ns_row(int n) { return ((long long)(n / 2 + 1) + 15) / 16 * 16; }
+
 // ------------------------------------------------------------ x/y config ---
 // Single-field passes (inverse x with the curl, both y passes): the strided
 // FFT pass configuration, 16 values per thread, 16 k_z columns per tile
@@ -48,7 +58,7 @@ struct NXCfg {
 template <int N, int SIGN>
 __global__ void __launch_bounds__(NXCfg<N>::THREADS, NXCfg<N>::MINB)
     k_ns_ypass(float2* w, NSGeom g, int ktiles, const float2* __restrict__ tw) {
-  constexpr long long H1 = N / 2 + 1, MM = (long long)N * N * H1;  // geometry of the n^3 grid
+  constexpr long long H1 = ns_row(N), MM = (long long)N * N * H1;  // the padded workspace
   constexpr int KD = (N - 1) / 3;                                  // largest kept |k| (2/3 rule)
   using C = NXCfg<N>;
   constexpr int G = C::G, S = C::S, T = C::T;
@@ -123,17 +133,19 @@ __global__ void __launch_bounds__(NICfg<N>::THREADS, NICfg<N>::MINB)
     k_ns_invx(const float2* __restrict__ u, float2* __restrict__ w, NSGeom g, int ktiles,
               const float2* __restrict__ tw) {
   constexpr long long H1 = N / 2 + 1, MM = (long long)N * N * H1;  // geometry of the n^3 grid
+  constexpr long long HW = ns_row(N), MW = (long long)N * N * HW;  // the padded workspace
   constexpr int KD = (N - 1) / 3;                                  // largest kept |k| (2/3 rule)
   using C = NICfg<N>;
   constexpr int G = C::G, S = C::S, T = C::T;
   extern __shared__ float2 smn[];
   const int c = threadIdx.x % T, j = threadIdx.x / T;
   const int dky = blockIdx.x / ktiles;
+  const int ay = dense_to_a(dky, N, KD);
   const int kz = (blockIdx.x - dky * ktiles) * T + c;
   const bool valid = kz < (KD + 1);
-  const int ay = dense_to_a(dky, N, KD);
   const long long q = (long long)ay * H1 + kz;
   const long long rs = (long long)N * H1;
+  const long long qw = (long long)ay * HW + kz, rw = (long long)N * HW;
   const float ky = (float)kwav(ay, N), kzf = (float)kz;
   const ColX<T> xc{smn, c};
   auto load = [&](int f, float2(&v)[G], bool ikx) {
@@ -148,7 +160,7 @@ __global__ void __launch_bounds__(NICfg<N>::THREADS, NICfg<N>::MINB)
   auto store = [&](int f, const float2(&v)[G]) {
     if (valid) {
 #pragma unroll
-      for (int m = 0; m < G; ++m) w[f * MM + (j + m * S) * rs + q] = v[m];
+      for (int m = 0; m < G; ++m) w[f * MW + (j + m * S) * rw + qw] = v[m];
     }
   };
   float2 a[G], b[G];
@@ -235,10 +247,10 @@ __device__ __forceinline__ float2 mul_root32(float2 a, int q) {
 //    asynchronous copy into one of two staging buffers, issued two fields
 //    ahead of their use, so the global loads' latency overlaps the transforms
 //    of the field before; the c2r reads X[k] and its mirror X[H - k] from there.
-template <int N>
+template <int N, int HW>  // HW: row length of the workspace (n/2 + 1, or the fused path's padded rows)
 __global__ void __launch_bounds__(NZCfg<N>::THREADS, NZCfg<N>::MINB)
     k_ns_z(float2* w, NSGeom g, const float2* __restrict__ tw, int* err) {
-  constexpr long long H1 = N / 2 + 1, MM = (long long)N * N * H1;  // geometry of the n^3 grid
+  constexpr long long H1 = HW, MM = (long long)N * N * H1;  // geometry of the workspace
   using C = NZCfg<N>;
   constexpr int H = C::H, G = C::G, S = C::S;
   constexpr int LOGN = Log2<N>::value;
@@ -253,11 +265,12 @@ __global__ void __launch_bounds__(NZCfg<N>::THREADS, NZCfg<N>::MINB)
   uint64_t* bar = reinterpret_cast<uint64_t*>(smz + (C::FIELDS + C::STAGE) / sizeof(float2)) + 2 * li;
 
   // Field f's element k of this line sits at element f MM + line H1 + k.  MM
-  // is even and H1 odd, so the line starts 16-byte aligned for even lines and
-  // 8 bytes past a 16-byte boundary for odd ones: the copy starts `lead`
-  // elements early (the previous line's last value, k_z = n/2, which this
-  // kernel never writes) and ends at k_z <= kc, inside the line.
-  const int lead = (int)(line & 1);
+  // is even; with H1 odd (rows of n/2 + 1) the line starts 16-byte aligned for
+  // even lines and 8 bytes past a 16-byte boundary for odd ones: the copy then
+  // starts `lead` elements early (the previous line's last value, k_z = n/2,
+  // which this kernel never writes) and ends at k_z <= kc, inside the line.
+  // With padded rows (H1 a multiple of 16) every line is aligned.
+  const int lead = (int)((line * H1) & 1);
   const uint32_t bytes = (uint32_t)(sizeof(float2) * ((KC + lead + 1) & ~1));
   auto issue = [&](int f) {  // one thread of the line; buffer f & 1 was last read two fields ago
     uint64_t* b = bar + (f & 1);
@@ -501,17 +514,19 @@ __global__ void __launch_bounds__(NUCfg<N>::THREADS, NUCfg<N>::MINB)
               NSGeom g, int ktiles, NSUpdate upd, int mode, const float2* __restrict__ extra,
               const float2* __restrict__ tw) {
   constexpr long long H1 = N / 2 + 1, MM = (long long)N * N * H1;  // geometry of the n^3 grid
+  constexpr long long HW = ns_row(N), MW = (long long)N * N * HW;  // the padded workspace (nh)
   constexpr int KD = (N - 1) / 3;                                  // largest kept |k| (2/3 rule)
   using C = NUCfg<N>;
   constexpr int G = C::G, S = C::S, T = C::T;
   extern __shared__ float2 smn[];
   const int c = threadIdx.x % T, j = threadIdx.x / T;
   const int dky = blockIdx.x / ktiles;
+  const int ay = dense_to_a(dky, N, KD);
   const int kz = (blockIdx.x - dky * ktiles) * T + c;
   const bool valid = kz < (KD + 1);
-  const int ay = dense_to_a(dky, N, KD);
   const long long q = (long long)ay * H1 + kz;
   const long long rs = (long long)N * H1;
+  const long long qw = (long long)ay * HW + kz, rw = (long long)N * HW;
   const ColX<T> xc{smn, c};
   // fields 0 and 1 are parked in shared memory after their transforms (this
   // thread's slots only), so one field at a time is held in registers
@@ -521,7 +536,7 @@ __global__ void __launch_bounds__(NUCfg<N>::THREADS, NUCfg<N>::MINB)
   for (int f = 0; f < 3; ++f) {
 #pragma unroll
     for (int m = 0; m < G; ++m)
-      V[m] = valid ? nh[f * MM + (j + m * S) * rs + q] : make_float2(0.f, 0.f);
+      V[m] = valid ? nh[f * MW + (j + m * S) * rw + qw] : make_float2(0.f, 0.f);
     fft_line<N, G, -1>(V, j, xc, tw);
     if (f < 2) {
 #pragma unroll
@@ -602,8 +617,9 @@ fftk_status ns_ensure(fftk_plan p) {
   s->kmax = ns_kmax(p->nx);
   s->etab_len = 3 * s->g.kd * s->g.kd + 1;
   const size_t fb = sizeof(float2) * (size_t)s->g.M;
+  const size_t fw = sizeof(float2) * (size_t)p->nx * p->nx * (size_t)ns_row(p->nx);  // padded rows (fused path)
   const int width = 2 + s->kmax + 1;
-  cudaError_t e = cudaMalloc(&s->w, 6 * fb);
+  cudaError_t e = cudaMalloc(&s->w, 6 * (fw > fb ? fw : fb));
   if (e == cudaSuccess) e = cudaMalloc(&s->u1, 3 * fb);
   if (e == cudaSuccess) e = cudaMemset(s->u1, 0, 3 * fb);
   if (e == cudaSuccess) e = cudaMalloc(&s->etab, sizeof(float2) * 2 * (size_t)s->etab_len);
@@ -666,7 +682,10 @@ struct NSLaunch {
         err = cudaFuncSetAttribute(k_ns_fwdx<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)NUCfg<N>::SMEM);
       if (err == cudaSuccess)
-        err = cudaFuncSetAttribute(k_ns_z<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        err = cudaFuncSetAttribute(k_ns_z<N, (int)ns_row(N)>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)NZCfg<N>::SMEM);
+      if (err == cudaSuccess)
+        err = cudaFuncSetAttribute(k_ns_z<N, N / 2 + 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)NZCfg<N>::SMEM);
       return err;
     });
@@ -681,8 +700,8 @@ struct NSLaunch {
     NSWork* s = p->ns;
     LaunchScope ls(p, KK_NS_Z, st);
     const long long lines = (long long)N * N;
-    k_ns_z<N><<<(unsigned)((lines + Z::LPC - 1) / Z::LPC), Z::THREADS, Z::SMEM, st>>>(s->w, s->g, twiddles(p, N),
-                                                                                    p->d_err);
+    k_ns_z<N, N / 2 + 1><<<(unsigned)((lines + Z::LPC - 1) / Z::LPC), Z::THREADS, Z::SMEM, st>>>(
+        s->w, s->g, twiddles(p, N), p->d_err);
     return cudaGetLastError();
   }
 
@@ -714,8 +733,8 @@ struct NSLaunch {
     {
       LaunchScope ls(p, KK_NS_Z, st);
       const long long lines = (long long)N * N;
-      k_ns_z<N><<<(unsigned)((lines + Z::LPC - 1) / Z::LPC), Z::THREADS, Z::SMEM, st>>>(s->w, g, twiddles(p, N),
-                                                                                       p->d_err);
+      k_ns_z<N, (int)ns_row(N)><<<(unsigned)((lines + Z::LPC - 1) / Z::LPC), Z::THREADS, Z::SMEM, st>>>(
+          s->w, g, twiddles(p, N), p->d_err);
     }
     {
       LaunchScope ls(p, KK_NS_FWDY, st);
