@@ -195,20 +195,24 @@ __global__ void __launch_bounds__(NICfg<N>::THREADS, NICfg<N>::MINB)
 // exchange through shared memory (8 values per thread would need three stages
 // and two exchanges, and the exchanges dominated the L1 traffic).  A thread
 // holds up to four such arrays (u x omega accumulators and a vorticity
-// component), 241 registers at n = 512: two CTAs of 128 threads per SM.
+// component), 230 registers at n = 512: two CTAs of 128 threads per SM.
+// Measured and dropped: three CTAs per SM with one staging buffer (168
+// registers, 1.120 against 1.126 ms), CTAs of 64 or 32 threads with five or
+// ten per SM (spills; 1.20 ms), the velocity parked in TMEM (slower).
 template <int N>
 struct NZCfg {
   static constexpr int H = N / 2;
   static constexpr int G = H < 16 ? H : 16;
   static constexpr int S = H / G;
   static constexpr int LPC = S >= 128 ? 1 : 128 / S;
+  static constexpr int NBUF = 2;                  // staging buffers per line
   static constexpr int THREADS = LPC * S;
   static constexpr bool WARP = S <= 32;
   static constexpr int KC = (N - 1) / 3 + 1;      // kept k_z count (2/3 rule)
   static constexpr int KCP = (KC + 2) & ~1;       // staged values per line and buffer (KC + alignment slack)
   static constexpr size_t FIELDS = sizeof(float2) * (size_t)LPC * H * 4;  // exchange + 3 parked fields
-  static constexpr size_t STAGE = sizeof(float2) * (size_t)LPC * 2 * KCP;  // two staging buffers per line
-  static constexpr size_t SMEM = FIELDS + STAGE + sizeof(uint64_t) * 2 * LPC;  // + one mbarrier per buffer
+  static constexpr size_t STAGE = sizeof(float2) * (size_t)LPC * NBUF * KCP;  // staging buffers
+  static constexpr size_t SMEM = FIELDS + STAGE + sizeof(uint64_t) * NBUF * LPC;  // + one mbarrier per buffer
   static constexpr int MINB = G == 16 ? 2 : 4;    // CTAs per SM the registers must allow
 };
 
@@ -261,8 +265,9 @@ __global__ void __launch_bounds__(NZCfg<N>::THREADS, NZCfg<N>::MINB)
   const bool valid = line < (long long)N * N;
   const LineX<C::WARP> xc{smz + li * H};
   float2* park = smz + C::LPC * H + li * 3 * H + j;  // [3][G][S] per line, this thread's column
-  float2* stage = smz + C::FIELDS / sizeof(float2) + li * 2 * C::KCP;  // this line's two buffers
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smz + (C::FIELDS + C::STAGE) / sizeof(float2)) + 2 * li;
+  constexpr int NB = C::NBUF;
+  float2* stage = smz + C::FIELDS / sizeof(float2) + li * NB * C::KCP;  // this line's buffers
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smz + (C::FIELDS + C::STAGE) / sizeof(float2)) + NB * li;
 
   // Field f's element k of this line sits at element f MM + line H1 + k.  MM
   // is even; with H1 odd (rows of n/2 + 1) the line starts 16-byte aligned for
@@ -272,26 +277,25 @@ __global__ void __launch_bounds__(NZCfg<N>::THREADS, NZCfg<N>::MINB)
   // With padded rows (H1 a multiple of 16) every line is aligned.
   const int lead = (int)((line * H1) & 1);
   const uint32_t bytes = (uint32_t)(sizeof(float2) * ((KC + lead + 1) & ~1));
-  auto issue = [&](int f) {  // one thread of the line; buffer f & 1 was last read two fields ago
-    uint64_t* b = bar + (f & 1);
+  auto issue = [&](int f) {  // one thread of the line; buffer f % NB was last read NB fields ago
+    uint64_t* b = bar + f % NB;
     tcg::fence_smem_async();
     tcg::mbar_expect(b, bytes);
-    tcg::bulk_g2s(stage + (f & 1) * C::KCP, w + f * MM + line * H1 - lead, bytes, b);
+    tcg::bulk_g2s(stage + (f % NB) * C::KCP, w + f * MM + line * H1 - lead, bytes, b);
   };
   bool ok = true;
   auto arrive = [&](int f) {  // wait for field f's copy (bounded; an expired wait is reported)
     if (!valid) return;
-    if (!tcg::mbar_wait(bar + (f & 1), (uint32_t)((f >> 1) & 1))) {
+    const uint32_t par = (uint32_t)((f / NB) & 1);
+    if (!tcg::mbar_wait(bar + f % NB, par)) {
       if (j == 0 && ok) atomicOr(err, 1);
       ok = false;
-      tcg::mbar_wait(bar + (f & 1), (uint32_t)((f >> 1) & 1));  // once more for the copy still in flight
+      tcg::mbar_wait(bar + f % NB, par);  // once more for the copy still in flight
     }
   };
   if (j == 0 && valid) {
-    tcg::mbar_init(bar);
-    tcg::mbar_init(bar + 1);
-    issue(0);
-    issue(1);
+    for (int b = 0; b < NB; ++b) tcg::mbar_init(bar + b);
+    for (int b = 0; b < NB; ++b) issue(b);
   }
   xc.sync();  // the barriers are initialised before anyone polls them
   // exp(-2 pi i k / N) at k = j + m S is Wj exp(-2 pi i m / (2G)) (N = 2 G S):
@@ -301,7 +305,7 @@ __global__ void __launch_bounds__(NZCfg<N>::THREADS, NZCfg<N>::MINB)
 
   // inverse z transform of field f (half-complex -> N real points, two per slot)
   auto c2r = [&](int f, float2 (&U)[G]) {
-    const float2* src = stage + (f & 1) * C::KCP + lead;
+    const float2* src = stage + (f % NB) * C::KCP + lead;
     arrive(f);
 #pragma unroll
     for (int m = 0; m < G; ++m) {
@@ -321,8 +325,8 @@ __global__ void __launch_bounds__(NZCfg<N>::THREADS, NZCfg<N>::MINB)
     if constexpr (S == 1) xc.sync();  // (one thread per line: the transform has no exchange)
     fft_line<H, G, +1, LOGN>(U, j, xc, tw);
     // every thread of the line has passed an exchange barrier since it read
-    // the buffer: refill it with field f + 2
-    if (f + 2 < 6 && j == 0 && valid) issue(f + 2);
+    // the buffer: refill it with field f + NB
+    if (f + NB < 6 && j == 0 && valid) issue(f + NB);
   };
 
   {
