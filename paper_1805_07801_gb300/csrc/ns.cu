@@ -300,6 +300,8 @@ __global__ void __launch_bounds__(NZCfg<N>::THREADS, NZCfg<N>::MINB)
   xc.sync();  // the barriers are initialised before anyone polls them
   // exp(-2 pi i k / N) at k = j + m S is Wj exp(-2 pi i m / (2G)) (N = 2 G S):
   // one table load per thread instead of one per value
+  // (measured against one table load per value at 16 values per thread:
+  // 1.126 against 1.190 ms per launch at 512^3)
   const float2 Wj = __ldg(&tw[j]);
   auto twk = [&](int m) { return mul_root32(Wj, m * (16 / G)); };
 
