@@ -75,6 +75,7 @@ def lib():
             L.oracle_ic_random.argtypes = [vp, vp, c.c_int, c.c_double, c.c_double]
             L.oracle_box_filter.argtypes = [vp, c.c_int, c.c_int, vp, vp]
             L.oracle_gradient.argtypes = [vp, c.c_int, vp]
+            L.oracle_les_stress.argtypes = [vp, vp, c.c_int, vp]
             L.oracle_invariants.argtypes = [vp, vp]
             L.oracle_invariants.restype = None
             L.oracle_sym_eig3.argtypes = [vp, vp, vp]
@@ -378,6 +379,16 @@ def box_filter(u, factor):
     tau = np.empty((6, m, m, m))
     _check(lib().oracle_box_filter(_ptr(u), n, factor, _ptr(ubar), _ptr(tau)), "box_filter")
     return ubar, tau
+
+
+def les_stress(ubar, tau):
+    """T[tau + ubar_i ubar_j - (T ubar)_i (T ubar)_j] on the coarse grid (T: the 2/3 truncation)."""
+    ubar = np.ascontiguousarray(ubar, dtype=np.float64)
+    tau = np.ascontiguousarray(tau, dtype=np.float64)
+    m = ubar.shape[1]
+    out = np.empty((6, m, m, m))
+    _check(lib().oracle_les_stress(_ptr(ubar), _ptr(tau), m, _ptr(out)), "les_stress")
+    return out
 
 
 def gradient(u):

@@ -1349,6 +1349,41 @@ int oracle_box_filter(const double *u, int n, int factor, double *ubar, double *
   return 0;
 }
 
+/* The subgrid stress of the coarse solver as it computes (the closure's
+ * training target): the coarse grid keeps only the 2/3 set of the filtered
+ * field, ubar_T = T ubar, and forms its products dealiased, so the exact
+ * coarse equations for ubar_T carry
+ *   tau_les_ij = T[ <u_i u_j> - ubar_T,i ubar_T,j ],
+ * with <u_i u_j> = tau_ij + ubar_i ubar_j (the box-filtered products) and T
+ * the 2/3 truncation on the m^3 grid.  In: ubar[3][m^3], tau[6][m^3]; out:
+ * tau_les[6][m^3] (pairs xx, yy, zz, xy, xz, yz). */
+int oracle_les_stress(const double *ubar, const double *tau, int m, double *out) {
+  if (!ok_grid(m)) return -1;
+  const long Mn = m, HZ = m / 2 + 1, M = Mn * Mn * HZ, R = Mn * Mn * Mn;
+  cplx *sp = (cplx *)malloc(sizeof(cplx) * (size_t)M);
+  double *ut = (double *)malloc(sizeof(double) * 3 * (size_t)R);
+  double *pr = (double *)malloc(sizeof(double) * (size_t)R);
+  if (!sp || !ut || !pr) return -2;
+  /* ubar_T = T ubar */
+  for (int q = 0; q < 3; q++) {
+    oracle_rfft3(ubar + q * R, sp, m, m, m);
+    oracle_dealias(sp, 1, m);
+    oracle_irfft3(sp, ut + q * R, m, m, m);
+  }
+  for (int p = 0; p < 6; p++) {
+    const int i = kPairI[p], j = kPairJ[p];
+    for (long x = 0; x < R; x++)
+      pr[x] = tau[p * R + x] + ubar[i * R + x] * ubar[j * R + x] - ut[i * R + x] * ut[j * R + x];
+    oracle_rfft3(pr, sp, m, m, m);
+    oracle_dealias(sp, 1, m);
+    oracle_irfft3(sp, out + p * R, m, m, m);
+  }
+  free(sp);
+  free(ut);
+  free(pr);
+  return 0;
+}
+
 int oracle_gradient(const double *u, int m, double *A) {
   if (!is_pow2(m) || m < 2) return -1;
   const long Mn = m, HZ = m / 2 + 1, M = Mn * Mn * HZ, R = Mn * Mn * Mn;

@@ -139,6 +139,12 @@ int oracle_project(ocplx *uhat, int n);
  * in the order xx, yy, zz, xy, xz, yz (m = n / factor). */
 int oracle_box_filter(const double *u, int n, int factor, double *ubar, double *tau);
 
+/* The subgrid stress of the coarse solver as it computes: with T the 2/3
+ * truncation on the m^3 grid and ubar_T = T ubar,
+ *   tau_les_ij = T[ tau_ij + ubar_i ubar_j - ubar_T,i ubar_T,j ]
+ * (ubar[3][m^3], tau[6][m^3] from oracle_box_filter; out[6][m^3]). */
+int oracle_les_stress(const double *ubar, const double *tau, int m, double *out);
+
 /* Velocity gradient A[i*3+j] = d u_i / d x_j of a real field u[3][m][m][m] on
  * the 2 pi-periodic grid, from the 2/3-truncated spectrum. A: [9][m][m][m]. */
 int oracle_gradient(const double *u, int m, double *A);

@@ -3,6 +3,8 @@ invariants, eigenframe, MLP (forward, backward, Adam) and the SGS force."""
 import numpy as np
 import pytest
 
+import synth
+
 RNG = np.random.default_rng(2024)
 
 
@@ -174,3 +176,43 @@ def test_box_filter_brute_force_random(oracle_mod):
     for p, (i, j) in enumerate(pairs):
         want = blk(u[i] * u[j]) - blk(u[i]) * blk(u[j])
         assert np.max(np.abs(tau[p] - want)) < 1e-13
+
+
+def _np_truncate(f):
+    """numpy's 2/3 truncation of real fields [..., m, m, m] (keep 3|k_i| < m)."""
+    m = f.shape[-1]
+    F = np.fft.rfftn(f, axes=(-3, -2, -1))
+    a = np.arange(m)
+    k = np.where(2 * a < m, a, a - m)
+    KX, KY, KZ = np.meshgrid(k, k, np.arange(m // 2 + 1), indexing="ij")
+    keep = (3 * np.abs(KX) < m) & (3 * np.abs(KY) < m) & (3 * KZ < m)
+    return np.fft.irfftn(F * keep, s=(m, m, m), axes=(-3, -2, -1))
+
+
+_PAIRS = [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]
+
+
+def test_les_stress_against_numpy_from_a_fine_field(oracle_mod):
+    # tau_les = T[<u_i u_j> - (T ubar)_i (T ubar)_j] with the block means and
+    # the truncation both done by numpy on a seeded fine field
+    n, f = 32, 4
+    m = n // f
+    u = np.stack([synth.uniform_pm1(3, c, (n, n, n)).astype(np.float64) for c in range(3)])
+    ubar, tau = oracle_mod.box_filter(u, f)
+    got = oracle_mod.les_stress(ubar, tau)
+    blocks = lambda a: a.reshape(m, f, m, f, m, f).mean(axis=(1, 3, 5))
+    ub = np.stack([blocks(u[c]) for c in range(3)])
+    ut = _np_truncate(ub)
+    want = np.stack([_np_truncate(blocks(u[i] * u[j]) - ut[i] * ut[j]) for (i, j) in _PAIRS])
+    assert np.max(np.abs(got - want)) < 1e-13
+
+
+def test_les_stress_of_a_band_limited_filtered_field_is_the_truncated_stress(oracle_mod):
+    # when ubar already lies in the kept set, T ubar = ubar and tau_les = T tau
+    m = 12
+    g = 2 * np.pi * np.arange(m) / m
+    X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
+    ubar = np.stack([np.sin(X + 2 * Y), np.cos(3 * Z) * 0.5, np.sin(Y - Z)])
+    tau = np.stack([synth.uniform_pm1(5, p, (m, m, m)).astype(np.float64) for p in range(6)])
+    got = oracle_mod.les_stress(ubar, tau)
+    assert np.max(np.abs(got - _np_truncate(tau))) < 1e-13
