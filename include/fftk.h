@@ -381,6 +381,18 @@ fftk_status tarang_box_filter(fftk_plan p, const void *uhat, int factor, float *
 fftk_status tarang_closure_features(fftk_plan p, const float *ubar, const float *tau, float *inv,
                                     float *frame, float *tau_frame, void *cuda_stream);
 
+/* The subgrid stress of the coarse solver as it computes it (the closure's
+ * training target; the paper has no closure).  The coarse grid (plan m^3,
+ * power of two) keeps only the 2/3 set of a filtered field, ubar_T = T ubar
+ * with T the truncation 3|k_i| < m, and forms its products dealiased, so
+ * the exact coarse equations for ubar_T carry
+ *   tau_les_ij = T[ tau_ij + ubar_i ubar_j - ubar_T,i ubar_T,j ]
+ * (tau + ubar ubar = the box-filtered products <u_i u_j>).  ubar[3][m^3] and
+ * tau[6][m^3] as from tarang_box_filter; out[6][m^3] in the same pair order.
+ * All three 16-byte aligned device arrays.  Synchronises; allocates its
+ * scratch. */
+fftk_status tarang_les_stress(fftk_plan p, const float *ubar, const float *tau, float *out, void *cuda_stream);
+
 /* MLP 5 -> 64 -> 64 -> 64 -> 6 with tanh on the hidden layers.  params: 9094
  * FP32 values W1[64][5], b1[64], W2[64][64], b2[64], W3[64][64], b3[64],
  * W4[6][64], b4[6].  Each layer's input (x, h1, h2, h3) is rounded to

@@ -120,6 +120,7 @@ def lib() -> ctypes.CDLL:
             "tarang_mlp_sync": ([vp, vp], i),
             "tarang_sgs_train": ([vp, vp, vp, vp, i, i, vp, vp, ll, i, c.c_float, c.c_ulonglong, vp, i, vp], i),
             "tarang_mlp_loss_grad": ([vp, vp, vp, vp, i, vp, vp, vp], i),
+            "tarang_les_stress": ([vp, vp, vp, vp, vp], i),
             "tarang_mlp_loss_grad_mode": ([vp, vp, vp, vp, i, vp, vp, i, vp], i),
             "tarang_mlp_forward_mode": ([vp, vp, vp, vp, i, i, vp], i),
             "tarang_mlp_adam": ([vp, vp, vp, vp, i, c.c_float, c.c_float, c.c_float, c.c_float, vp], i),
@@ -330,6 +331,11 @@ def tarang_box_filter(plan: int, uhat_ptr, factor: int, ubar_ptr, tau_ptr, strea
 def tarang_closure_features(plan: int, ubar_ptr, tau_ptr, inv_ptr, frame_ptr, tau_frame_ptr, stream=0) -> None:
     _check(lib().tarang_closure_features(_vp(plan), _vp(ubar_ptr), _vp(tau_ptr), _vp(inv_ptr), _vp(frame_ptr),
                                          _vp(tau_frame_ptr), _vp(stream)), "tarang_closure_features")
+
+
+def tarang_les_stress(plan: int, ubar_ptr, tau_ptr, out_ptr, stream=0) -> None:
+    _check(lib().tarang_les_stress(_vp(plan), _vp(ubar_ptr), _vp(tau_ptr), _vp(out_ptr), _vp(stream)),
+           "tarang_les_stress")
 
 
 def tarang_mlp_create(max_batch: int) -> int:

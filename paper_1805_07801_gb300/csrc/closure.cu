@@ -92,6 +92,40 @@ __device__ __forceinline__ int kw(int a, int n) { return 2 * a < n ? a : a - n; 
 __device__ __forceinline__ int kdv(int k, int n) { return 2 * (k < 0 ? -k : k) == n ? 0 : k; }
 
 // spectra of the 9 gradient components i k_j u_i from a 2/3-truncated copy of u
+// zero every mode outside the 2/3 set (3|k_i| < m on every axis) of nf
+// spectra [nf][m][m][m/2+1]
+__global__ void k_truncate(float2* __restrict__ f, int m, int nf) {
+  const int h1 = m / 2 + 1;
+  const long long M = (long long)m * m * h1;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < (long long)nf * M;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long r = i % M;
+    const int c = (int)(r % h1);
+    const long long ab = r / h1;
+    const int b = (int)(ab % m), a = (int)(ab / m);
+    const int ka = 2 * a < m ? a : a - m, kb = 2 * b < m ? b : b - m;
+    if (!(3 * abs(ka) < m && 3 * abs(kb) < m && 3 * c < m)) f[i] = make_float2(0.f, 0.f);
+  }
+}
+
+// P_p = tau_p + ubar_i ubar_j - ut_i ut_j for the six pairs (i, j) of
+// xx, yy, zz, xy, xz, yz (FP32 products of FP32 fields)
+__global__ void k_les_products(const float* __restrict__ ubar, const float* __restrict__ tau,
+                               const float* __restrict__ ut, float* __restrict__ P, long long R) {
+  const int pi[6] = {0, 1, 2, 0, 0, 1}, pj[6] = {0, 1, 2, 1, 2, 2};
+  for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < R; x += (long long)gridDim.x * blockDim.x) {
+    float ub[3], tt[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      ub[q] = ubar[q * R + x];
+      tt[q] = ut[q * R + x];
+    }
+#pragma unroll
+    for (int p = 0; p < 6; ++p)
+      P[p * R + x] = fmaf(ub[pi[p]], ub[pj[p]], tau[p * R + x]) - tt[pi[p]] * tt[pj[p]];
+  }
+}
+
 __global__ void k_grad_spectra(const float2* __restrict__ uh, float2* __restrict__ gh, int n) {
   const int h1 = n / 2 + 1;
   const long long M = (long long)n * n * h1;
@@ -852,6 +886,49 @@ extern "C" fftk_status tarang_closure_features(fftk_plan p, const float* ubar, c
   cudaFree(uh);
   cudaFree(gh);
   cudaFree(A);
+  return s;
+}
+
+extern "C" fftk_status tarang_les_stress(fftk_plan p, const float* ubar, const float* tau, float* out,
+                                         void* cuda_stream) {
+  if (!p || !ubar || !tau || !out || mis16(ubar) || mis16(tau) || mis16(out)) return FFTK_ERR_INVALID_ARG;
+  if (p->nx != p->ny || p->nx != p->nz || p->nx < 8 || !is_pow2(p->nx)) return FFTK_ERR_UNSUPPORTED_SIZE;
+  const int m = p->nx;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  const long long R = (long long)m * m * m, M = (long long)m * m * (m / 2 + 1);
+  float2* sp = nullptr;
+  float* ut = nullptr;
+  float* P = nullptr;
+  cudaError_t e = cudaMalloc(&sp, sizeof(float2) * 6 * (size_t)M);
+  if (e == cudaSuccess) e = cudaMalloc(&ut, sizeof(float) * 3 * (size_t)R);
+  if (e == cudaSuccess) e = cudaMalloc(&P, sizeof(float) * 6 * (size_t)R);
+  fftk_status s = e == cudaSuccess ? FFTK_OK : FFTK_ERR_OOM;
+  // ubar_T = T ubar
+  if (s == FFTK_OK) s = fftk_r2c(p, ubar, sp, 3, cuda_stream);
+  if (s == FFTK_OK) {
+    LaunchScope ls(p, KK_AUX, st);
+    k_truncate<<<grid_for(3 * M, 256), 256, 0, st>>>(sp, m, 3);
+    s = from_cuda(cudaGetLastError());
+  }
+  if (s == FFTK_OK) s = fftk_c2r(p, sp, ut, 3, cuda_stream);
+  // T[tau + ubar_i ubar_j - ubar_T,i ubar_T,j]
+  if (s == FFTK_OK) {
+    LaunchScope ls(p, KK_AUX, st);
+    k_les_products<<<grid_for(R, 256), 256, 0, st>>>(ubar, tau, ut, P, R);
+    s = from_cuda(cudaGetLastError());
+  }
+  if (s == FFTK_OK) s = fftk_r2c(p, P, sp, 6, cuda_stream);
+  if (s == FFTK_OK) {
+    LaunchScope ls(p, KK_AUX, st);
+    k_truncate<<<grid_for(6 * M, 256), 256, 0, st>>>(sp, m, 6);
+    s = from_cuda(cudaGetLastError());
+  }
+  if (s == FFTK_OK) s = fftk_c2r(p, sp, out, 6, cuda_stream);
+  if (s == FFTK_OK) s = from_cuda(cudaStreamSynchronize(st));
+  cudaGetLastError();
+  cudaFree(sp);
+  cudaFree(ut);
+  cudaFree(P);
   return s;
 }
 

@@ -62,6 +62,32 @@ def test_box_filter_matches_oracle(fk, oracle_mod, n, factor):
     assert np.max(np.abs(tau.cpu().numpy() - tau_o)) < 1e-5 * uu
 
 
+@pytest.mark.parametrize("m", [16, 32])
+def test_les_stress_matches_oracle(fk, oracle_mod, m):
+    # box filter of a 4x finer seeded field, then the coarse-solver stress
+    n = 4 * m
+    u = _ic(oracle_mod, n, seed=7, k0=float(m) / 2)
+    ur = oracle_mod.irfft3(u.astype(np.complex128), n)
+    ub_o, tau_o = oracle_mod.box_filter(ur, 4)
+    want = oracle_mod.les_stress(ub_o, tau_o)
+    plan = fk.fftk_plan_create(m, m, m)
+    try:
+        ubd, taud = _f32(ub_o), _f32(tau_o)
+        out = empty_real((6, m, m, m))
+        fk.tarang_les_stress(plan, ubd.data_ptr(), taud.data_ptr(), out.data_ptr(), stream())
+        got = out.cpu().numpy()
+        # the inputs as the kernels see them (FP32) through the FP64 oracle
+        want32 = oracle_mod.les_stress(ub_o.astype(np.float32).astype(np.float64),
+                                       tau_o.astype(np.float32).astype(np.float64))
+    finally:
+        fk.fftk_plan_destroy(plan)
+    uu = np.max(np.abs(tau_o[:3] + ub_o ** 2))
+    assert np.max(np.abs(got - want32)) < 1e-5 * uu
+    assert np.max(np.abs(got - want)) < 2e-5 * uu
+    # the filtered field reaches past the 2/3 set: the extra term is not small
+    assert np.max(np.abs(oracle_mod.les_stress(ub_o, 0 * tau_o))) > 1e-3 * uu
+
+
 def test_closure_features_match_oracle(fk, oracle_mod):
     m = 32
     u = _ic(oracle_mod, m, seed=2, k0=3.0)
