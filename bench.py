@@ -16,6 +16,7 @@ Multi-GPU runs (torchrun) are independent replicas: the method is not sharded.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -1109,7 +1110,7 @@ def run_fft_sweep(args):
                       "peak_GBps": hbm, "peak_kind": peak_kind, "sizes": out}), flush=True)
 
 
-def run_closure(which: str, out_path: str):
+def run_closure(which: str, out_path: str, flux_weights=None, targets=None):
     """The learned-closure workflow (resolved snapshots -> filtered data ->
     training -> coarse runs with and without the model); prints one JSON line
     and writes the full results to out_path."""
@@ -1119,6 +1120,10 @@ def run_closure(which: str, out_path: str):
     from paper_1805_07801_gb300 import les
 
     cfg = les.ClosureConfig() if which == "full" else les.ClosureConfig.small()
+    if flux_weights:
+        cfg = dataclasses.replace(cfg, flux_weights=tuple(flux_weights))
+    if targets:
+        cfg = dataclasses.replace(cfg, targets=tuple(targets))
     res = les.run(cfg, log=lambda s: print(s, file=sys.stderr, flush=True))
     if out_path:
         os.makedirs(os.path.dirname(os.path.abspath(out_path)), exist_ok=True)
@@ -1134,6 +1139,15 @@ def run_closure(which: str, out_path: str):
         for w in ("stated", "long"):
             if w in r:
                 line[name][w] = {k: r[w][k] for k in ("max_rel_err", "mean_rel_err", "shells_within_5pct")}
+    if "variants" in res:
+        line["variants"] = [{"target": v["target"], "flux_weight": v["flux_weight"],
+                             "heldout_loss": v.get("heldout_loss"),
+                             "heldout_loss_zero_model": v.get("heldout_loss_zero_model"),
+                             "stated": {k: v["model"]["stated"][k] for k in ("mean_rel_err", "max_rel_err",
+                                                                           "shells_within_5pct")},
+                             "long": {k: v["model"]["long"][k] for k in ("mean_rel_err", "max_rel_err",
+                                                                       "shells_within_5pct")}}
+                            for v in res["variants"] if v["model"]["finite"]]
     line["workload"] = f"closure {which}: {cfg.n}^3 -> {cfg.m}^3"
     print(json.dumps(line), flush=True)
 
@@ -1154,6 +1168,10 @@ def main():
     ap.add_argument("--closure", choices=["full", "small"], default=None,
                     help="run the learned-closure workflow instead of the benchmark")
     ap.add_argument("--closure-out", default="", help="JSON file for the closure workflow's results")
+    ap.add_argument("--flux-weights", type=float, nargs="*", default=None,
+                    help="closure: loss weights of the frame stress's diagonal components, one model each")
+    ap.add_argument("--targets", nargs="*", choices=["les", "box", "box_coarse", "blend"], default=None,
+                    help="closure: training data sets, one model each (default all four)")
     ap.add_argument("--fft-sweep", action="store_true", help="batched pair sweep 256^3 x 64 ... 2048^3")
     ap.add_argument("--forced", type=int, default=0, metavar="N",
                     help="run N^3 forced turbulence for --steps steps and print its JSON line")
@@ -1173,7 +1191,7 @@ def main():
         run_case(args.case)
         return
     if args.closure:
-        run_closure(args.closure, args.closure_out)
+        run_closure(args.closure, args.closure_out, args.flux_weights, args.targets)
         return
     if args.forced:
         run_forced(args.forced, args.steps)

@@ -14,7 +14,11 @@ keeps small host-side statistics):
 2. Closure data.  Each snapshot is box-filtered to the coarse grid
    (tarang_box_filter: ubar and tau_ij = <u_i u_j> - ubar_i ubar_j); the
    coarse gradient's five invariants, the strain eigenframe Q and the stress
-   in that frame Q^T tau Q come from tarang_closure_features.
+   in that frame Q^T tau Q come from tarang_closure_features.  The "les"
+   target instead takes the stress the coarse solver misses as it computes,
+   T[tau_ij + ubar_i ubar_j - (T ubar)_i (T ubar)_j] with T the 2/3
+   truncation (tarang_les_stress), and the features of the coarse state
+   P T ubar that the model sees at run time.
 3. Training.  The 5 -> 64 -> 64 -> 64 -> 6 tanh network maps normalised
    invariants to the normalised frame stress (MSE, Adam), through
    tarang_sgs_train; the last snapshot is held out.
@@ -35,10 +39,10 @@ import time
 import numpy as np
 import torch
 
-from . import (FFTKError, fftk_fill_normal, fftk_plan_create, fftk_plan_destroy, fftk_r2c, make_params,
+from . import (FFTKError, fftk_c2r, fftk_fill_normal, fftk_plan_create, fftk_plan_destroy, fftk_r2c, make_params,
                make_sgs_model, tarang_box_filter, tarang_closure_features, tarang_dealias_project, tarang_diag,
-               tarang_ic_random, tarang_mlp_create, tarang_mlp_destroy, tarang_mlp_loss_grad, tarang_ns_step,
-               tarang_sgs_train)
+               tarang_ic_random, tarang_les_stress, tarang_mlp_create, tarang_mlp_destroy, tarang_mlp_loss_grad,
+               tarang_ns_step, tarang_sgs_train)
 
 NPARAMS = 9094
 DIMS = (5, 64, 64, 64, 6)
@@ -67,6 +71,20 @@ class ClosureConfig:
     les_sample_every: int = 10
     kcmp: int = 20             # shells 1..kcmp are compared
     init_seed: int = 0         # network initialisation and batch order
+    # loss weight of the frame stress's diagonal components (the ones that
+    # carry the local energy flux -tau_ij S_ij in the strain eigenframe); one
+    # model is trained per value, on the same data, and the first is reported
+    # as "model"
+    flux_weights: tuple = (1.0,)
+    # training data per model: "les" = the stress the coarse solver misses
+    # as it computes (tarang_les_stress) with features of the coarse state
+    # P T ubar; "box" = the box-filter stress tau with features of ubar;
+    # "box_coarse" = tau with features of P T ubar (the state the model sees
+    # at run time); "blend" = (1 - blend) box_coarse + blend les, frame by
+    # frame (both share the features).  One model per (target, flux weight);
+    # the first is reported as "model"
+    targets: tuple = ("box", "box_coarse", "les", "blend")
+    blend: float = 0.5
 
     @property
     def factor(self) -> int:
@@ -77,7 +95,7 @@ class ClosureConfig:
         """256^3 resolved / 32^3 coarse (the same factor 8), shorter window
         and training: the workflow end to end in about a minute."""
         return cls(n=256, m=32, dt=1e-3, snapshot_every=1.25, ref_every=0.25, train_steps=3000, batch=16384,
-                   lr=2e-3, les_steps=2000, les_long_steps=5000, kcmp=10)
+                   lr=2e-3, les_steps=2000, les_long_steps=5000, kcmp=10, targets=("box",))
 
 
 def _dev_empty(shape, dtype=torch.float32):
@@ -118,23 +136,47 @@ def advance(plan: int, uhat, prm, steps: int) -> float:
 def filtered_state(plan_n: int, plan_m: int, uhat, cfg: ClosureConfig, features: bool):
     """Box filter of a resolved state onto the coarse grid: the coarse solver
     state (2/3-truncated, projected), its spectrum and, with `features`, the
-    closure data (invariants and frame stress, host copies)."""
+    closure data per training target (invariants and frame stress, host
+    copies)."""
     m = cfg.m
     R = m ** 3
     ubar = _dev_empty((3, m, m, m))
     tau = _dev_empty((6, m, m, m))
     tarang_box_filter(plan_n, uhat.data_ptr(), cfg.factor, ubar.data_ptr(), tau.data_ptr(), _stream())
-    out = {}
-    if features:
-        inv = _dev_empty((5, R))
-        frame = _dev_empty((9, R))
-        taup = _dev_empty((6, R))
-        tarang_closure_features(plan_m, ubar.data_ptr(), tau.data_ptr(), inv.data_ptr(), frame.data_ptr(),
-                                taup.data_ptr(), _stream())
-        out.update(inv=inv.cpu().numpy(), taup=taup.cpu().numpy())
     uc = _dev_empty((3, m, m, _half(m), 2))
     fftk_r2c(plan_m, ubar.data_ptr(), uc.data_ptr(), 3, _stream())
     tarang_dealias_project(plan_m, uc.data_ptr(), _stream())
+    out = {}
+    if features:
+        def closure_data(u, t):
+            inv = _dev_empty((5, R))
+            frame = _dev_empty((9, R))
+            taup = _dev_empty((6, R))
+            tarang_closure_features(plan_m, u.data_ptr(), t.data_ptr(), inv.data_ptr(), frame.data_ptr(),
+                                    taup.data_ptr(), _stream())
+            return dict(inv=inv.cpu().numpy(), taup=taup.cpu().numpy())
+
+        ucoarse = None
+        wanted = list(cfg.targets)
+        if "blend" in wanted:
+            wanted = [t for t in wanted if t != "blend"] + ["les", "box_coarse", "blend"]
+        for target in dict.fromkeys(wanted):
+            if target in ("les", "box_coarse") and ucoarse is None:
+                ucoarse = _dev_empty((3, m, m, m))
+                fftk_c2r(plan_m, uc.data_ptr(), ucoarse.data_ptr(), 3, _stream())
+            if target == "box":
+                out[target] = closure_data(ubar, tau)
+            elif target == "box_coarse":
+                out[target] = closure_data(ucoarse, tau)
+            elif target == "les":
+                tles = _dev_empty((6, m, m, m))
+                tarang_les_stress(plan_m, ubar.data_ptr(), tau.data_ptr(), tles.data_ptr(), _stream())
+                out[target] = closure_data(ucoarse, tles)
+            elif target == "blend":
+                out[target] = dict(inv=out["les"]["inv"],
+                                   taup=(1.0 - cfg.blend) * out["box_coarse"]["taup"] + cfg.blend * out["les"]["taup"])
+            else:
+                raise ValueError(f"unknown closure target {target!r}")
     E, eps, EK = tarang_diag(plan_m, uc.data_ptr(), cfg.nu, _stream())
     out.update(uc=uc, E=E, EK=np.asarray(EK))
     return out
@@ -176,13 +218,18 @@ def resolved_run(plan_n: int, plan_m: int, cfg: ClosureConfig, log=None):
     return snaps, np.mean(spectra, axis=0), len(spectra), steps / secs
 
 
-def normalisation(inv: np.ndarray, taup: np.ndarray):
+def normalisation(inv: np.ndarray, taup: np.ndarray, flux_weight: float = 1.0):
     """Input shift/scale (mean, 1/std of each invariant) and output scale (RMS
-    of each frame-stress component) over the training set."""
+    of each frame-stress component) over the training set.  A flux weight w
+    divides the scale of the diagonal components (xx, yy, zz of the frame
+    stress) by sqrt(w): their normalised targets, and so their squared errors
+    in the loss, grow by w, while the model's outputs are scaled back the
+    same way at inference."""
     shift = inv.mean(axis=1)
     scale = 1.0 / np.maximum(inv.std(axis=1), 1e-30)
     out_scale = np.sqrt(np.mean(taup.astype(np.float64) ** 2, axis=1))
     out_scale = np.maximum(out_scale, 1e-30)
+    out_scale[:3] /= np.sqrt(flux_weight)
     return shift, scale, out_scale
 
 
@@ -316,23 +363,9 @@ def run(cfg: ClosureConfig, log=print):
         # training set: every snapshot but the last, which is held out
         hold = snaps[-1] if len(snaps) > 1 else None
         tr = snaps[:-1] if len(snaps) > 1 else snaps
-        inv = np.concatenate([s["inv"] for s in tr], axis=1)
-        taup = np.concatenate([s["taup"] for s in tr], axis=1)
-        shift, scale, out_scale = normalisation(inv, taup)
-        x = ((inv.T - shift) * scale).astype(np.float32)
-        t = (taup.T / out_scale).astype(np.float32)
-        p, hist, secs, sps = train(x, t, cfg, log)
-        res.update(train_seconds=secs, train_samples_per_s=sps, loss_history=hist, train_set=int(x.shape[0]))
-        if hold is not None:
-            xh = ((hold["inv"].T - shift) * scale)
-            th = hold["taup"].T / out_scale
-            res["heldout_loss"] = eval_loss(p, xh, th)
-            res["heldout_loss_zero_model"] = float(np.mean(th ** 2))
-        res["normalisation"] = dict(in_shift=shift.tolist(), in_scale=scale.tolist(), out_scale=out_scale.tolist())
-
-        model = make_sgs_model(p.data_ptr(), shift, scale, out_scale)
         u0 = snaps[0]["uc"]
-        for name, mdl in (("model", model), ("no_model", None)):
+
+        def evaluate(mdl):
             r = coarse_run(plan_m, u0, cfg, mdl, log)
             out = dict(finite=r["finite"], steps=r["steps"])
             if r["finite"]:
@@ -341,7 +374,43 @@ def run(cfg: ClosureConfig, log=print):
                 out["long"] = _compare(r["EK_long"], ref, cfg.kcmp)
             else:
                 out["error"] = r["error"]
-            res[name] = out
+            return out
+
+        variants = []
+        first = None
+        for target, w in [(tg, w) for tg in cfg.targets for w in cfg.flux_weights]:
+            inv = np.concatenate([s[target]["inv"] for s in tr], axis=1)
+            taup = np.concatenate([s[target]["taup"] for s in tr], axis=1)
+            shift, scale, out_scale = normalisation(inv, taup, w)
+            x = ((inv.T - shift) * scale).astype(np.float32)
+            t = (taup.T / out_scale).astype(np.float32)
+            del inv, taup
+            p, hist, secs, sps = train(x, t, cfg, log)
+            v = dict(target=target, flux_weight=w, train_seconds=secs, train_samples_per_s=sps,
+                     loss_history=hist, train_set=int(x.shape[0]),
+                     normalisation=dict(in_shift=shift.tolist(), in_scale=scale.tolist(),
+                                        out_scale=out_scale.tolist()))
+            if hold is not None:
+                xh = ((hold[target]["inv"].T - shift) * scale)
+                th = hold[target]["taup"].T / out_scale
+                v["heldout_loss"] = eval_loss(p, xh, th)
+                v["heldout_loss_zero_model"] = float(np.mean(th ** 2))
+            model = make_sgs_model(p.data_ptr(), shift, scale, out_scale)
+            v["model"] = evaluate(model)
+            variants.append(v)
+            if first is None:
+                first = (p, model, v)
+        p, model, v = first
+        for k in ("train_seconds", "train_samples_per_s", "loss_history", "train_set", "heldout_loss",
+                  "heldout_loss_zero_model", "normalisation"):
+            if k in v:
+                res[k] = v[k]
+        res["model"] = v["model"]
+        res["flux_weight"] = v["flux_weight"]
+        res["target"] = v["target"]
+        if len(variants) > 1:
+            res["variants"] = [{k: x[k] for k in x if k not in ("loss_history", "normalisation")} for x in variants]
+        res["no_model"] = evaluate(None)
         res["coarse_steps_per_s"] = timed_coarse_steps(plan_m, u0, cfg, model)
         res["coarse_steps_per_s_no_model"] = timed_coarse_steps(plan_m, u0, cfg, None)
         # wall-clock per unit of simulated time, resolved over coarse
