@@ -767,7 +767,7 @@ int oracle_ns_step_rk4(cplx *uhat, int n, const oracle_ns_params *p, int nsteps)
  *   N_u = P[F(u x omega) + theta z],  N_theta = -i k . F(u theta) + u_z,
  * both 2/3-truncated. */
 int oracle_rbc_rhs(const cplx *st, cplx *out, int n) {
-  if (!is_pow2(n) || n < 2) return -1;
+  if (!ok_grid(n)) return -1;
   const long N = n, HZ = n / 2 + 1, M = N * N * HZ, R = N * N * N;
   int rc = oracle_ns_rhs(st, out, n, NULL); /* P[F(u x omega)] */
   if (rc) return rc;
@@ -816,7 +816,7 @@ int oracle_rbc_rhs(const cplx *st, cplx *out, int n) {
  * integrating factors exp(-nu k^2 dt) for u and exp(-kappa k^2 dt) for theta,
  * in the forms of oracle_ns_step and oracle_ns_step_rk4. */
 int oracle_rbc_step(cplx *st, int n, double Ra, double Pr, double dt, int nsteps, int scheme) {
-  if (!is_pow2(n) || n < 2 || Ra <= 0.0 || Pr <= 0.0 || (scheme != 0 && scheme != 1)) return -1;
+  if (!ok_grid(n) || Ra <= 0.0 || Pr <= 0.0 || (scheme != 0 && scheme != 1)) return -1;
   const long N = n, HZ = n / 2 + 1, M = N * N * HZ;
   const double nu = sqrt(Pr / Ra), kappa = 1.0 / sqrt(Ra * Pr);
   cplx *us = (cplx *)malloc(sizeof(cplx) * 4 * (size_t)M);
