@@ -894,9 +894,10 @@ def run_rbc(n: int, steps: int):
     s0[3].copy_(s0[2])
     del nr
     out = {}
-    for name, scheme, ntr, basis in (("rk4", fk.TARANG_RK4, 52, fk.TARANG_RBC_FFF),
-                                     ("rk2", fk.TARANG_RK2, 26, fk.TARANG_RBC_FFF),
-                                     ("sff_rk4", fk.TARANG_RK4, 52, fk.TARANG_RBC_SFF)):
+    cases = [("rk4", fk.TARANG_RK4, 52, fk.TARANG_RBC_FFF), ("rk2", fk.TARANG_RK2, 26, fk.TARANG_RBC_FFF)]
+    if n & (n - 1) == 0:  # the plates' sine/cosine passes need power-of-two axes
+        cases.append(("sff_rk4", fk.TARANG_RK4, 52, fk.TARANG_RBC_SFF))
+    for name, scheme, ntr, basis in cases:
         s = s0.clone()
         if basis == fk.TARANG_RBC_SFF:  # the same coefficients read in the plates' bases, truncated to them
             s[:, (2 * n - 1) // 3:] = 0

@@ -225,8 +225,13 @@ fftk_status tarang_ns_step(fftk_plan p, void *uhat, const tarang_params *prm, in
  * u theta) transforms per stage, the paper's 52 transforms per RK4 step
  * (Sec. 7), restricted to the truncated set, with the products formed inside
  * the z pass; between plates the x passes are sine/cosine passes.  FP32 in
- * both plan dtypes.  Device memory: 15 more complex fields (allocated on
- * first use, kept by the plan). */
+ * both plan dtypes.  Cubes: n a power of two in [8, 1024] for both bases;
+ * the periodic cube also takes n = 3 * 2^m in [12, 768] (the paper's XC40
+ * convection sizes, Sec. 7), where the right-hand side runs through the
+ * plan's full transforms (radix-3 passes) with the products formed in real
+ * space (7 more real fields).  Other sizes: FFTK_ERR_UNSUPPORTED_SIZE.
+ * Device memory: 15 more complex fields (allocated on first use, kept by
+ * the plan). */
 enum { TARANG_RBC_FFF = 0, TARANG_RBC_SFF = 1 };
 
 typedef struct {

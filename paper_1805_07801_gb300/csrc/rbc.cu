@@ -21,6 +21,7 @@ namespace fftk {
 
 struct RBCWork {
   float2* w7 = nullptr;   // 7 spectra: u, omega, theta; then n (u x omega), u theta, in place
+  float* r7 = nullptr;    // 7 real fields (3 * 2^m cubes: the unfused right-hand side)
   float2* s1 = nullptr;   // stage state (4 fields)
   float2* acc = nullptr;  // RK4 accumulator (4 fields)
   float2* tab = nullptr;  // integrating factors, hi + lo by integer k^2: E_nu, E_kappa, H_nu, H_kappa
@@ -31,6 +32,7 @@ struct RBCWork {
 void rbc_free(RBCWork* r) {
   if (!r) return;
   cudaFree(r->w7);
+  cudaFree(r->r7);
   cudaFree(r->s1);
   cudaFree(r->acc);
   cudaFree(r->tab);
@@ -473,6 +475,64 @@ static cudaError_t rbc_z(fftk_plan p, float2* w, const RBCSlots& sl, cudaStream_
   return cudaErrorInvalidValue;
 }
 
+// Pointwise products of the unfused right-hand side, in place over the seven
+// real fields (u, omega, theta): n = u x omega into 0..2, u theta into 3..5.
+__global__ void k_rbc_products(float* __restrict__ r, long long R) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < R; i += (long long)gridDim.x * blockDim.x) {
+    const float ux = r[i], uy = r[i + R], uz = r[i + 2 * R];
+    const float wx = r[i + 3 * R], wy = r[i + 4 * R], wz = r[i + 5 * R];
+    const float th = r[i + 6 * R];
+    r[i] = fmaf(uy, wz, -uz * wy);
+    r[i + R] = fmaf(uz, wx, -ux * wz);
+    r[i + 2 * R] = fmaf(ux, wy, -uy * wx);
+    r[i + 3 * R] = ux * th;
+    r[i + 4 * R] = uy * th;
+    r[i + 5 * R] = uz * th;
+  }
+}
+
+// The periodic right-hand side on 3 * 2^m cubes, through the plan's full
+// transforms (one radix-3 step per 1D pass): (u, omega, theta) on the kept
+// modes into a cleared workspace, inverse transforms of the seven fields,
+// the products in real space, forward transforms of the six products, then
+// the update of the fused path (which reads only the kept modes).
+static cudaError_t rbc_stage_unfused(fftk_plan p, const float2* x, const float2* u0, float2* out,
+                                     const RBCUpdate& upd, int mode, cudaStream_t st) {
+  NSWork* s = p->ns;
+  RBCWork* r = s->rbc;
+  const NSGeom g = s->g;
+  const long long R = (long long)g.n * g.n * g.n;
+  if (!r->r7) {
+    cudaError_t ea = cudaMalloc(&r->r7, sizeof(float) * 7 * (size_t)R);
+    if (ea != cudaSuccess) {
+      cudaGetLastError();
+      r->r7 = nullptr;
+      return ea;
+    }
+  }
+  const unsigned grid = 152 * 8;
+  float2* w = r->w7;
+  cudaError_t e = cudaMemsetAsync(w, 0, sizeof(float2) * 7 * (size_t)g.M, st);
+  if (e != cudaSuccess) return e;
+  {
+    LaunchScope ls(p, KK_RBC_PREP, st);
+    k_rbc_prep<<<grid, 256, 0, st>>>(x, w, g);
+  }
+  e = c2r_overwrite(p, w, r->r7, 7, st);
+  if (e != cudaSuccess) return e;
+  {
+    LaunchScope ls(p, KK_AUX, st);
+    k_rbc_products<<<grid, 256, 0, st>>>(r->r7, R);
+  }
+  e = r2c_scaled(p, r->r7, w, 6, (float)(1.0 / (double)R), st);
+  if (e != cudaSuccess) return e;
+  {
+    LaunchScope ls(p, KK_RBC_UPDATE, st);
+    k_rbc_update<<<grid, 256, 0, st>>>(w, x, u0, r->s1, r->acc, out, g, upd, mode);
+  }
+  return cudaGetLastError();
+}
+
 // One right-hand side of the stage input x and the update of `mode`:
 // spectral preparation, inverse x and y passes restricted to the kept set,
 // the fused z pass (products in registers), forward y and x passes, update.
@@ -508,6 +568,7 @@ static cudaError_t rbc_stage(fftk_plan p, const float2* x, const float2* u0, flo
     }
     return cudaGetLastError();
   }
+  if (!is_pow2(g.n)) return rbc_stage_unfused(p, x, u0, out, upd, mode, st);
   // w7 = [u_x, u_y, u_z, omega_x, omega_y, omega_z, theta] -> [n_x, n_y, n_z, u_x theta, ...]
   {
     LaunchScope ls(p, KK_RBC_PREP, st);
@@ -527,10 +588,14 @@ static cudaError_t rbc_stage(fftk_plan p, const float2* x, const float2* u0, flo
   return cudaGetLastError();
 }
 
-static fftk_status rbc_check(fftk_plan p, const void* state) {
+// Cubes as for the Navier-Stokes solver (powers of two in [8, 1024], 3 * 2^m
+// in [12, 768]); the plates (SFF) need power-of-two axes for their sine and
+// cosine transforms.
+static fftk_status rbc_check(fftk_plan p, const void* state, int basis = TARANG_RBC_FFF) {
   if (!p || !state || misaligned16(state)) return FFTK_ERR_INVALID_ARG;
   if (p->nx != p->ny || p->nx != p->nz) return FFTK_ERR_UNSUPPORTED_SIZE;
-  if (p->nx < 8 || p->nx > 1024 || !is_pow2(p->nx)) return FFTK_ERR_UNSUPPORTED_SIZE;
+  if (!ns_size_ok(p->nx)) return FFTK_ERR_UNSUPPORTED_SIZE;
+  if (basis == TARANG_RBC_SFF && !is_pow2(p->nx)) return FFTK_ERR_UNSUPPORTED_SIZE;
   return FFTK_OK;
 }
 
@@ -539,10 +604,10 @@ static fftk_status rbc_check(fftk_plan p, const void* state) {
 using namespace fftk;
 
 extern "C" fftk_status tarang_rbc_rhs(fftk_plan p, int basis, const void* state, void* out, void* cuda_stream) {
-  fftk_status s = rbc_check(p, state);
+  if (basis != TARANG_RBC_FFF && basis != TARANG_RBC_SFF) return FFTK_ERR_INVALID_ARG;
+  fftk_status s = rbc_check(p, state, basis);
   if (s != FFTK_OK) return s;
   if (!out || out == state || misaligned16(out)) return FFTK_ERR_INVALID_ARG;
-  if (basis != TARANG_RBC_FFF && basis != TARANG_RBC_SFF) return FFTK_ERR_INVALID_ARG;
   s = rbc_ensure(p);
   if (s != FFTK_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
@@ -557,7 +622,7 @@ extern "C" fftk_status tarang_rbc_rhs(fftk_plan p, int basis, const void* state,
 
 extern "C" fftk_status tarang_rbc_step(fftk_plan p, void* state, const tarang_rbc_params* prm, int nsteps,
                                        void* cuda_stream) {
-  fftk_status s = rbc_check(p, state);
+  fftk_status s = rbc_check(p, state, prm ? prm->basis : TARANG_RBC_FFF);
   if (s != FFTK_OK) return s;
   if (!prm || nsteps < 0 || !(prm->Ra > 0.0) || !(prm->Pr > 0.0) || !(prm->dt > 0.0) || !std::isfinite(prm->Ra) ||
       !std::isfinite(prm->Pr) || !std::isfinite(prm->dt) || (prm->scheme != TARANG_RK2 && prm->scheme != TARANG_RK4) ||
