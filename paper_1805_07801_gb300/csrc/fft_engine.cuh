@@ -85,6 +85,33 @@ __device__ __forceinline__ float2 rot(float2 a, float c, float s) {
   return cmul(a, make_float2(c, SIGN * s));
 }
 
+// cos and sin of pi/16 and 3 pi/16
+#define FFTK_C32A 0.98078528040323044913f
+#define FFTK_S32A 0.19509032201612826785f
+#define FFTK_C32B 0.83146961230254523708f
+#define FFTK_S32B 0.55557023301960222474f
+
+// a * exp(-2 pi i q / 32) for a q (0 <= q < 32) known at compile time after
+// unrolling: the eighth-turn remainder by its (cos, sin) constants, then the
+// quarter and half turns exactly.  The Hermitian-split factor exp(-2 pi i k / N)
+// of a real line of N = 2 G S points at k = j + m S (G values per thread on S
+// threads) is W_j mul_root32 by q = m 16 / G: one table load per thread.
+__device__ __forceinline__ float2 mul_root32(float2 a, int q) {
+  float2 r;
+  switch (q & 7) {
+    case 0: r = a; break;
+    case 1: r = rot<-1>(a, FFTK_C32A, FFTK_S32A); break;
+    case 2: r = rot<-1>(a, FFTK_C16, FFTK_S16); break;
+    case 3: r = rot<-1>(a, FFTK_C32B, FFTK_S32B); break;
+    case 4: r = rot<-1>(a, FFTK_C8, FFTK_C8); break;
+    case 5: r = rot<-1>(a, FFTK_S32B, FFTK_C32B); break;
+    case 6: r = rot<-1>(a, FFTK_S16, FFTK_C16); break;
+    default: r = rot<-1>(a, FFTK_S32A, FFTK_C32A); break;
+  }
+  if (q & 8) r = mul_si<-1>(r);
+  return (q & 16) ? make_float2(-r.x, -r.y) : r;
+}
+
 // --------------------------------------------------------------- codelets --
 // In-place DFT of R values held in registers, natural order in and out.
 template <int SIGN>

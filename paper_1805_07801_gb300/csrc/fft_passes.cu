@@ -51,6 +51,7 @@ __global__ void __launch_bounds__(ZCfg<N>::THREADS, ZCfg<N>::MINB)
   xc.sync();
   if (valid) {
     float2* dst = out + line * (H + 1);
+    const float2 Wj = __ldg(&tw[j]);  // exp(-2 pi i k / N) = W_j exp(-2 pi i m / 2G), k = j + m S
 #pragma unroll
     for (int m = 0; m < G; ++m) {
       const int k = j + m * S;
@@ -59,8 +60,7 @@ __global__ void __launch_bounds__(ZCfg<N>::THREADS, ZCfg<N>::MINB)
       const float2 E = cscale(cadd(A, Bc), 0.5f);
       const float2 D = csub(A, Bc);
       const float2 O = make_float2(0.5f * D.y, -0.5f * D.x);  // D / (2i)
-      const float2 W = __ldg(&tw[k]);                          // exp(-2 pi i k / N)
-      dst[k] = cscale(cadd(E, cmul(W, O)), scale);
+      dst[k] = cscale(cadd(E, cmul(mul_root32(Wj, m * (16 / G)), O)), scale);
     }
     if (j == 0) dst[H] = make_float2((v[0].x - v[0].y) * scale, 0.f);
   }
@@ -83,25 +83,33 @@ __global__ void __launch_bounds__(ZCfg<N>::THREADS, ZCfg<N>::MINB)
   const bool valid = line < nlines;
   const LineX<C::WARP> xc{sm + li * H};
   const float2* src = in + line * (H + 1);
+  // X[0..H-1] of the line pass through the exchange buffer once, so the
+  // mirror X[H - k] is read from there instead of a second global load
+  // (X[H] itself, the k = 0 mirror, is one broadcast load)
   float2 v[G];
 #pragma unroll
   for (int m = 0; m < G; ++m) {
+    v[m] = valid ? src[j + m * S] : make_float2(0.f, 0.f);
+    xc.st(j + m * S, v[m]);
+  }
+  const float2 XH = valid ? src[H] : make_float2(0.f, 0.f);
+  const float2 Wj = __ldg(&tw[j]);  // exp(-2 pi i k / N) = W_j exp(-2 pi i m / 2G), k = j + m S
+  xc.sync();
+#pragma unroll
+  for (int m = 0; m < G; ++m) {
     const int k = j + m * S;
-    float2 A = make_float2(0.f, 0.f), B = make_float2(0.f, 0.f);
-    if (valid) {
-      A = src[k];
-      B = src[H - k];
-    }
+    float2 A = v[m];
+    float2 B = k == 0 ? XH : xc.ld(H - k);
     if (k == 0) {
       A.y = 0.f;
       B.y = 0.f;
     }
     const float2 Bc = cconj(B);
     const float2 E = cadd(A, Bc);
-    const float2 W = __ldg(&tw[k]);
-    const float2 O = cmulc(csub(A, Bc), W);
+    const float2 O = cmulc(csub(A, Bc), mul_root32(Wj, m * (16 / G)));
     v[m] = make_float2(E.x - O.y, E.y + O.x);
   }
+  xc.sync();  // every mirror has been read before the transform's exchanges
   fft_line<H, G, +1, LOGN>(v, j, xc, tw);
   if (valid) {
     float2* dst = reinterpret_cast<float2*>(out + line * N);
