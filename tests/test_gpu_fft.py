@@ -72,6 +72,9 @@ SHAPES = [
     # pass (ragged last tile at 40 columns); the others are ragged tiles of
     # the plain pass for 1024- and 2048-point lines
     (1024, 2, 8), (512, 8, 8), (2048, 1, 8), (4, 1024, 8),
+    # row lengths Q with a remainder past the last full tile (y passes with
+    # Q = nz/2 + 1 = 129, 33, 17 and 25 columns; an x pass with Q = 30)
+    (8, 256, 256), (4, 512, 64), (2, 1024, 32), (16, 256, 48), (256, 6, 8),
 ]
 
 
