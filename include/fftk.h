@@ -83,8 +83,11 @@ fftk_status fftk_plan_create(int nx, int ny, int nz, fftk_dtype dtype, fftk_plan
  * INVALID_ARG. */
 fftk_status fftk_plan_destroy(fftk_plan p);
 
-/* Bytes of device workspace fftk_c2r needs for `batch` transforms
- * (one complex array: batch * nx * ny * (nz/2+1) * 8).  0 on bad arguments. */
+/* Bytes of device workspace fftk_r2c and fftk_c2r need for `batch`
+ * transforms: two complex arrays of batch * nx * ny * (nz/2+1) * 8 bytes when
+ * nx > 1 and ny > 1 (each strided pass then reads one array and writes
+ * another), else one.  fftk_inverse with a Fourier z axis uses the first
+ * array.  0 on bad arguments. */
 size_t fftk_workspace_bytes(fftk_plan p, int batch);
 
 /* Hand the plan a caller-owned device workspace (NULL, 0 = go back to a
@@ -94,7 +97,9 @@ fftk_status fftk_set_workspace(fftk_plan p, void *dev_ptr, size_t bytes);
 /* Forward 3D real-to-complex transform (paper Sec. 3, steps 1-5): z r2c, then
  * y c2c, then x c2c, with the 1/(nx ny nz) factor of Eq. (1)'s inverse.
  * in:  float [batch][nx][ny][nz]; out: float2 [batch][nx][ny][nz/2+1].
- * Out-of-place: overlapping in/out is INVALID_ARG.  `in` is not modified. */
+ * Out-of-place: overlapping in/out is INVALID_ARG.  `in` is not modified.
+ * With nx > 1 and ny > 1 the y pass writes the plan's workspace and the x
+ * pass reads it back (fftk_workspace_bytes). */
 fftk_status fftk_r2c(fftk_plan p, const float *in, void *out, int batch, void *cuda_stream);
 
 /* Inverse 3D complex-to-real transform ("the reverse of the above", Sec. 3):
