@@ -50,6 +50,7 @@ struct RBCWork;  // Rayleigh-Benard scratch, below
 struct NSWork {
   NSGeom g;
   float2* w = nullptr;     // 6 fields
+  float2* w2 = nullptr;    // 6 more fields: the fused passes alternate between w and w2
   float2* u1 = nullptr;    // 3 fields
   float2* etab = nullptr;  // exp(-nu k^2 dt) as hi + lo, k^2 in [0, 3 kd^2]
   int etab_len = 0;
