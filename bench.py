@@ -107,8 +107,8 @@ def fft_pass_bytes(n):
 # --------------------------------------------------- measured DRAM traffic ---
 KERNEL_SOURCES = {
     "ns": ["ns.cu", "ns_common.cuh", "fft_engine.cuh", "internal.h", "tcgen05.cuh"],
-    "fft": ["fft_passes.cu", "fft_engine.cuh", "internal.h"],
-    "fft16": ["fft_tc.cu", "tcgen05.cuh", "fft_passes.cu", "fft_engine.cuh", "internal.h"],
+    "fft": ["fft_passes.cu", "fft_engine.cuh", "internal.h", "abi.cu"],
+    "fft16": ["fft_tc.cu", "tcgen05.cuh", "fft_passes.cu", "fft_engine.cuh", "internal.h", "abi.cu"],
 }
 
 
