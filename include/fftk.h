@@ -83,11 +83,15 @@ fftk_status fftk_plan_create(int nx, int ny, int nz, fftk_dtype dtype, fftk_plan
  * INVALID_ARG. */
 fftk_status fftk_plan_destroy(fftk_plan p);
 
-/* Bytes of device workspace fftk_r2c and fftk_c2r need for `batch`
+/* Bytes of device workspace fftk_r2c and fftk_c2r use for `batch`
  * transforms: two complex arrays of batch * nx * ny * (nz/2+1) * 8 bytes when
  * nx > 1 and ny > 1 (each strided pass then reads one array and writes
- * another), else one.  fftk_inverse with a Fourier z axis uses the first
- * array.  0 on bad arguments. */
+ * another), else one.  fftk_r2c uses the first array only.  With one array
+ * (a caller's smaller buffer, or a plan-owned one when two cannot be
+ * allocated) fftk_c2r runs its y pass in place; with none fftk_r2c runs both
+ * passes in place in `out`, and fftk_c2r fails (OOM or INVALID_ARG).
+ * fftk_inverse with a Fourier z axis uses the first array.  0 on bad
+ * arguments. */
 size_t fftk_workspace_bytes(fftk_plan p, int batch);
 
 /* Hand the plan a caller-owned device workspace (NULL, 0 = go back to a
@@ -99,7 +103,8 @@ fftk_status fftk_set_workspace(fftk_plan p, void *dev_ptr, size_t bytes);
  * in:  float [batch][nx][ny][nz]; out: float2 [batch][nx][ny][nz/2+1].
  * Out-of-place: overlapping in/out is INVALID_ARG.  `in` is not modified.
  * With nx > 1 and ny > 1 the y pass writes the plan's workspace and the x
- * pass reads it back (fftk_workspace_bytes). */
+ * pass reads it back, or both run in place in `out` when no workspace can be
+ * had (fftk_workspace_bytes). */
 fftk_status fftk_r2c(fftk_plan p, const float *in, void *out, int batch, void *cuda_stream);
 
 /* Inverse 3D complex-to-real transform ("the reverse of the above", Sec. 3):

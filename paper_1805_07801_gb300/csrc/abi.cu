@@ -239,10 +239,31 @@ static size_t spec_bytes(fftk_plan p, int batch) {
 // With both strided passes, r2c and c2r run each of them out of place (one
 // spectrum-sized array of workspace for r2c, two for c2r); every pass then
 // reads one array and writes another, which measured faster than the same
-// pass in place (1024^3: forward y 2.19 -> 2.07 ms, forward x 2.10 -> 2.01 ms).
+// pass in place (1024^3: forward y 2.19 -> 2.07 ms, forward x 2.10 -> 2.01 ms,
+// inverse y 2.15 -> 2.04 ms).
 extern "C" size_t fftk_workspace_bytes(fftk_plan p, int batch) {
   if (!p || batch < 1) return 0;
   return spec_bytes(p, batch) * ((p->nx > 1 && p->ny > 1) ? 2 : 1);
+}
+
+// Workspace for the strided passes: `want` spectrum-sized arrays (1 or 2) if
+// the plan's workspace holds them or they can be allocated, else `need`
+// arrays (the passes then run in place where the second array is missing);
+// *got = the number of arrays obtained (0 when none were needed and none
+// could be had).
+static fftk_status pass_ws(fftk_plan p, size_t spec, int want, int need, float2** w, int* got) {
+  void* wv = nullptr;
+  *got = 0;
+  for (int k = want; k >= 1; --k) {
+    const fftk_status s = ensure_ws(p, (size_t)k * spec, &wv);
+    if (s == FFTK_OK) {
+      *w = static_cast<float2*>(wv);
+      *got = k;
+      return FFTK_OK;
+    }
+    if (k <= need) return s;
+  }
+  return FFTK_OK;
 }
 
 extern "C" fftk_status fftk_set_workspace(fftk_plan p, void* dev_ptr, size_t bytes) {
@@ -302,15 +323,18 @@ extern "C" fftk_status fftk_r2c(fftk_plan p, const float* in, void* out, int bat
   const float scale = (float)(1.0 / ((double)p->nx * (double)p->ny * (double)p->nz));
   const bool do_y = p->ny > 1, do_x = p->nx > 1;
   // with both strided passes, the y pass writes the plan's workspace and the
-  // x pass reads it back into `out`
+  // x pass reads it back into `out` (in place in `out` when no workspace can
+  // be had)
   float2* mid = o;
   if (do_x && do_y) {
-    void* wv = nullptr;
-    const size_t wb = fftk_workspace_bytes(p, batch);
-    fftk_status s = ensure_ws(p, wb, &wv);
+    float2* w = nullptr;
+    int got = 0;
+    fftk_status s = pass_ws(p, out_bytes, 1, 0, &w, &got);
     if (s != FFTK_OK) return s;
-    if (overlap(wv, wb, in, in_bytes) || overlap(wv, wb, out, out_bytes)) return FFTK_ERR_INVALID_ARG;
-    mid = static_cast<float2*>(wv);
+    if (got) {
+      if (overlap(w, out_bytes, in, in_bytes) || overlap(w, out_bytes, out, out_bytes)) return FFTK_ERR_INVALID_ARG;
+      mid = w;
+    }
   }
   cudaError_t e = launch_z_r2c(p, in, o, B * p->nx * p->ny, (do_x || do_y) ? 1.f : scale, st);
   if (e == cudaSuccess && do_y)
@@ -333,14 +357,15 @@ extern "C" fftk_status fftk_c2r(fftk_plan p, const void* in, float* out, int bat
   const bool do_x = p->nx > 1, do_y = p->ny > 1;
   cudaError_t e = cudaSuccess;
   if (do_x || do_y) {
-    void* wv = nullptr;
-    const size_t wb = fftk_workspace_bytes(p, batch);
-    fftk_status s = ensure_ws(p, wb, &wv);
+    // x: in -> w0, y: w0 -> w1 (both passes out of place), z: -> out; with
+    // one array of workspace the y pass runs in place in w0
+    float2* w0 = nullptr;
+    int got = 0;
+    fftk_status s = pass_ws(p, in_bytes, (do_x && do_y) ? 2 : 1, 1, &w0, &got);
     if (s != FFTK_OK) return s;
-    if (overlap(wv, wb, in, in_bytes) || overlap(wv, wb, out, out_bytes)) return FFTK_ERR_INVALID_ARG;
-    // x: in -> w0, y: w0 -> w1 (both passes out of place), z: -> out
-    float2* w0 = static_cast<float2*>(wv);
-    float2* w1 = (do_x && do_y) ? w0 + in_bytes / sizeof(float2) : w0;
+    const size_t wb = (size_t)got * in_bytes;
+    if (overlap(w0, wb, in, in_bytes) || overlap(w0, wb, out, out_bytes)) return FFTK_ERR_INVALID_ARG;
+    float2* w1 = got == 2 ? w0 + in_bytes / sizeof(float2) : w0;
     if (do_x) {
       e = strided_pass(p, p->nx, +1, src, w0, B, (long long)p->ny * p->hz, 1.f, KK_X_INV, st);
       src = w0;

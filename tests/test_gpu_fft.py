@@ -193,6 +193,29 @@ def test_caller_workspace_and_launch_count(fk, oracle_mod):
         assert e.value.status == fk.FFTK_ERR_INVALID_ARG
 
 
+def test_smaller_caller_workspaces_run_the_passes_in_place(fk, oracle_mod):
+    # one spectrum of workspace: c2r runs its y pass in place; less than one:
+    # r2c runs both strided passes in place in its output (c2r then fails)
+    import torch
+
+    shape = (32, 16, 64)
+    f = synth.uniform_pm1(4, 0, shape)
+    Fo = oracle_mod.rfft3(f.astype(np.float64))
+    with Plan(fk, shape) as plan:
+        one = fk.fftk_workspace_bytes(plan, 1) // 2
+        ws = torch.empty(one // 4, dtype=torch.float32, device="cuda:0")
+        fk.fftk_set_workspace(plan, ws.data_ptr(), one)
+        Fg = gpu_r2c(fk, plan, f)
+        g = gpu_c2r(fk, plan, Fg.astype(np.complex64), shape[2])
+        assert rel_l2(Fg, Fo) < REL and rel_l2(g, f) < REL
+        small = torch.empty(16, dtype=torch.float32, device="cuda:0")
+        fk.fftk_set_workspace(plan, small.data_ptr(), 64)
+        assert rel_l2(gpu_r2c(fk, plan, f), Fo) < REL
+        with pytest.raises(fk.FFTKError) as e:
+            gpu_c2r(fk, plan, Fg.astype(np.complex64), shape[2])
+        assert e.value.status == fk.FFTK_ERR_INVALID_ARG
+
+
 def test_profile_records_each_pass(fk):
     shape = (64, 64, 64)
     f = synth.uniform_pm1(0, 0, shape)
