@@ -1132,7 +1132,7 @@ def run_fft_sweep(args):
                       "peak_GBps": hbm, "peak_kind": peak_kind, "sizes": out}), flush=True)
 
 
-def run_closure(which: str, out_path: str, flux_weights=None, targets=None):
+def run_closure(which: str, out_path: str, flux_weights=None, targets=None, seeded_runs=0):
     """The learned-closure workflow (resolved snapshots -> filtered data ->
     training -> coarse runs with and without the model); prints one JSON line
     and writes the full results to out_path."""
@@ -1146,6 +1146,8 @@ def run_closure(which: str, out_path: str, flux_weights=None, targets=None):
         cfg = dataclasses.replace(cfg, flux_weights=tuple(flux_weights))
     if targets:
         cfg = dataclasses.replace(cfg, targets=tuple(targets))
+    if seeded_runs:
+        cfg = dataclasses.replace(cfg, seeded_runs=int(seeded_runs))
     res = les.run(cfg, log=lambda s: print(s, file=sys.stderr, flush=True))
     if out_path:
         os.makedirs(os.path.dirname(os.path.abspath(out_path)), exist_ok=True)
@@ -1162,7 +1164,7 @@ def run_closure(which: str, out_path: str, flux_weights=None, targets=None):
             if w in r:
                 line[name][w] = {k: r[w][k] for k in ("max_rel_err", "mean_rel_err", "shells_within_5pct")}
     if "variants" in res:
-        line["variants"] = [{"target": v["target"], "flux_weight": v["flux_weight"],
+        line["variants"] = [{"data": v.get("data"), "target": v["target"], "flux_weight": v["flux_weight"],
                              "heldout_loss": v.get("heldout_loss"),
                              "heldout_loss_zero_model": v.get("heldout_loss_zero_model"),
                              "stated": {k: v["model"]["stated"][k] for k in ("mean_rel_err", "max_rel_err",
@@ -1194,6 +1196,8 @@ def main():
                     help="closure: loss weights of the frame stress's diagonal components, one model each")
     ap.add_argument("--targets", nargs="*", choices=["les", "box", "box_coarse", "blend"], default=None,
                     help="closure: training data sets, one model each (default all four)")
+    ap.add_argument("--seeded-runs", type=int, default=0, metavar="K",
+                    help="closure: also train on one snapshot from each of K separately seeded runs")
     ap.add_argument("--fft-sweep", action="store_true", help="batched pair sweep 256^3 x 64 ... 2048^3")
     ap.add_argument("--forced", type=int, default=0, metavar="N",
                     help="run N^3 forced turbulence for --steps steps and print its JSON line")
@@ -1213,7 +1217,7 @@ def main():
         run_case(args.case)
         return
     if args.closure:
-        run_closure(args.closure, args.closure_out, args.flux_weights, args.targets)
+        run_closure(args.closure, args.closure_out, args.flux_weights, args.targets, args.seeded_runs)
         return
     if args.forced:
         run_forced(args.forced, args.steps)

@@ -85,6 +85,12 @@ class ClosureConfig:
     # the first is reported as "model"
     targets: tuple = ("box", "box_coarse", "les", "blend")
     blend: float = 0.5
+    # a second training set: one snapshot from each of `seeded_runs` runs of
+    # their own (seeds seed + 1, ...), each after the same spin-up; the last
+    # is held out.  Models for `seeded_targets` are trained on it and
+    # evaluated like the others (0 = off)
+    seeded_runs: int = 0
+    seeded_targets: tuple = ("box", "blend")
 
     @property
     def factor(self) -> int:
@@ -216,6 +222,29 @@ def resolved_run(plan_n: int, plan_m: int, cfg: ClosureConfig, log=None):
         secs += advance(plan_n, uhat, prm, ref_steps)
         steps += ref_steps
     return snaps, np.mean(spectra, axis=0), len(spectra), steps / secs
+
+
+def seeded_snapshots(plan_n: int, plan_m: int, cfg: ClosureConfig, log=None):
+    """One filtered snapshot (with closure data) from each of cfg.seeded_runs
+    forced runs seeded seed + 1, seed + 2, ..., each after the spin-up."""
+    prm = make_params(cfg.nu, cfg.dt, cfg.force_eps, (1, 4))
+    spin = int(round(cfg.spinup_time / cfg.dt))
+    chunk = max(1, int(round(0.5 / cfg.dt)))
+    out = []
+    for i in range(cfg.seeded_runs):
+        uhat = initial_state(plan_n, cfg.n, dataclasses.replace(cfg, seed=cfg.seed + 1 + i))
+        done = 0
+        while done < spin:
+            k = min(chunk, spin - done)
+            advance(plan_n, uhat, prm, k)
+            done += k
+        f = filtered_state(plan_n, plan_m, uhat, cfg, True)
+        del f["uc"]
+        out.append(f)
+        if log:
+            log(f"  seeded run {i + 1} (seed {cfg.seed + 1 + i}): filtered E={f['E']:.5f}")
+        del uhat
+    return out
 
 
 def normalisation(inv: np.ndarray, taup: np.ndarray, flux_weight: float = 1.0):
@@ -378,28 +407,37 @@ def run(cfg: ClosureConfig, log=print):
 
         variants = []
         first = None
-        for target, w in [(tg, w) for tg in cfg.targets for w in cfg.flux_weights]:
-            inv = np.concatenate([s[target]["inv"] for s in tr], axis=1)
-            taup = np.concatenate([s[target]["taup"] for s in tr], axis=1)
-            shift, scale, out_scale = normalisation(inv, taup, w)
-            x = ((inv.T - shift) * scale).astype(np.float32)
-            t = (taup.T / out_scale).astype(np.float32)
-            del inv, taup
-            p, hist, secs, sps = train(x, t, cfg, log)
-            v = dict(target=target, flux_weight=w, train_seconds=secs, train_samples_per_s=sps,
-                     loss_history=hist, train_set=int(x.shape[0]),
-                     normalisation=dict(in_shift=shift.tolist(), in_scale=scale.tolist(),
-                                        out_scale=out_scale.tolist()))
-            if hold is not None:
-                xh = ((hold[target]["inv"].T - shift) * scale)
-                th = hold[target]["taup"].T / out_scale
-                v["heldout_loss"] = eval_loss(p, xh, th)
-                v["heldout_loss_zero_model"] = float(np.mean(th ** 2))
-            model = make_sgs_model(p.data_ptr(), shift, scale, out_scale)
-            v["model"] = evaluate(model)
-            variants.append(v)
-            if first is None:
-                first = (p, model, v)
+
+        def train_variants(tr, hold, targets, data):
+            nonlocal first
+            for target, w in [(tg, w) for tg in targets for w in cfg.flux_weights]:
+                inv = np.concatenate([s[target]["inv"] for s in tr], axis=1)
+                taup = np.concatenate([s[target]["taup"] for s in tr], axis=1)
+                shift, scale, out_scale = normalisation(inv, taup, w)
+                x = ((inv.T - shift) * scale).astype(np.float32)
+                t = (taup.T / out_scale).astype(np.float32)
+                del inv, taup
+                p, hist, secs, sps = train(x, t, cfg, log)
+                v = dict(data=data, target=target, flux_weight=w, train_seconds=secs, train_samples_per_s=sps,
+                         loss_history=hist, train_set=int(x.shape[0]),
+                         normalisation=dict(in_shift=shift.tolist(), in_scale=scale.tolist(),
+                                            out_scale=out_scale.tolist()))
+                if hold is not None:
+                    xh = ((hold[target]["inv"].T - shift) * scale)
+                    th = hold[target]["taup"].T / out_scale
+                    v["heldout_loss"] = eval_loss(p, xh, th)
+                    v["heldout_loss_zero_model"] = float(np.mean(th ** 2))
+                model = make_sgs_model(p.data_ptr(), shift, scale, out_scale)
+                v["model"] = evaluate(model)
+                variants.append(v)
+                if first is None:
+                    first = (p, model, v)
+
+        train_variants(tr, hold, cfg.targets, "time-sampled")
+        if cfg.seeded_runs > 1:
+            sn = seeded_snapshots(plan_n, plan_m, dataclasses.replace(cfg, targets=tuple(cfg.seeded_targets)), log)
+            train_variants(sn[:-1], sn[-1], cfg.seeded_targets, "seeded")
+            del sn
         p, model, v = first
         for k in ("train_seconds", "train_samples_per_s", "loss_history", "train_set", "heldout_loss",
                   "heldout_loss_zero_model", "normalisation"):
