@@ -291,20 +291,27 @@ static cudaError_t strided_pass(fftk_plan p, int L, int sign, const float2* in, 
 }
 
 namespace fftk {
-cudaError_t r2c_scaled(fftk_plan p, const float* in, float2* out, long long B, float scale, cudaStream_t st) {
+cudaError_t r2c_scaled(fftk_plan p, const float* in, float2* out, long long B, float scale, cudaStream_t st,
+                       float2* scratch) {
   const bool do_y = p->ny > 1, do_x = p->nx > 1;
+  // with a scratch array the y pass writes it and the x pass reads it back
+  float2* mid = (scratch && do_x && do_y) ? scratch : out;
   cudaError_t e = launch_z_r2c(p, in, out, B * p->nx * p->ny, (do_x || do_y) ? 1.f : scale, st);
   if (e == cudaSuccess && do_y)
-    e = strided_pass(p, p->ny, -1, out, out, B * p->nx, p->hz, do_x ? 1.f : scale, KK_Y_FWD, st);
+    e = strided_pass(p, p->ny, -1, out, mid, B * p->nx, p->hz, do_x ? 1.f : scale, KK_Y_FWD, st);
   if (e == cudaSuccess && do_x)
-    e = strided_pass(p, p->nx, -1, out, out, B, (long long)p->ny * p->hz, scale, KK_X_FWD, st);
+    e = strided_pass(p, p->nx, -1, do_y ? mid : out, out, B, (long long)p->ny * p->hz, scale, KK_X_FWD, st);
   return e;
 }
 
-cudaError_t c2r_overwrite(fftk_plan p, float2* spec, float* out, long long B, cudaStream_t st) {
+cudaError_t c2r_overwrite(fftk_plan p, float2* spec, float* out, long long B, cudaStream_t st, float2* scratch) {
+  // with a scratch array of the spectrum's size the x pass writes it and the
+  // y pass reads it back (both out of place)
+  float2* mid = (scratch && p->nx > 1 && p->ny > 1) ? scratch : spec;
   cudaError_t e = cudaSuccess;
-  if (p->nx > 1) e = strided_pass(p, p->nx, +1, spec, spec, B, (long long)p->ny * p->hz, 1.f, KK_X_INV, st);
-  if (e == cudaSuccess && p->ny > 1) e = strided_pass(p, p->ny, +1, spec, spec, B * p->nx, p->hz, 1.f, KK_Y_INV, st);
+  if (p->nx > 1) e = strided_pass(p, p->nx, +1, spec, mid, B, (long long)p->ny * p->hz, 1.f, KK_X_INV, st);
+  if (e == cudaSuccess && p->ny > 1)
+    e = strided_pass(p, p->ny, +1, p->nx > 1 ? mid : spec, spec, B * p->nx, p->hz, 1.f, KK_Y_INV, st);
   if (e == cudaSuccess) e = launch_z_c2r(p, spec, out, B * p->nx * p->ny, st);
   return e;
 }

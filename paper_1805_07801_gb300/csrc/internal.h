@@ -175,8 +175,12 @@ cudaError_t upload_dft16_operands(fftk_plan p);
 // The plan's forward transform of B real fields without argument checks
 // (scale applied in the last pass), and its inverse of B spectra whose x and y
 // passes run in place (the spectra are overwritten) before the z pass into out.
-cudaError_t r2c_scaled(fftk_plan p, const float* in, float2* out, long long B, float scale, cudaStream_t st);
-cudaError_t c2r_overwrite(fftk_plan p, float2* spec, float* out, long long B, cudaStream_t st);
+// (scratch: optional array of the spectrum's size; given, the strided passes
+// run out of place through it)
+cudaError_t r2c_scaled(fftk_plan p, const float* in, float2* out, long long B, float scale, cudaStream_t st,
+                       float2* scratch = nullptr);
+cudaError_t c2r_overwrite(fftk_plan p, float2* spec, float* out, long long B, cudaStream_t st,
+                          float2* scratch = nullptr);
 // A tiled FP32 tensor map for TMA loads: dims[0] innermost (in floats),
 // strides[i] the byte stride of dimension i + 1 (a multiple of 16), box the
 // box extents (box[0] * 4 bytes a multiple of 16); out-of-range elements of a

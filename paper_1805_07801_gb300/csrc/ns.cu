@@ -877,13 +877,17 @@ static cudaError_t ns_rhs_unfused(fftk_plan p, const float2* u, const float2* u0
     LaunchScope ls(p, KK_AUX, st);
     k_curl_full<<<grid, 256, 0, st>>>(u, s->w, g);
   }
-  e = c2r_overwrite(p, s->w, s->r6, 6, st);
+  // the second six-field workspace holds the strided passes' intermediate
+  // spectra (they run out of place)
+  e = ns_second_workspace(p);
+  if (e != cudaSuccess) return e;
+  e = c2r_overwrite(p, s->w, s->r6, 6, st, s->w2);
   if (e != cudaSuccess) return e;
   {
     LaunchScope ls(p, KK_AUX, st);
     k_cross<<<grid, 256, 0, st>>>(s->r6, R);
   }
-  e = r2c_scaled(p, s->r6, s->w, 3, (float)(1.0 / ((double)g.n * g.n * g.n)), st);
+  e = r2c_scaled(p, s->r6, s->w, 3, (float)(1.0 / ((double)g.n * g.n * g.n)), st, s->w2);
   if (e != cudaSuccess) return e;
   {
     LaunchScope ls(p, KK_AUX, st);
