@@ -73,7 +73,8 @@ def ns_kernel_bytes(n):
 def ns_rhs_bytes_unfused(n):
     """Bytes one right-hand side moves on a 3 * 2^m grid (no fused passes): the
     six spectra cleared and filled with (u, i k x u) on the kept modes, their
-    inverse x and y passes in place and the z pass to six real fields, u x omega
+    inverse x and y passes (out of place through a second workspace, the same
+    bytes) and the z pass to six real fields, u x omega
     (six read, three written), the three forward transforms, and the update
     (n, u and, in stage 2, u1 read and the state written on the kept modes)."""
     A, _, _, M = ns_counts(n)
