@@ -157,7 +157,13 @@ fftk_status fftk_inverse(fftk_plan p, const int *basis, const void *in, float *o
  * x and y passes on the tensor cores (split FP16 radix-16 stages, restricted
  * to the 2/3-rule set) around the same fused FP32 z kernel: curl on the kept
  * modes, inverse x and y of six fields, z with u x omega, forward y and x of
- * three fields, update. */
+ * three fields, update.
+ * Device memory (plan-owned, allocated on the first solver call and kept):
+ * a six-field workspace (rows of n/2 + 1 complex values rounded up to a
+ * multiple of 16), the three-field stage state, and for FP32 plans a second
+ * six-field workspace that the fused passes alternate with the first (about
+ * 8.5 GB at 512^3); 3 * 2^m cubes add six real fields.  Out of memory is
+ * FFTK_ERR_OOM. */
 /* Learned subgrid-stress model (not in the paper; see tarang_mlp_*): the
  * network maps the 5 invariants of the resolved velocity gradient A
  * (tr S^2, tr R^2, tr S^3, tr R^2 S, tr R^2 S^2 with S, R the symmetric and
